@@ -1,0 +1,155 @@
+"""Sequential CPU oracle for the extremum graph (test infrastructure only).
+
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path (the CUDA library and
+its binding) never imports, links or calls it, and the two share no code: the
+oracle is plain C in ``eg_oracle.c`` built with the host compiler.
+
+Every function of the C file follows the paper's definitions one vertex at a
+time (Sec. 3.2 Algorithm 1, Sec. 3.3 and Table 1, Sec. 3.4 Algorithm 2, Sec. 2
+for the arcs); see its header for the list.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import tempfile
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "eg_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libeg_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+EO_OK, EO_ERR_ARG, EO_ERR_NAN, EO_ERR_OOM = 0, 1, 2, 3
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no fast-math: IEEE comparisons only)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    fd, tmp = tempfile.mkstemp(suffix=".so", dir=_BUILD)
+    os.close(fd)
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math",
+           "-ffp-contract=off", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        lib.eo_compute.argtypes = [P, ctypes.c_int, P, ctypes.c_int, ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_void_p)]
+        lib.eo_compute.restype = ctypes.c_int
+        lib.eo_counts.argtypes = [P, P]
+        lib.eo_counts.restype = None
+        lib.eo_copy.argtypes = [P] * 11
+        lib.eo_copy.restype = None
+        lib.eo_free.argtypes = [P]
+        lib.eo_free.restype = None
+        lib.eo_neighbour_offsets.argtypes = [ctypes.c_int, P]
+        lib.eo_neighbour_offsets.restype = ctypes.c_int
+        lib.eo_grid_adjacent.argtypes = [ctypes.c_int, P, P]
+        lib.eo_grid_adjacent.restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+@dataclass
+class OracleGraph:
+    """Extremum graph plus the per-vertex arrays it is built from."""
+    asc: np.ndarray      # uint32[N]   gradient pointer (itself at a maximum)
+    label: np.ndarray    # uint32[N]   maximum reached
+    beta0p: np.ndarray   # uint8[N]    upper-link components
+    maxima: np.ndarray   # uint32[M]   ascending
+    max_val: np.ndarray  # float32[M]
+    saddles: np.ndarray  # uint32[S]   ascending
+    sad_b0: np.ndarray   # uint8[S]
+    sad_val: np.ndarray  # float32[S]
+    row_ptr: np.ndarray  # uint64[S+1]
+    col: np.ndarray      # uint32[A]
+    n_paths: int         # sum of beta0+ over saddles
+
+    def arcs(self):
+        """Set of (saddle, maximum) pairs."""
+        out = set()
+        for i, s in enumerate(self.saddles.tolist()):
+            for m in self.col[self.row_ptr[i]:self.row_ptr[i + 1]].tolist():
+                out.add((s, m))
+        return out
+
+
+def compute(field: np.ndarray, extents=None, naive: bool = False,
+            minimum: bool = False) -> OracleGraph:
+    """Extremum graph of ``field`` (float32).
+
+    ``extents`` lists the grid size per axis with axis 0 fastest; by default it
+    is the numpy shape reversed, so a C-ordered array ``a[z, y, x]`` has
+    ``x`` as axis 0.  ``minimum`` selects the minimum graph (reversed order).
+    """
+    lib = _load()
+    f = np.ascontiguousarray(field, dtype=np.float32).reshape(-1)
+    if extents is None:
+        extents = tuple(reversed(np.asarray(field).shape))
+    ext = np.ascontiguousarray(extents, dtype=np.int64)
+    d = int(ext.size)
+    h = ctypes.c_void_p()
+    st = lib.eo_compute(f.ctypes.data, d, ext.ctypes.data, int(naive), int(minimum),
+                        ctypes.byref(h))
+    if st != EO_OK:
+        raise OracleError({EO_ERR_ARG: "bad argument", EO_ERR_NAN: "NaN in field",
+                           EO_ERR_OOM: "out of memory"}.get(st, str(st)))
+    try:
+        c = np.zeros(5, dtype=np.int64)
+        lib.eo_counts(h, c.ctypes.data)
+        n, nm, ns, npaths, na = (int(x) for x in c)
+        g = OracleGraph(
+            asc=np.empty(n, np.uint32), label=np.empty(n, np.uint32),
+            beta0p=np.empty(n, np.uint8), maxima=np.empty(nm, np.uint32),
+            max_val=np.empty(nm, np.float32), saddles=np.empty(ns, np.uint32),
+            sad_b0=np.empty(ns, np.uint8), sad_val=np.empty(ns, np.float32),
+            row_ptr=np.empty(ns + 1, np.uint64), col=np.empty(na, np.uint32),
+            n_paths=npaths)
+        lib.eo_copy(h, g.asc.ctypes.data, g.label.ctypes.data, g.beta0p.ctypes.data,
+                    g.maxima.ctypes.data, g.max_val.ctypes.data, g.saddles.ctypes.data,
+                    g.sad_b0.ctypes.data, g.sad_val.ctypes.data, g.row_ptr.ctypes.data,
+                    g.col.ctypes.data)
+        return g
+    finally:
+        lib.eo_free(h)
+
+
+def neighbour_offsets(d: int) -> np.ndarray:
+    """Offsets kept by Algorithm 1 against the origin, shape (2(2^d-1), d)."""
+    lib = _load()
+    out = np.zeros((2 * (2 ** d - 1), d), dtype=np.int64)
+    n = lib.eo_neighbour_offsets(d, out.ctypes.data)
+    if n < 0:
+        raise OracleError("bad dimension")
+    return out[:n]
+
+
+def grid_adjacent(p, q) -> bool:
+    """Algorithm 1 on two coordinate vectors."""
+    lib = _load()
+    a = np.ascontiguousarray(p, dtype=np.int64)
+    b = np.ascontiguousarray(q, dtype=np.int64)
+    return bool(lib.eo_grid_adjacent(int(a.size), a.ctypes.data, b.ctypes.data))

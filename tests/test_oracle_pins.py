@@ -1,0 +1,295 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle itself.
+
+  * golden closed forms derived by hand (tests/golden/*.txt, each cites the
+    definitions it follows);
+  * brute force on tiny grids (tests/brute.py: all-pairs Algorithm 1, BFS
+    components, sort-based order, naive walks);
+  * the neighbour count 2(2^d - 1) stated in Sec. 3.2;
+  * the Euler-characteristic identity for a PL function on a disk (2D), which
+    ties the beta0+ counts of all vertices to a global invariant;
+  * symmetries of the Freudenthal neighbourhood (axis permutation, reflection)
+    and invariance under f -> 2f;
+  * densities of maxima in iid noise, 1 / (2^(d+1) - 1) in the interior.
+"""
+import glob
+import zlib
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2303_02724_gb300 import fields as F
+from tests.brute import brute_graph, alg1_adjacent
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- golden ----
+
+def _read_golden(path):
+    meta, sec = {}, {}
+    for line in open(path):
+        line = line.rstrip("\n")
+        if not line.strip():
+            continue
+        if line.startswith("#"):
+            if ":" in line:
+                k, v = line[1:].split(":", 1)
+                meta[k.strip()] = v.strip()
+            continue
+        k, v = line.split(":", 1)
+        sec[k.strip()] = v.strip()
+    return meta, sec
+
+
+def _golden_field(meta, sec):
+    ext = tuple(int(x) for x in meta["extents"].split())
+    if "field" in sec:
+        vals = np.array([float(x) for x in sec["field"].split()], np.float32)
+    else:
+        g = np.array([float(x) for x in sec["gx"].split()], np.float64)
+        h = np.array([float(x) for x in sec["hy"].split()], np.float64)
+        vals = (h[:, None] + g[None, :]).astype(np.float32).reshape(-1)
+    return ext, vals
+
+
+@pytest.mark.parametrize("path", sorted(glob.glob(os.path.join(GOLDEN, "*.txt"))),
+                         ids=lambda p: os.path.basename(p))
+def test_golden(path):
+    meta, sec = _read_golden(path)
+    ext, vals = _golden_field(meta, sec)
+    g = oracle.compute(vals, extents=ext, minimum=bool(int(meta.get("minimum", "0"))))
+    ints = lambda s: [int(x) for x in s.split()] if s else []
+    assert g.maxima.tolist() == ints(sec["maxima"])
+    assert g.saddles.tolist() == ints(sec.get("saddles", ""))
+    assert g.sad_b0.tolist() == ints(sec.get("beta0", ""))
+    arcs = {tuple(int(y) for y in a.split(",")) for a in sec.get("arcs", "").split()}
+    assert g.arcs() == arcs
+    if "labels" in sec:
+        assert g.label.tolist() == ints(sec["labels"])
+    if "labels_rule" in sec:  # 2d_separable: x<=3 -> 29, x>=4 -> 33
+        x = np.arange(vals.size) % ext[0]
+        assert np.array_equal(g.label, np.where(x <= 3, 29, 33).astype(np.uint32))
+    assert np.array_equal(g.max_val, vals[g.maxima])
+    assert np.array_equal(g.sad_val, vals[g.saddles])
+
+
+# ----------------------------------------------------------- Algorithm 1 ----
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4, 5])
+def test_neighbour_count(d):
+    off = oracle.neighbour_offsets(d)
+    assert len(off) == 2 * (2 ** d - 1)                   # Sec. 3.2
+    assert len({tuple(o) for o in off}) == len(off)
+    assert {tuple(-o) for o in off} == {tuple(o) for o in off}  # symmetric
+
+
+def test_neighbours_2d_3d_match_figure():
+    # Fig. 2 (c,f): 6 neighbours in 2D, 14 in 3D; the 2D set is the hexagon
+    got2 = {tuple(o) for o in oracle.neighbour_offsets(2)}
+    assert got2 == {(1, 0), (0, 1), (1, 1), (-1, 0), (0, -1), (-1, -1)}
+    got3 = {tuple(o) for o in oracle.neighbour_offsets(3)}
+    assert len(got3) == 14 and (1, 1, 1) in got3 and (1, -1, 0) not in got3
+
+
+def test_alg1_cases():
+    assert not oracle.grid_adjacent((0, 0), (0, 0))
+    assert oracle.grid_adjacent((1, 1), (0, 0))
+    assert oracle.grid_adjacent((0, 0), (1, 1))
+    assert not oracle.grid_adjacent((1, 0), (0, 1))
+    assert not oracle.grid_adjacent((2, 0), (0, 0))
+    assert oracle.grid_adjacent((3, 4, 5, 6), (3, 5, 6, 6))
+    for p, q in [((0, 0, 0), (1, 0, 1)), ((2, 2), (1, 2)), ((0, 1), (1, 0))]:
+        assert oracle.grid_adjacent(p, q) == alg1_adjacent(p, q)
+
+
+# ------------------------------------------------------------ brute force ---
+
+SHAPES = [(8, 8), (4, 4, 4), (3, 3, 3, 3), (10,), (5, 3), (1, 7), (2, 1, 3), (3, 2, 2, 2),
+          (2, 2), (1,), (2,), (1, 1, 1), (5, 4, 3), (6, 1)]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("kind", ["normal", "ties"])
+@pytest.mark.parametrize("minimum", [False, True])
+def test_brute_force(shape, kind, minimum):
+    n = int(np.prod(shape))
+    seed = zlib.crc32(repr((shape, kind)).encode()) % 1000
+    f = (F.white_noise(shape, seed) if kind == "normal" else F.integer_ties(shape, seed, 3)).values
+    g = oracle.compute(f, extents=shape, minimum=minimum)
+    b = brute_graph(f, shape, minimum=minimum)
+    assert g.asc.tolist() == b["asc"].tolist()
+    assert g.label.tolist() == b["label"].tolist()
+    assert g.beta0p.tolist() == b["beta"].tolist()
+    assert g.maxima.tolist() == b["maxima"]
+    assert g.saddles.tolist() == b["saddles"]
+    assert g.arcs() == b["arcs"]
+    assert g.n_paths == sum(len(b["reps"][s]) for s in b["saddles"])
+    assert n == g.label.size
+
+
+def test_naive_equals_memo():
+    for f in [F.config_2d_256(side=96).values, F.white_noise((17, 13, 11), 7).values,
+              F.integer_ties((9, 8, 7, 3), 3, 2).values]:
+        a = oracle.compute(f)
+        b = oracle.compute(f, naive=True)
+        assert np.array_equal(a.label, b.label)
+        assert np.array_equal(a.col, b.col)
+
+
+# ------------------------------------------------------------- invariants ---
+
+def _higher(f, v, w):
+    return (f[w] > f[v]) | ((f[w] == f[v]) & (w > v))
+
+
+@pytest.mark.parametrize("case", ["2d", "3d", "4d", "ties3d"])
+def test_invariants(case):
+    f = {"2d": lambda: F.config_2d_256(side=80),
+         "3d": lambda: F.config_3d_256(side=24),
+         "4d": lambda: F.white_noise((7, 6, 5, 6), 11),
+         "ties3d": lambda: F.integer_ties((12, 10, 9), 5, 3)}[case]()
+    vals = f.values.reshape(-1)
+    g = oracle.compute(f.values)
+    n = vals.size
+    v = np.arange(n, dtype=np.uint32)
+    is_max = np.zeros(n, bool)
+    is_max[g.maxima] = True
+    # maxima are exactly the fixed points of the gradient (empty upper link)
+    assert np.array_equal(is_max, g.asc == v)
+    assert np.array_equal(is_max, g.beta0p == 0)
+    # the gradient strictly climbs
+    nm = ~is_max
+    assert np.all(_higher(vals, v[nm], g.asc[nm]))
+    # every label is a maximum, maxima label themselves
+    assert np.all(is_max[g.label])
+    assert np.array_equal(g.label[g.maxima], g.maxima)
+    assert len(g.maxima) >= 1
+    # CSR rows sorted, unique, maxima only; label(s) is among the arcs of s
+    for i, s in enumerate(g.saddles):
+        row = g.col[g.row_ptr[i]:g.row_ptr[i + 1]]
+        assert np.all(np.diff(row.astype(np.int64)) > 0)
+        assert np.all(is_max[row])
+        assert g.label[s] in row
+        assert 1 <= len(row) <= g.sad_b0[i]
+    assert g.n_paths == int(g.sad_b0.sum())
+    assert np.array_equal(g.sad_b0, g.beta0p[g.saddles])
+
+
+def test_scale_invariance():
+    f = F.config_3d_256(side=20).values
+    a = oracle.compute(f)
+    b = oracle.compute(f * np.float32(2.0))
+    assert np.array_equal(a.label, b.label) and np.array_equal(a.col, b.col)
+    assert np.array_equal(a.saddles, b.saddles)
+
+
+def _remap_graph(g, mapping):
+    """Graph with every vertex id v replaced by mapping[v] (sets, no order)."""
+    M = set(mapping[g.maxima].tolist())
+    S = set(mapping[g.saddles].tolist())
+    A = {(int(mapping[s]), int(mapping[m])) for s, m in g.arcs()}
+    return M, S, A
+
+
+@pytest.mark.parametrize("shape", [(9, 7), (6, 5, 4), (4, 3, 5, 3)])
+def test_axis_permutation_and_reflection(shape):
+    f = F.white_noise(shape, 21).values
+    assert len(np.unique(f)) == f.size  # tie-free: SoS plays no part
+    g = oracle.compute(f)
+    ids = np.arange(f.size).reshape(f.shape)
+    d = len(shape)
+    # reflection of every axis: v -> N-1-v
+    fr = f[(slice(None, None, -1),) * d].copy()
+    gr = oracle.compute(fr)
+    mapping = ids[(slice(None, None, -1),) * d].reshape(-1)  # new id -> old id
+    inv = np.empty_like(mapping)
+    inv[mapping] = np.arange(f.size)
+    assert _remap_graph(g, inv) == (set(gr.maxima.tolist()), set(gr.saddles.tolist()), gr.arcs())
+    # cyclic permutation of axes
+    perm = tuple(range(1, d)) + (0,)
+    fp = np.ascontiguousarray(np.transpose(f, perm))
+    gp = oracle.compute(fp)
+    mapping = np.transpose(ids, perm).reshape(-1)
+    inv = np.empty_like(mapping)
+    inv[mapping] = np.arange(f.size)
+    assert _remap_graph(g, inv) == (set(gp.maxima.tolist()), set(gp.saddles.tolist()), gp.arcs())
+    assert np.array_equal(inv[g.label], gp.label[inv])
+
+
+def _interior_minima_2d(f):
+    ny, nx = f.shape
+    c = f[1:-1, 1:-1]
+    cnt = np.ones_like(c, dtype=bool)
+    for dy, dx in [(0, 1), (1, 0), (1, 1), (0, -1), (-1, 0), (-1, -1)]:
+        nb = f[1 + dy:ny - 1 + dy, 1 + dx:nx - 1 + dx]
+        cnt &= nb > c
+    return int(cnt.sum())
+
+
+@pytest.mark.parametrize("which", ["cfg2d", "white", "ties"])
+def test_euler_characteristic_2d(which):
+    """Sum over vertices of 1 - chi(upper link) = chi(disk) = 1.
+
+    In 2D a proper part of a link is a union of beta0+ paths (chi = beta0+),
+    and only an interior minimum has the whole link cycle above it (chi = 0)."""
+    f = {"cfg2d": lambda: F.config_2d_256(side=120).values,
+         "white": lambda: F.white_noise((37, 29), 3).values,
+         "ties": lambda: F.integer_ties((31, 23), 4, 5).values}[which]()
+    if which == "ties":
+        # make the interior-minimum count below use the same perturbed order
+        rank = np.argsort(np.lexsort((np.arange(f.size), f.reshape(-1))))
+        f = rank.reshape(f.shape).astype(np.float32)
+    g = oracle.compute(f)
+    total = int(np.sum(1 - g.beta0p.astype(np.int64))) + _interior_minima_2d(f)
+    assert total == 1
+
+
+@pytest.mark.parametrize("d,shape", [(2, (300, 300)), (3, (48, 48, 48)), (4, (16, 16, 16, 16))])
+def test_maxima_density_iid(d, shape):
+    f = F.white_noise(shape, 100 + d).values
+    g = oracle.compute(f)
+    x = np.unravel_index(g.maxima.astype(np.int64), f.shape)
+    interior = np.ones(len(g.maxima), bool)
+    for k in range(d):
+        interior &= (x[k] > 0) & (x[k] < f.shape[k] - 1)
+    n_int = int(np.prod([s - 2 for s in shape]))
+    p = 1.0 / (2 ** (d + 1) - 1)
+    got = interior.sum()
+    sigma = np.sqrt(n_int * p * (1 - p))
+    assert abs(got - n_int * p) < 5 * sigma
+
+
+def test_single_gaussian_one_maximum():
+    for ext in [(33, 29), (17, 19, 15)]:
+        f = F.gaussian_sum(ext, 9, 1, (5.0, 5.0), (1.0, 1.0), True, None).values
+        g = oracle.compute(f)
+        assert len(g.maxima) == 1
+        assert np.all(g.label == g.maxima[0])
+
+
+@pytest.mark.parametrize("shape", [(5, 4, 3), (3, 3, 3, 2)])
+def test_constant_field_higher_d(shape):
+    n = int(np.prod(shape))
+    g = oracle.compute(np.zeros(shape[::-1], np.float32))
+    assert g.maxima.tolist() == [n - 1] and len(g.saddles) == 0
+    assert np.all(g.label == n - 1)
+
+
+def test_signed_zero_and_inf():
+    # -0 == +0 ties by index; infinities are ordinary ordered values
+    f = np.array([0.0, -0.0, np.inf, -np.inf, 1.0], np.float32)
+    g = oracle.compute(f)
+    b = brute_graph(f, (5,))
+    assert g.maxima.tolist() == b["maxima"] == [2, 4]
+    assert g.label.tolist() == b["label"].tolist()
+
+
+def test_errors():
+    with pytest.raises(oracle.OracleError):
+        oracle.compute(np.array([0.0, np.nan], np.float32))
+    with pytest.raises(oracle.OracleError):
+        oracle.compute(np.zeros(4, np.float32), extents=(0, 4))
+    with pytest.raises(oracle.OracleError):
+        oracle.compute(np.zeros(4, np.float32), extents=(1,) * 7)
