@@ -1,0 +1,185 @@
+/*
+ * eg.h -- C ABI of the GB300 extremum-graph library.
+ *
+ * The library computes the extremum graph (maximum graph by default) of a
+ * float32 scalar field sampled on a d-dimensional regular grid, 1 <= d <= 4,
+ * under the Freudenthal triangulation of the grid (Sec. 3.2, Algorithm 1), as
+ * defined in Sec. 2 of Ande, Subhash & Natarajan, "Tachyon: efficient shared
+ * memory parallel computation of extremum graphs":
+ *
+ *   nodes   the maxima (upper link empty) and the (n-1)-saddles (upper link
+ *           with two or more connected components), Table 1;
+ *   arcs    (s, m) iff a gradient path that leaves saddle s through one of its
+ *           upper-link components ends at maximum m (Sec. 3.4, Algorithm 2:
+ *           UpperLinkRep, then follow the gradient = the highest upper-link
+ *           vertex, Sec. 3.3);
+ *   labels  for every vertex, the maximum its gradient path reaches (the
+ *           descending manifold of that maximum, i.e. the Morse decomposition).
+ *
+ * Ties are broken by simulation of simplicity (Sec. 3.3): vertex w is higher
+ * than v iff f[w] > f[v], or f[w] == f[v] and w > v (linear index).  -0.0
+ * equals +0.0; infinities are ordinary values; NaN is rejected.
+ *
+ * Grid layout: axis 0 is fastest; vertex index v = x0 + n0*(x1 + n1*(x2 + ..)).
+ * Every vertex id in and out of the library is this linear index (uint32), so a
+ * field holds at most 2^32 - 1 vertices.
+ *
+ * Conventions for every call:
+ *   - Status codes, never exceptions; the library never aborts the process.
+ *   - "device" pointers are CUDA device pointers on the handle's device;
+ *     "host" pointers are ordinary host memory (pinned or pageable).
+ *   - Streams are passed as void* (a cudaStream_t; NULL = the legacy default
+ *     stream).  Calls enqueue work on the stream and return; the results of a
+ *     computation are ready once eg_get_graph returns EG_OK.
+ *   - The library owns every intermediate and result device buffer until
+ *     eg_release; the caller owns its inputs and its host output buffers.
+ *   - A handle may be used from several host threads; calls on one handle are
+ *     serialised internally.
+ */
+#ifndef EG_H
+#define EG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define EG_API __attribute__((visibility("default")))
+#else
+#define EG_API
+#endif
+
+#define EG_MAX_DIM 4
+
+typedef enum eg_status {
+    EG_OK = 0,
+    EG_ERR_ARG = 1,            /* bad dimension, extent, pointer, size or id      */
+    EG_ERR_NAN = 2,            /* the field holds a NaN                           */
+    EG_ERR_OOM = 3,            /* device or pinned host memory exhausted          */
+    EG_ERR_CUDA = 4,           /* a CUDA runtime call failed                      */
+    EG_ERR_NOT_CONVERGED = 5,  /* gradient-path resolution exceeded its bound     */
+    EG_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up              */
+    EG_ERR_BUSY = 7,           /* admission refused: not enough free device memory */
+    EG_ERR_INTERNAL = 8        /* a device-side consistency check failed          */
+} eg_status;
+
+/* eg_config.flags */
+#define EG_FLAG_MINIMUM_GRAPH 0x1u  /* minimum graph: the same order reversed (Sec. 2) */
+#define EG_FLAG_NO_LABELS     0x2u  /* do not keep per-vertex labels in the result    */
+
+/* Tuning knobs.  Zero in any field means "library default / autotuned". */
+typedef struct eg_config {
+    uint32_t flags;
+    int32_t classify_rows;   /* 2D/3D classification: grid rows per tile step      */
+    int32_t jump_tile;       /* tile edge (vertices) for tile-local path jumping   */
+    int32_t jump_rounds;     /* upper bound on global jump rounds (0 = automatic)  */
+    int32_t persistent_ctas; /* CTAs per SM for the persistent work-queue kernels  */
+    int32_t reserved[3];
+} eg_config;
+
+typedef struct eg_ctx *eg_handle;
+typedef uint64_t eg_result_id;
+
+/* One field of a batch.  field: device float32, caller-owned, valid until the
+ * batch's results are read; extents[k] >= 1 for k < d. */
+typedef struct eg_field_desc {
+    const float *field;
+    int32_t d;
+    int32_t flags;           /* per-field EG_FLAG_* (ORed with the handle's)        */
+    int64_t extents[EG_MAX_DIM];
+} eg_field_desc;
+
+/* Result description.  eg_get_graph always fills the counts; every array
+ * pointer that is non-NULL receives a copy (host memory, caller-allocated with
+ * at least the counted size).  Call once with NULL arrays to learn the sizes. */
+typedef struct eg_graph {
+    int32_t d;
+    int64_t extents[EG_MAX_DIM];
+    int64_t n_vertices;
+    int64_t n_maxima;        /* M                                                   */
+    int64_t n_saddles;       /* S                                                   */
+    int64_t n_paths;         /* P = sum of beta0+ over saddles (gradient paths)     */
+    int64_t n_arcs;          /* A = number of unique (saddle, maximum) pairs        */
+    uint32_t *maxima;        /* [M]   ascending vertex ids                          */
+    float *max_val;          /* [M]   f at each maximum (exact copy)                */
+    uint32_t *saddles;       /* [S]   ascending vertex ids                          */
+    uint8_t *sad_beta0;      /* [S]   upper-link components of each saddle          */
+    float *sad_val;          /* [S]   f at each saddle (exact copy)                 */
+    uint64_t *row_ptr;       /* [S+1] CSR row offsets into col                      */
+    uint32_t *col;           /* [A]   maxima of each saddle, ascending, unique      */
+    uint32_t *labels;        /* [N]   maximum reached from every vertex             */
+} eg_graph;
+
+/* Create a handle on CUDA device `device`.  cfg may be NULL (defaults).
+ * Errors: EG_ERR_ARG (bad device or out == NULL), EG_ERR_CUDA. */
+EG_API eg_status eg_create(eg_handle *out, int device, const eg_config *cfg);
+
+/* Wait for all work of the handle, free every buffer it owns (results
+ * included) and the handle itself.  NULL is accepted. */
+EG_API eg_status eg_destroy(eg_handle h);
+
+/* Extremum graph of one field (Sec. 3.3 classification, Sec. 3.4 arcs).
+ * field: device float32[N], caller-owned, must stay valid until the result is
+ * read; d in 1..4; extents[0..d-1] >= 1, product < 2^32; stream: cudaStream_t.
+ * Enqueues classification, path resolution and graph assembly on `stream`; the
+ * call itself waits only for the node counts (to size the result buffers).
+ * On success *out names the result.
+ * Errors: EG_ERR_ARG, EG_ERR_NAN (field holds NaN), EG_ERR_OOM, EG_ERR_CUDA. */
+EG_API eg_status eg_compute(eg_handle h, const float *field, int d, const int64_t *extents,
+                            void *stream, eg_result_id *out);
+
+/* As eg_compute, for a field in HOST memory: the host-to-device copy of the
+ * field is enqueued on `stream` first (through the handle's pinned staging
+ * buffer when the field is pageable).  field must stay valid until the call
+ * returns. */
+EG_API eg_status eg_compute_host(eg_handle h, const float *field, int d,
+                                 const int64_t *extents, void *stream, eg_result_id *out);
+
+/* Many fields of uneven sizes and dimensions in one launch per step: the
+ * classification and output kernels drain a device work queue of
+ * (field, tile) items, and the whole step sequence is replayed from a
+ * captured CUDA graph when the batch layout repeats.  out_ids[n] receives one
+ * result per field, in order.  Field pointers must stay valid until their
+ * results are read.  Errors as eg_compute; on error no result is created. */
+EG_API eg_status eg_batch_submit(eg_handle h, const eg_field_desc *fields, int n, void *stream,
+                                 eg_result_id *out_ids);
+
+/* Wait for the result and copy it into the caller's host buffers (see
+ * eg_graph).  Device-side failures detected during the computation (NaN,
+ * unbounded path, queue timeout) are reported here.
+ * Errors: EG_ERR_ARG (unknown id), plus any deferred device status. */
+EG_API eg_status eg_get_graph(eg_handle h, eg_result_id id, eg_graph *out);
+
+/* Same as eg_get_graph but fills the array pointers with the library-owned
+ * DEVICE buffers instead of copying (valid until eg_release). */
+EG_API eg_status eg_get_graph_device(eg_handle h, eg_result_id id, eg_graph *out);
+
+/* Free a result's buffers (they return to the handle's pool). */
+EG_API eg_status eg_release(eg_handle h, eg_result_id id);
+
+/* Device memory the library would need to compute a field of this shape
+ * (result buffers excluded), for admission control.  Returns 0 on bad input. */
+EG_API uint64_t eg_workspace_bytes(int d, const int64_t *extents);
+
+/* Free and total device memory seen by the handle's device, plus the bytes the
+ * handle currently holds (pool + live results). */
+EG_API eg_status eg_mem_info(eg_handle h, uint64_t *free_bytes, uint64_t *total_bytes,
+                             uint64_t *held_bytes);
+
+/* Kernel launches issued by the handle since its creation (for accounting). */
+EG_API uint64_t eg_launch_count(eg_handle h);
+
+/* Test hook: make the k-th next device allocation of the handle fail with
+ * EG_ERR_OOM (k = 0 disables).  Host-side fault injection only. */
+EG_API eg_status eg_debug_fail_alloc(eg_handle h, int k);
+
+/* Human-readable name of a status code (static string). */
+EG_API const char *eg_status_str(eg_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EG_H */

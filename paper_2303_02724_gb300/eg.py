@@ -1,0 +1,277 @@
+"""Python binding of the C ABI in include/eg.h (argument marshalling only).
+
+Every step of the computation runs in the CUDA library; this module only
+converts torch tensors / numpy arrays to pointers and sizes and back.  There
+is no CPU fallback: if libeg.so is missing or cannot load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libeg.so")
+MAX_DIM = 4
+
+EG_OK, EG_ERR_ARG, EG_ERR_NAN, EG_ERR_OOM, EG_ERR_CUDA = 0, 1, 2, 3, 4
+EG_ERR_NOT_CONVERGED, EG_ERR_TIMEOUT, EG_ERR_BUSY, EG_ERR_INTERNAL = 5, 6, 7, 8
+EG_FLAG_MINIMUM_GRAPH = 0x1
+EG_FLAG_NO_LABELS = 0x2
+
+
+class EGError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {status_str(status)} ({status})" if what else status_str(status))
+
+
+class EGConfig(ctypes.Structure):
+    _fields_ = [("flags", ctypes.c_uint32), ("classify_rows", ctypes.c_int32),
+                ("jump_tile", ctypes.c_int32), ("jump_rounds", ctypes.c_int32),
+                ("persistent_ctas", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+class EGFieldDesc(ctypes.Structure):
+    _fields_ = [("field", ctypes.c_void_p), ("d", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("extents", ctypes.c_int64 * MAX_DIM)]
+
+
+class EGGraphC(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int32), ("extents", ctypes.c_int64 * MAX_DIM),
+                ("n_vertices", ctypes.c_int64), ("n_maxima", ctypes.c_int64),
+                ("n_saddles", ctypes.c_int64), ("n_paths", ctypes.c_int64),
+                ("n_arcs", ctypes.c_int64),
+                ("maxima", ctypes.c_void_p), ("max_val", ctypes.c_void_p),
+                ("saddles", ctypes.c_void_p), ("sad_beta0", ctypes.c_void_p),
+                ("sad_val", ctypes.c_void_p), ("row_ptr", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("labels", ctypes.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+# name -> (restype, argtypes); every symbol declared in include/eg.h
+_P = ctypes.c_void_p
+SIGNATURES = {
+    "eg_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.POINTER(EGConfig)]),
+    "eg_destroy": (ctypes.c_int, [_P]),
+    "eg_compute": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, ctypes.POINTER(ctypes.c_uint64)]),
+    "eg_compute_host": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, ctypes.POINTER(ctypes.c_uint64)]),
+    "eg_batch_submit": (ctypes.c_int, [_P, ctypes.POINTER(EGFieldDesc), ctypes.c_int, _P,
+                                        ctypes.POINTER(ctypes.c_uint64)]),
+    "eg_get_graph": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(EGGraphC)]),
+    "eg_get_graph_device": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(EGGraphC)]),
+    "eg_release": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "eg_workspace_bytes": (ctypes.c_uint64, [ctypes.c_int, _P]),
+    "eg_mem_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                   ctypes.POINTER(ctypes.c_uint64)]),
+    "eg_launch_count": (ctypes.c_uint64, [_P]),
+    "eg_debug_fail_alloc": (ctypes.c_int, [_P, ctypes.c_int]),
+    "eg_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load libeg.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                               "(the library has no CPU fallback)")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def status_str(s: int) -> str:
+    try:
+        return load().eg_status_str(int(s)).decode()
+    except Exception:  # library missing: still give a readable message
+        return f"status {s}"
+
+
+def _check(s: int, what: str):
+    if s != EG_OK:
+        raise EGError(s, what)
+
+
+def _extents_of(shape) -> tuple:
+    return tuple(int(x) for x in reversed(tuple(shape)))
+
+
+@dataclass
+class Graph:
+    """Extremum graph copied to host memory."""
+    d: int
+    extents: tuple
+    n_vertices: int
+    n_paths: int
+    maxima: np.ndarray
+    max_val: np.ndarray
+    saddles: np.ndarray
+    sad_b0: np.ndarray
+    sad_val: np.ndarray
+    row_ptr: np.ndarray
+    col: np.ndarray
+    labels: Optional[np.ndarray]
+
+    def arcs(self):
+        out = set()
+        for i, s in enumerate(self.saddles.tolist()):
+            for m in self.col[self.row_ptr[i]:self.row_ptr[i + 1]].tolist():
+                out.add((s, m))
+        return out
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class Handle:
+    """One library handle on one CUDA device."""
+
+    def __init__(self, device: int = 0, minimum: bool = False, config: Optional[EGConfig] = None):
+        lib = load()
+        cfg = config if config is not None else EGConfig()
+        if minimum:
+            cfg.flags |= EG_FLAG_MINIMUM_GRAPH
+        h = ctypes.c_void_p()
+        _check(lib.eg_create(ctypes.byref(h), int(device), ctypes.byref(cfg)), "eg_create")
+        self._h = h
+        self._lib = lib
+        self.device = device
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.eg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---------------------------------------------------------------- submit
+    def compute(self, field, stream=None) -> int:
+        """field: contiguous float32 CUDA tensor; axis 0 of the grid is its LAST dim."""
+        if not field.is_cuda or field.dtype.itemsize != 4 or not field.is_contiguous():
+            raise ValueError("field must be a contiguous float32 CUDA tensor")
+        ext = _extents_of(field.shape)
+        e = (ctypes.c_int64 * max(1, len(ext)))(*ext)
+        rid = ctypes.c_uint64()
+        _check(self._lib.eg_compute(self._h, ctypes.c_void_p(field.data_ptr()), len(ext), e,
+                                    ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(rid)),
+               "eg_compute")
+        return rid.value
+
+    def compute_host(self, field: np.ndarray, stream=None) -> int:
+        """field: float32 numpy array in host memory (copied inside the call)."""
+        a = np.ascontiguousarray(field, dtype=np.float32)
+        ext = _extents_of(a.shape)
+        e = (ctypes.c_int64 * max(1, len(ext)))(*ext)
+        rid = ctypes.c_uint64()
+        _check(self._lib.eg_compute_host(self._h, ctypes.c_void_p(a.ctypes.data), len(ext), e,
+                                         ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(rid)),
+               "eg_compute_host")
+        return rid.value
+
+    def batch_submit(self, fields: Sequence, stream=None, flags: Sequence[int] = ()) -> list:
+        n = len(fields)
+        descs = (EGFieldDesc * max(1, n))()
+        for i, f in enumerate(fields):
+            if not f.is_cuda or f.dtype.itemsize != 4 or not f.is_contiguous():
+                raise ValueError("fields must be contiguous float32 CUDA tensors")
+            ext = _extents_of(f.shape)
+            descs[i].field = f.data_ptr()
+            descs[i].d = len(ext)
+            descs[i].flags = int(flags[i]) if i < len(flags) else 0
+            for k, x in enumerate(ext):
+                descs[i].extents[k] = x
+        ids = (ctypes.c_uint64 * max(1, n))()
+        _check(self._lib.eg_batch_submit(self._h, descs, n, ctypes.c_void_p(_stream_ptr(stream)), ids),
+               "eg_batch_submit")
+        return [ids[i] for i in range(n)]
+
+    # --------------------------------------------------------------- results
+    def counts(self, rid: int) -> dict:
+        g = EGGraphC()
+        _check(self._lib.eg_get_graph(self._h, ctypes.c_uint64(rid), ctypes.byref(g)), "eg_get_graph")
+        return dict(n_vertices=g.n_vertices, n_maxima=g.n_maxima, n_saddles=g.n_saddles,
+                    n_paths=g.n_paths, n_arcs=g.n_arcs)
+
+    def get_graph(self, rid: int, labels: bool = True) -> Graph:
+        g = EGGraphC()
+        _check(self._lib.eg_get_graph(self._h, ctypes.c_uint64(rid), ctypes.byref(g)), "eg_get_graph")
+        M, S, A, N = g.n_maxima, g.n_saddles, g.n_arcs, g.n_vertices
+        out = Graph(d=g.d, extents=tuple(g.extents[:g.d]), n_vertices=N, n_paths=g.n_paths,
+                    maxima=np.empty(M, np.uint32), max_val=np.empty(M, np.float32),
+                    saddles=np.empty(S, np.uint32), sad_b0=np.empty(S, np.uint8),
+                    sad_val=np.empty(S, np.float32), row_ptr=np.empty(S + 1, np.uint64),
+                    col=np.empty(A, np.uint32), labels=np.empty(N, np.uint32) if labels else None)
+        g.maxima = out.maxima.ctypes.data
+        g.max_val = out.max_val.ctypes.data
+        g.saddles = out.saddles.ctypes.data
+        g.sad_beta0 = out.sad_b0.ctypes.data
+        g.sad_val = out.sad_val.ctypes.data
+        g.row_ptr = out.row_ptr.ctypes.data
+        g.col = out.col.ctypes.data
+        g.labels = out.labels.ctypes.data if labels else None
+        _check(self._lib.eg_get_graph(self._h, ctypes.c_uint64(rid), ctypes.byref(g)), "eg_get_graph")
+        return out
+
+    def get_graph_device(self, rid: int) -> EGGraphC:
+        g = EGGraphC()
+        _check(self._lib.eg_get_graph_device(self._h, ctypes.c_uint64(rid), ctypes.byref(g)),
+               "eg_get_graph_device")
+        return g
+
+    def release(self, rid: int):
+        _check(self._lib.eg_release(self._h, ctypes.c_uint64(rid)), "eg_release")
+
+    def mem_info(self):
+        fr, to, he = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(self._lib.eg_mem_info(self._h, ctypes.byref(fr), ctypes.byref(to), ctypes.byref(he)),
+               "eg_mem_info")
+        return fr.value, to.value, he.value
+
+    def launch_count(self) -> int:
+        return int(self._lib.eg_launch_count(self._h))
+
+    def debug_fail_alloc(self, k: int):
+        _check(self._lib.eg_debug_fail_alloc(self._h, int(k)), "eg_debug_fail_alloc")
+
+    # ------------------------------------------------------------- one shot
+    def graph_of(self, field, labels: bool = True, stream=None) -> Graph:
+        rid = self.compute(field, stream)
+        try:
+            return self.get_graph(rid, labels)
+        finally:
+            self.release(rid)
+
+
+def workspace_bytes(extents) -> int:
+    e = (ctypes.c_int64 * max(1, len(extents)))(*extents)
+    return int(load().eg_workspace_bytes(len(extents), e))

@@ -1,0 +1,56 @@
+"""The C-ABI library builds, loads and exports every symbol include/eg.h declares.
+
+No compute call is made (this runs without a GPU)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2303_02724_gb300 import _build, eg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    src = open(os.path.join(ROOT, "include", "eg.h")).read()
+    return sorted(set(re.findall(r"EG_API\s+[^;]*?\b(eg_\w+)\s*\(", src, re.S)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    return _build.build()
+
+
+def test_header_declares_the_boundary():
+    syms = _declared_symbols()
+    for name in ["eg_create", "eg_destroy", "eg_compute", "eg_batch_submit", "eg_get_graph",
+                 "eg_release", "eg_status_str"]:
+        assert name in syms
+
+
+def test_every_declared_symbol_is_exported(lib_path):
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True,
+                         check=True).stdout
+    exported = set(re.findall(r"\b(eg_\w+)\b", out))
+    missing = [s for s in _declared_symbols() if s not in exported]
+    assert not missing, missing
+    # nothing else leaks out of the library under the eg_ prefix
+    assert exported <= set(_declared_symbols())
+
+
+def test_binding_covers_header():
+    assert set(eg.SIGNATURES) == set(_declared_symbols())
+
+
+def test_loads_and_host_only_calls(lib_path):
+    lib = eg.load(lib_path)
+    assert eg.status_str(eg.EG_ERR_NAN) == "field contains NaN"
+    assert eg.status_str(0) == "ok"
+    # workspace estimate is pure host arithmetic
+    assert eg.workspace_bytes((256, 256)) > 256 * 256 * 4
+    assert eg.workspace_bytes((0, 4)) == 0
+    assert eg.workspace_bytes((1 << 16, 1 << 16, 2)) == 0  # more than 2^32 - 1 vertices
+    assert lib.eg_launch_count(None) == 0
+    assert lib.eg_release(None, 1) == eg.EG_ERR_ARG
+    assert lib.eg_destroy(None) == eg.EG_OK

@@ -1,0 +1,129 @@
+"""GPU path vs the CPU oracle, element by element (bit-exact: integer outputs,
+and float values that are copies of input values).
+
+All calls go through the C ABI (libeg.so via the ctypes binding)."""
+import zlib
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2303_02724_gb300 import fields as F
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def handle():
+    from paper_2303_02724_gb300 import _build, eg
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    _build.build()
+    h = eg.Handle(0)
+    yield h
+    h.close()
+
+
+@pytest.fixture(scope="module")
+def handle_min():
+    from paper_2303_02724_gb300 import _build, eg
+    _build.build()
+    h = eg.Handle(0, minimum=True)
+    yield h
+    h.close()
+
+
+def assert_same(gg, og, labels=True):
+    assert np.array_equal(gg.maxima, og.maxima), "maxima"
+    assert np.array_equal(gg.saddles, og.saddles), "saddles"
+    assert np.array_equal(gg.sad_b0, og.sad_b0), "beta0+"
+    assert np.array_equal(gg.row_ptr, og.row_ptr), "row_ptr"
+    assert np.array_equal(gg.col, og.col), "col"
+    assert gg.n_paths == og.n_paths
+    assert np.array_equal(gg.max_val.view(np.uint32), og.max_val.view(np.uint32)), "max_val"
+    assert np.array_equal(gg.sad_val.view(np.uint32), og.sad_val.view(np.uint32)), "sad_val"
+    if labels:
+        assert np.array_equal(gg.labels, og.label), "labels"
+
+
+def run_gpu(h, values):
+    t = torch.from_numpy(np.ascontiguousarray(values)).cuda()
+    g = h.graph_of(t)
+    torch.cuda.synchronize()
+    return g
+
+
+SMALL = [(1,), (2,), (7,), (1, 1), (3, 1), (1, 5), (2, 2), (5, 3), (8, 8), (17, 9), (1, 1, 1), (2, 3, 4),
+         (4, 4, 4), (5, 1, 3), (9, 7, 5), (3, 3, 3, 3), (2, 1, 3, 2), (5, 4, 3, 2), (1, 1, 1, 7)]
+
+
+@pytest.mark.parametrize("shape", SMALL, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("kind", ["normal", "ties"])
+def test_small_shapes(handle, shape, kind):
+    seed = zlib.crc32(repr((shape, kind)).encode()) % 10000
+    f = F.white_noise(shape, seed) if kind == "normal" else F.integer_ties(shape, seed, 3)
+    assert_same(run_gpu(handle, f.values), oracle.compute(f.values))
+
+
+@pytest.mark.parametrize("shape", [(8, 8), (4, 4, 4), (3, 3, 3, 3), (33, 17, 5), (300,)])
+def test_minimum_graph(handle_min, shape):
+    f = F.white_noise(shape, 77)
+    assert_same(run_gpu(handle_min, f.values), oracle.compute(f.values, minimum=True))
+
+
+@pytest.mark.parametrize("case", ["2d_cfg_small", "3d_cfg_small", "grf_small", "4d_white", "ties_3d",
+                                  "ragged_2d", "ragged_3d", "constant", "ramp"])
+def test_multi_brick(handle, case):
+    f = {
+        "2d_cfg_small": lambda: F.config_2d_256(side=160),
+        "3d_cfg_small": lambda: F.config_3d_256(side=40),
+        "grf_small": lambda: F.grf((48, 40, 36), 2),
+        "4d_white": lambda: F.white_noise((11, 10, 9, 8), 5),
+        "ties_3d": lambda: F.integer_ties((37, 29, 23), 8, 4),
+        "ragged_2d": lambda: F.white_noise((1023, 3), 9),
+        "ragged_3d": lambda: F.gaussian_sum((65, 33, 17), 3, 7, (3.0, 9.0), (0.5, 1.0), False, ("uniform", 1e-3)),
+        "constant": lambda: F.Field(np.zeros((31, 45), np.float32), (45, 31)),
+        "ramp": lambda: F.Field(np.arange(5000, dtype=np.float32).reshape(50, 100), (100, 50)),
+    }[case]()
+    assert_same(run_gpu(handle, f.values), oracle.compute(f.values))
+
+
+def test_config_2d_256_full(handle):
+    f = F.config_2d_256()
+    assert_same(run_gpu(handle, f.values), oracle.compute(f.values))
+
+
+def test_special_values(handle):
+    v = np.array([[0.0, -0.0, np.inf, -np.inf, 1e-42, -1e-42, 3.4e38, 0.0]], np.float32)
+    assert_same(run_gpu(handle, v), oracle.compute(v))
+
+
+def test_nan_rejected(handle):
+    from paper_2303_02724_gb300 import eg
+    v = np.zeros((16, 16), np.float32)
+    v[3, 7] = np.nan
+    with pytest.raises(eg.EGError) as ei:
+        run_gpu(handle, v)
+    assert ei.value.status == eg.EG_ERR_NAN
+    # the handle stays usable
+    f = F.white_noise((12, 12), 1)
+    assert_same(run_gpu(handle, f.values), oracle.compute(f.values))
+
+
+def test_host_entry_point(handle):
+    f = F.config_3d_256(side=24)
+    rid = handle.compute_host(f.values)
+    g = handle.get_graph(rid)
+    handle.release(rid)
+    assert_same(g, oracle.compute(f.values))
+
+
+def test_batch_uneven(handle):
+    specs = F.batch_specs(3, 24, scale=0.12)
+    flds = [F.batch_field(e, s, gn) for (e, s, gn) in specs]
+    ts = [torch.from_numpy(x.values).cuda() for x in flds]
+    ids = handle.batch_submit(ts)
+    for x, rid in zip(flds, ids):
+        g = handle.get_graph(rid)
+        handle.release(rid)
+        assert_same(g, oracle.compute(x.values))
