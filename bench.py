@@ -1,0 +1,362 @@
+#!/usr/bin/env python
+"""Benchmark of the extremum-graph path on GB300.
+
+One step = one full extremum graph of one field (classification, path
+resolution, arcs and CSR assembly: every step of the hot path), computed by
+libeg.so through its C ABI.  Default workload: the 3D 512^3 float32 Gaussian
+random field with P(k) ~ k^-11/3 (seed 2), the single-field roofline
+configuration.  The field (537 MB) is larger than L2 (129 MB), so no flush is
+needed between timed steps.
+
+Output: ONE JSON line on rank 0 (see the keys below).  Multi-GPU runs (torchrun)
+are replicas: each rank computes its own copy of the workload, no collective
+touches the data path ("scaling": "weak").
+
+--impl reference times the CPU oracle (test infrastructure, sequential C) on
+a bounded slab of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "grf512": ("3D 512^3 float32 Gaussian random field, P(k)~k^-11/3, zero mean, unit variance, seed 2; "
+               "Freudenthal 14-neighbour; plain single-field path"),
+    "gauss3d256": ("3D 256^3 float32, 64 anisotropic Gaussians (sigma U[6,30], amplitude U[0.3,1]) + "
+                   "U(-1e-3,1e-3) noise, seed 1; plain single-field path"),
+    "gauss2d256": ("2D 256x256 float32, 16 isotropic Gaussians (sigma U[4,16], amplitude U[0.5,1]) + "
+                   "N(0,0.01) noise, seed 0"),
+    "grf384": ("3D 384^3 float32 Gaussian random field, P(k)~k^-11/3, seed 2 (profiling case: larger than "
+               "L2, a few GB on the device)"),
+}
+
+
+def make_field(name):
+    from paper_2303_02724_gb300 import fields as F
+    if name == "grf512":
+        return F.config_3d_512()
+    if name == "gauss3d256":
+        return F.config_3d_256()
+    if name == "gauss2d256":
+        return F.config_2d_256()
+    if name == "grf384":
+        return F.config_3d_512(side=384)
+    raise ValueError(name)
+
+
+def oracle_slab(field, max_vertices):
+    """Bounded sample of a field for the CPU oracle: its first slabs along the
+    slowest axis (whole rows/planes), about max_vertices vertices."""
+    v = field.values
+    per = int(v[0].size)
+    k = max(1, min(v.shape[0], max_vertices // per))
+    return v[:k], f"first {k} of {v.shape[0]} slabs along the slowest axis ({k * per} vertices)"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device}.csv") \
+            if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/eg_clocks_{os.getpid()}.csv"
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def path_bytes(c):
+    """Algorithmic bytes of one field: read f, write labels, the graph and its
+    value copies (maxima, saddles, beta0+, row_ptr as uint64, col)."""
+    N, M, S, A = c["n_vertices"], c["n_maxima"], c["n_saddles"], c["n_arcs"]
+    return 4 * N + 4 * N + 8 * M + 9 * S + 8 * (S + 1) + 4 * A
+
+
+def kernel_bytes(c):
+    """Compulsory bytes of each step's own contract (inputs read once, outputs
+    written once).  classify: f, gradient pointers, critical records (12 B),
+    counts; resolve: pointers in, labels out; emit: records in, graph out."""
+    N, M, S, P, A = c["n_vertices"], c["n_maxima"], c["n_saddles"], c["n_paths"], c["n_arcs"]
+    rec = 12 * (M + S)
+    return {"classify": 4 * N + 4 * N + rec,
+            "resolve": 4 * N + 4 * N,
+            "emit": rec + 4 * P + 8 * M + 9 * S + 8 * (S + 1) + 4 * A}
+
+
+def graph_d2h_bytes(c):
+    M, S, A = c["n_maxima"], c["n_saddles"], c["n_arcs"]
+    return 8 * M + 9 * S + 8 * (S + 1) + 4 * A
+
+
+def traffic_from_profiles(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        from paper_2303_02724_gb300 import _build
+        d = json.load(open(p))
+        if d.get("source_fingerprint") != _build._fingerprint():
+            return None
+        return d.get("kernels", {}).get(kernel, {}).get("dram_bytes_per_launch")
+    except Exception:
+        return None
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        if args.impl == "reference":
+            return ws, rank, local
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return ws, rank, local
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle
+    fld = make_field(args.workload)
+    sample, desc = oracle_slab(fld, args.ref_sample_vertices)
+    n = int(sample.size)
+    for _ in range(args.warmup):
+        oracle.compute(sample)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.compute(sample)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = n * args.steps / total / 1e6
+    line = {
+        "impl": "reference", "metric": "Mvertices/s full extremum graph (bit-exact)", "value": value,
+        "unit": "Mvertices/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "sample": desc},
+        "cpu_baseline": {"value": value, "unit": "Mvertices/s", "cores": 1, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": "Mvertices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="grf512", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-sample-vertices", type=int, default=8 * 1024 * 1024)
+    ap.add_argument("--ref-sample-vertices", type=int, default=2 * 1024 * 1024)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+
+    import numpy as np
+    import torch
+    from paper_2303_02724_gb300 import _build, eg
+
+    _build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    fld = make_field(args.workload)
+    N = fld.n
+    t_field = torch.from_numpy(fld.values).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    h = eg.Handle(local)
+    h.set_timing(True)
+
+    def step():
+        rid = h.compute(t_field, stream)
+        g = h.get_graph_device(rid)  # waits for the result (counts only)
+        return rid, g
+
+    counts = None
+    for _ in range(args.warmup):
+        rid, g = step()
+        counts = dict(n_vertices=g.n_vertices, n_maxima=g.n_maxima, n_saddles=g.n_saddles,
+                      n_paths=g.n_paths, n_arcs=g.n_arcs)
+        h.release(rid)
+
+    clocks = ClockSampler(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    launches0 = h.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    step_ms = []
+    for _ in range(args.steps):
+        rid, g = step()
+        step_ms.append(h.step_times(rid))
+        h.release(rid)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if dist is not None:
+        dist.barrier()
+    launches = h.launch_count() - launches0
+    clk = clocks.stop()
+    ms_total = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    value = N * args.steps * ws / (ms_total / 1e3) / 1e6
+
+    # roofline of the dominant step (device time from the library's events)
+    names = ["classify", "resolve", "emit"]
+    mean_ms = {nm: statistics.mean(s[i] for s in step_ms) for i, nm in enumerate(names)}
+    dom = max(mean_ms, key=mean_ms.get)
+    kb = kernel_bytes(counts)
+    peak, peak_kind = peaks()
+    achieved = kb[dom] / (mean_ms[dom] / 1e3) / 1e9
+    mean_step_ms = statistics.mean(s[3] for s in step_ms)
+    pb = path_bytes(counts)
+    path_achieved = pb / (mean_step_ms / 1e3) / 1e9
+
+    # end to end through the C ABI with host buffers: H2D of the field and
+    # D2H of the graph inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        host = torch.from_numpy(fld.values).pin_memory().numpy()
+        for _ in range(2):
+            rid = h.compute_host(host, stream)
+            h.get_graph(rid, labels=False)
+            h.release(rid)
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            rid = h.compute_host(host, stream)
+            h.get_graph(rid, labels=False)
+            h.release(rid)
+        torch.cuda.synchronize(dev)
+        e2e_s = time.perf_counter() - t0
+        if dist is not None:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e_value = N * args.steps * ws / e2e_s / 1e6
+
+        e2e = {"value": e2e_value, "unit": "Mvertices/s", "h2d_bytes_per_step": 4 * N,
+               "d2h_bytes_per_step": graph_d2h_bytes(counts)}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        sample, desc = oracle_slab(fld, args.cpu_sample_vertices)
+        t0 = time.perf_counter()
+        oracle.compute(sample)
+        dt = time.perf_counter() - t0
+        cpu = {"value": sample.size / dt / 1e6, "unit": "Mvertices/s", "cores": 1, "kind": "oracle",
+               "sample": desc + f", {dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": "Mvertices/s full extremum graph (bit-exact)", "value": value, "unit": "Mvertices/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.workload], "vertices": N, "l2": "inputs larger than L2"
+                       if N * 4 > 129e6 else "input smaller than L2; not flushed",
+                       "parallelism": f"replicas x{ws}", **{k: v for k, v in counts.items() if k != "n_vertices"}},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "traffic": traffic_from_profiles(dom),
+                         "algorithmic_bytes": kb[dom], "ms": mean_ms[dom]},
+            "path_roofline": {"achieved": path_achieved, "frac": path_achieved / peak,
+                              "algorithmic_bytes": pb, "ms": mean_step_ms},
+            "step_ms": mean_ms,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    h.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -169,6 +169,16 @@ EG_API uint64_t eg_workspace_bytes(int d, const int64_t *extents);
 EG_API eg_status eg_mem_info(eg_handle h, uint64_t *free_bytes, uint64_t *total_bytes,
                              uint64_t *held_bytes);
 
+/* Step timing.  With timing enabled, every computation records CUDA events on
+ * its own stream around each step; eg_step_times then returns, once the
+ * result is complete, the device time in milliseconds of
+ *   ms[0] classification (steps a+c), ms[1] path resolution (step b),
+ *   ms[2] graph assembly (steps d+e), ms[3] the whole computation.
+ * For a batch every field of the submission reports the batch's times.
+ * Errors: EG_ERR_ARG (unknown id, or timing was off for that computation). */
+EG_API eg_status eg_set_timing(eg_handle h, int enable);
+EG_API eg_status eg_step_times(eg_handle h, eg_result_id id, float ms[4]);
+
 /* Kernel launches issued by the handle since its creation (for accounting). */
 EG_API uint64_t eg_launch_count(eg_handle h);
 

@@ -165,6 +165,12 @@ struct Launch {
     void *desc_dev = nullptr;
     void *desc_host = nullptr;
     size_t bytes = 0;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // step timing (optional)
+    ~Launch()
+    {
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+    }
 };
 
 }  // namespace
@@ -188,6 +194,7 @@ struct eg_ctx {
     std::unordered_map<uint64_t, std::unique_ptr<Result>> results;
     uint64_t next_id = 1;
     std::atomic<uint64_t> launches{0};
+    bool timing = false;
 };
 
 namespace {
@@ -353,6 +360,11 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
     if ((e = cudaMemcpyAsync(L->desc_dev, L->desc_host, L->bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return fail(from_cuda(e));
     const FieldDev *Ddev = static_cast<const FieldDev *>(L->desc_dev);
+    if (h->timing) {
+        for (auto &ev : L->ev)
+            if ((e = cudaEventCreate(&ev)) != cudaSuccess) return fail(from_cuda(e));
+        cudaEventRecord(L->ev[0], st);
+    }
     for (auto &G : groups) {
         if ((e = launch_classify_d(G.d, Ddev + G.first, G.count, G.bricks, st)) != cudaSuccess) return fail(from_cuda(e));
         h->launches++;
@@ -360,6 +372,7 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
     cudaEvent_t k1;
     if ((e = cudaEventCreateWithFlags(&k1, cudaEventDisableTiming)) != cudaSuccess) return fail(from_cuda(e));
     cudaEventRecord(k1, st);
+    if (h->timing) cudaEventRecord(L->ev[1], st);
     for (auto &G : groups) {
         if ((e = launch_resolve(Ddev + G.first, G.count, G.bricks, st)) != cudaSuccess) {
             cudaEventDestroy(k1);
@@ -367,6 +380,7 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
         }
         h->launches++;
     }
+    if (h->timing) cudaEventRecord(L->ev[2], st);
     // node counts: side stream waits for classify only
     void *hcounts = nullptr;
     if ((e = h->hpool.alloc(&hcounts, sizeof(SmallBlock) * size_t(nf))) != cudaSuccess) {
@@ -424,6 +438,7 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
         if ((e = cudaMemsetAsync(h->ws_emit, 0, need, st)) != cudaSuccess) return fail(from_cuda(e));
         char *ws = static_cast<char *>(h->ws_emit);
         size_t pos = 0;
+        if (h->timing) cudaEventRecord(L->ev[3], st);
         for (auto &G : groups) {
             if ((e = launch_emit_d(G.d, Ddev + G.first, G.count, G.bricks, ws + pos, h->sm_count, st)) != cudaSuccess)
                 return fail(from_cuda(e));
@@ -431,6 +446,7 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
             pos += emit_workspace_bytes(G.bricks);
         }
     }
+    if (h->timing) cudaEventRecord(L->ev[4], st);
     cudaEventRecord(h->ws_free, st);
     ids.resize(nf);
     for (int i = 0; i < nf; i++) {
@@ -709,6 +725,37 @@ eg_status eg_mem_info(eg_handle h, uint64_t *free_bytes, uint64_t *total_bytes, 
     if (free_bytes) *free_bytes = fr;
     if (total_bytes) *total_bytes = to;
     if (held_bytes) *held_bytes = h->pool.held;
+    return EG_OK;
+}
+
+eg_status eg_set_timing(eg_handle h, int enable)
+{
+    if (!h) return EG_ERR_ARG;
+    std::lock_guard<std::mutex> g(h->mu);
+    h->timing = enable != 0;
+    return EG_OK;
+}
+
+eg_status eg_step_times(eg_handle h, eg_result_id id, float ms[4])
+{
+    if (!h || !ms) return EG_ERR_ARG;
+    std::lock_guard<std::mutex> g(h->mu);
+    cudaSetDevice(h->device);
+    auto it = h->results.find(id);
+    if (it == h->results.end() || !it->second->launch || !it->second->launch->ev[0]) return EG_ERR_ARG;
+    Launch &L = *it->second->launch;
+    cudaError_t e = cudaEventSynchronize(L.ev[4]);
+    if (e != cudaSuccess) return from_cuda(e);
+    // ev: start | classify | resolve | (count read-back, buffer set-up) | emit
+    float a = 0, b = 0, c = 0, t = 0;
+    cudaEventElapsedTime(&a, L.ev[0], L.ev[1]);
+    cudaEventElapsedTime(&b, L.ev[1], L.ev[2]);
+    cudaEventElapsedTime(&c, L.ev[3], L.ev[4]);
+    cudaEventElapsedTime(&t, L.ev[0], L.ev[4]);
+    ms[0] = a;
+    ms[1] = b;
+    ms[2] = c;
+    ms[3] = t;
     return EG_OK;
 }
 

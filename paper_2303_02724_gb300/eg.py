@@ -70,6 +70,8 @@ SIGNATURES = {
     "eg_workspace_bytes": (ctypes.c_uint64, [ctypes.c_int, _P]),
     "eg_mem_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                    ctypes.POINTER(ctypes.c_uint64)]),
+    "eg_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
+    "eg_step_times": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_float)]),
     "eg_launch_count": (ctypes.c_uint64, [_P]),
     "eg_debug_fail_alloc": (ctypes.c_int, [_P, ctypes.c_int]),
     "eg_status_str": (ctypes.c_char_p, [ctypes.c_int]),
@@ -256,6 +258,15 @@ class Handle:
         _check(self._lib.eg_mem_info(self._h, ctypes.byref(fr), ctypes.byref(to), ctypes.byref(he)),
                "eg_mem_info")
         return fr.value, to.value, he.value
+
+    def set_timing(self, enable: bool = True):
+        _check(self._lib.eg_set_timing(self._h, int(bool(enable))), "eg_set_timing")
+
+    def step_times(self, rid: int):
+        """(classify, resolve, emit, total) device milliseconds of a computation."""
+        ms = (ctypes.c_float * 4)()
+        _check(self._lib.eg_step_times(self._h, ctypes.c_uint64(rid), ms), "eg_step_times")
+        return tuple(float(x) for x in ms)
 
     def launch_count(self) -> int:
         return int(self._lib.eg_launch_count(self._h))
