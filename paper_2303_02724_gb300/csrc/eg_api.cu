@@ -16,7 +16,7 @@
 #include <unordered_map>
 #include <vector>
 
-#include "../../include/eg.h"
+#include "eg.h"
 #include "eg_internal.cuh"
 #include "eg_kernels.h"
 
@@ -152,7 +152,7 @@ struct Result {
     void *lab = nullptr;
     void *small = nullptr;  // SmallBlock on device
     void *maxima = nullptr, *max_val = nullptr, *saddles = nullptr, *sad_b0 = nullptr, *sad_val = nullptr,
-         *row_ptr = nullptr, *col = nullptr;
+         *row_ptr = nullptr, *col = nullptr, *ends = nullptr, *ucnt = nullptr;
     uint64_t M = 0, S = 0, P = 0, A = 0;
     bool have_A = false;
     uint32_t err = 0;
@@ -185,8 +185,13 @@ struct eg_ctx {
     cudaStream_t side = nullptr;
     cudaEvent_t ws_free = nullptr;  // recorded after the last kernel that used the workspace
     // workspace (reused by every computation)
-    void *ws_rec_sid = nullptr, *ws_rec_info = nullptr, *ws_bcnt = nullptr, *ws_emit = nullptr;
+    void *ws_rec_sid = nullptr, *ws_rec_info = nullptr, *ws_rec_val = nullptr;
+    uint64_t ws_rec_cap = 0;
+    void *ws_bcnt = nullptr, *ws_boff = nullptr, *ws_acnt = nullptr, *ws_aoff = nullptr;
     uint64_t ws_bricks = 0;
+    void *ws_scan = nullptr;
+    uint64_t ws_tiles = 0;
+    void *lut3 = nullptr;  // 2^14-bit saddle table of the 3D link graph
     void *stage = nullptr;  // device staging for eg_compute_host
     size_t stage_bytes = 0;
     void *hstage = nullptr;  // pinned staging for pageable host fields
@@ -221,40 +226,113 @@ bool make_shape(int d, const int64_t *ext, Shape &sh)
         if (N > 0xffffffffull) return false;
         sh.n[i] = uint32_t(ext[i]);
     }
+    // fields of 1..3 dimensions run as 3D: unused axes have extent 1
+    for (int i = d; i < kMaxDim; i++) sh.s[i] = uint32_t(N);
     sh.d = d;
     sh.N = N;
     return true;
 }
 
-uint64_t bricks_of(uint64_t N) { return (N + kBrick - 1) / kBrick; }
+// Brick layout of one field (see eg_internal.cuh): row layout for the
+// plane-marching classifier when the rows are short enough, else flat.
+struct Layout {
+    int kd;
+    bool zm;
+    uint32_t ty, nyb, nbricks, bcap, zc, nzc;
+    size_t smem;
+};
 
-eg_status ensure_workspace(eg_ctx *h, uint64_t bricks, cudaStream_t st)
+Layout make_layout(const Shape &sh, int sm_count, const eg_config &cfg)
 {
-    if (bricks <= h->ws_bricks) return EG_OK;
-    // previous computations may still read the old workspace
+    Layout L{};
+    L.kd = sh.d == 4 ? 4 : 3;
+    const uint32_t n0 = sh.n[0], n1 = sh.n[1], n2 = sh.n[2];
+    if (L.kd == 3 && n0 <= 1024) {
+        // one thread per 8 consecutive vertices of a row, 256 threads per CTA
+        const uint32_t txn = (n0 + 7) / 8;
+        uint32_t ty = 256 / txn;
+        if (cfg.classify_rows >= 1) ty = std::min<uint32_t>(ty, uint32_t(cfg.classify_rows));
+        // rows per brick: the saddle queue of the classifier stores ring rows in 7 bits
+        ty = std::max<uint32_t>(1, std::min(std::min(ty, 126u), n1));
+        L.zm = true;
+        L.ty = ty;
+        L.nyb = (n1 + ty - 1) / ty;
+        L.nbricks = L.nyb * n2;
+        L.bcap = ty * n0;
+        // enough work items to fill the GPU a few times over
+        const uint64_t want = uint64_t(std::max(sm_count, 1)) * 8;
+        uint32_t nzc = uint32_t(std::min<uint64_t>(n2, std::max<uint64_t>(1, (want + L.nyb - 1) / L.nyb)));
+        L.zc = (n2 + nzc - 1) / nzc;
+        L.nzc = (n2 + L.zc - 1) / L.zc;
+        L.smem = zm_smem_bytes(n0, ty);
+    } else {
+        L.zm = false;
+        L.ty = 0;
+        L.nyb = 0;
+        L.nbricks = uint32_t((sh.N + kFlatBrick - 1) / kFlatBrick);
+        L.bcap = kFlatBrick;
+        L.zc = L.nzc = 0;
+        L.smem = 0;
+    }
+    return L;
+}
+
+template <typename T>
+eg_status grow(eg_ctx *h, void **p, uint64_t &cap, uint64_t want, size_t elem)
+{
+    if (want <= cap && *p) return EG_OK;
+    h->pool.release(*p);
+    *p = nullptr;
+    cap = 0;
+    const uint64_t c = std::max<uint64_t>(want, 64);
+    cudaError_t e = h->pool.alloc(p, c * elem);
+    if (e != cudaSuccess) return from_cuda(e);
+    cap = c;
+    return EG_OK;
+}
+
+eg_status ensure_workspace(eg_ctx *h, uint64_t recs, uint64_t bricks, uint64_t tiles)
+{
+    if (recs <= h->ws_rec_cap && bricks <= h->ws_bricks && tiles <= h->ws_tiles) return EG_OK;
+    // earlier computations may still use the old workspace
     cudaEventSynchronize(h->ws_free);
-    h->pool.release(h->ws_rec_sid);
-    h->pool.release(h->ws_rec_info);
-    h->pool.release(h->ws_bcnt);
-    h->pool.release(h->ws_emit);
-    h->ws_rec_sid = h->ws_rec_info = h->ws_bcnt = h->ws_emit = nullptr;
-    h->ws_bricks = 0;
-    uint64_t cap = std::max<uint64_t>(bricks, 16);
-    cudaError_t e;
-    if ((e = h->pool.alloc(&h->ws_rec_sid, cap * kBrick * sizeof(uint32_t))) != cudaSuccess) return from_cuda(e);
-    if ((e = h->pool.alloc(&h->ws_rec_info, cap * kBrick * sizeof(uint64_t))) != cudaSuccess) return from_cuda(e);
-    if ((e = h->pool.alloc(&h->ws_bcnt, cap * sizeof(uint4))) != cudaSuccess) return from_cuda(e);
-    if ((e = h->pool.alloc(&h->ws_emit, emit_workspace_bytes(cap) + 256 * kMaxDim)) != cudaSuccess)
-        return from_cuda(e);
-    h->ws_bricks = cap;
-    (void)st;
+    eg_status s;
+    uint64_t cap = h->ws_rec_cap;
+    if (recs > h->ws_rec_cap) {
+        uint64_t c1 = h->ws_rec_cap, c2 = h->ws_rec_cap;
+        if ((s = grow<uint32_t>(h, &h->ws_rec_sid, cap, recs, 4)) != EG_OK) return s;
+        if ((s = grow<uint64_t>(h, &h->ws_rec_info, c1, recs, 8)) != EG_OK) return s;
+        if ((s = grow<float>(h, &h->ws_rec_val, c2, recs, 4)) != EG_OK) return s;
+        h->ws_rec_cap = std::min(cap, std::min(c1, c2));
+    }
+    if (bricks > h->ws_bricks) {
+        uint64_t a = h->ws_bricks, b = h->ws_bricks, c = h->ws_bricks, d = h->ws_bricks;
+        if ((s = grow<uint4>(h, &h->ws_bcnt, a, bricks, sizeof(uint4))) != EG_OK) return s;
+        if ((s = grow<uint4>(h, &h->ws_boff, b, bricks, sizeof(uint4))) != EG_OK) return s;
+        if ((s = grow<uint32_t>(h, &h->ws_acnt, c, bricks, 4)) != EG_OK) return s;
+        if ((s = grow<uint64_t>(h, &h->ws_aoff, d, bricks, 8)) != EG_OK) return s;
+        h->ws_bricks = std::min(std::min(a, b), std::min(c, d));
+    }
+    if (tiles > h->ws_tiles) {
+        uint64_t t = h->ws_tiles;
+        h->pool.release(h->ws_scan);
+        h->ws_scan = nullptr;
+        const uint64_t c = std::max<uint64_t>(tiles, 64);
+        cudaError_t e = h->pool.alloc(&h->ws_scan, scan_workspace_bytes(c));
+        if (e != cudaSuccess) {
+            h->ws_tiles = 0;
+            return from_cuda(e);
+        }
+        (void)t;
+        h->ws_tiles = c;
+    }
     return EG_OK;
 }
 
 void free_result_buffers(eg_ctx *h, Result *r)
 {
-    void **bufs[] = {&r->lab, &r->small, &r->maxima, &r->max_val, &r->saddles,
-                     &r->sad_b0, &r->sad_val, &r->row_ptr, &r->col};
+    void **bufs[] = {&r->lab, &r->small, &r->maxima, &r->max_val, &r->saddles, &r->sad_b0,
+                     &r->sad_val, &r->row_ptr, &r->col, &r->ends, &r->ucnt};
     for (void **b : bufs) {
         h->pool.release(*b);
         *b = nullptr;
@@ -275,18 +353,27 @@ struct Job {
     uint32_t flags;
 };
 
-// Run a set of fields (all of one call) through the three steps.
+// Run a set of fields (all of one call) through the pipeline.
 eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std::vector<uint64_t> &ids)
 {
     const int nf = int(jobs.size());
-    // order fields by dimension so every launch covers a contiguous slice
+    std::vector<Layout> lay(nf);
+    for (int i = 0; i < nf; i++) lay[i] = make_layout(jobs[i].sh, h->sm_count, h->cfg);
+    // group fields by classifier kind so every launch covers a contiguous slice
+    auto key = [&](int i) {
+        return (lay[i].zm ? 0 : 2) * 16 + lay[i].kd * 2 + ((jobs[i].flags & kFlagMinimum) ? 1 : 0);
+    };
     std::vector<int> order(nf);
     for (int i = 0; i < nf; i++) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return jobs[a].sh.d < jobs[b].sh.d; });
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key(a) < key(b); });
 
-    uint64_t total_bricks = 0;
-    for (auto &j : jobs) total_bricks += bricks_of(j.sh.N);
-    eg_status es = ensure_workspace(h, total_bricks, st);
+    uint64_t total_bricks = 0, total_recs = 0, total_tiles = 0;
+    for (int i = 0; i < nf; i++) {
+        total_bricks += lay[i].nbricks;
+        total_recs += uint64_t(lay[i].nbricks) * lay[i].bcap;
+        total_tiles += scan_tiles(lay[i].nbricks);
+    }
+    eg_status es = ensure_workspace(h, total_recs, total_bricks, total_tiles);
     if (es != EG_OK) return es;
 
     auto L = std::make_shared<Launch>();
@@ -305,83 +392,107 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
     };
     if ((e = h->pool.alloc(&L->desc_dev, L->bytes)) != cudaSuccess) return fail(from_cuda(e));
     if ((e = h->hpool.alloc(&L->desc_host, L->bytes)) != cudaSuccess) return fail(from_cuda(e));
-    FieldDev *D = reinterpret_cast<FieldDev *>(L->desc_host);
-    std::memset(D, 0, L->bytes);
+    FieldDev *Dh = reinterpret_cast<FieldDev *>(L->desc_host);
+    std::memset(Dh, 0, L->bytes);
 
-    // per-dimension groups: brick0 is relative to the group's first field
-    uint64_t ws_off = 0;  // brick offset into the shared workspace
-    struct Group { int d, first, count; uint64_t bricks, ws0; };
+    struct Group { int key, first, count; uint64_t brick0, bricks, items; size_t smem; bool zm, minimum; int kd; };
     std::vector<Group> groups;
+    uint64_t brick0 = 0, rec0 = 0, tile0 = 0;
     for (int oi = 0; oi < nf; oi++) {
-        const Job &j = jobs[order[oi]];
-        if (groups.empty() || groups.back().d != j.sh.d) groups.push_back({j.sh.d, oi, 0, 0, ws_off});
+        const int i = order[oi];
+        const Job &j = jobs[i];
+        const Layout &ly = lay[i];
+        if (groups.empty() || groups.back().key != key(i))
+            groups.push_back({key(i), oi, 0, brick0, 0, 0, 0, ly.zm, (j.flags & kFlagMinimum) != 0, ly.kd});
         Group &G = groups.back();
         auto r = std::make_unique<Result>();
         r->d = j.sh.d;
-        for (int i = 0; i < kMaxDim; i++) r->ext[i] = i < j.sh.d ? j.sh.n[i] : 0;
+        for (int q = 0; q < kMaxDim; q++) r->ext[q] = q < j.sh.d ? j.sh.n[q] : 0;
         r->N = j.sh.N;
         r->flags = j.flags;
         r->launch = L;
-        if ((e = h->pool.alloc(&r->lab, j.sh.N * sizeof(uint32_t))) != cudaSuccess) {
-            res[order[oi]] = std::move(r);
-            return fail(from_cuda(e));
-        }
-        if ((e = h->pool.alloc(&r->small, sizeof(SmallBlock))) != cudaSuccess) {
-            res[order[oi]] = std::move(r);
-            return fail(from_cuda(e));
-        }
-        FieldDev &F = D[oi];
+        e = h->pool.alloc(&r->lab, j.sh.N * sizeof(uint32_t));
+        if (e == cudaSuccess) e = h->pool.alloc(&r->small, sizeof(SmallBlock));
+        res[i] = std::move(r);
+        if (e != cudaSuccess) return fail(from_cuda(e));
+        Result &R = *res[i];
+        FieldDev &F = Dh[oi];
         F.f = j.field;
-        F.lab = static_cast<uint32_t *>(r->lab);
-        F.rec_sid = static_cast<uint32_t *>(h->ws_rec_sid) + ws_off * kBrick;
-        F.rec_info = static_cast<uint64_t *>(h->ws_rec_info) + ws_off * kBrick;
-        F.bcnt = static_cast<uint4 *>(h->ws_bcnt) + ws_off;
-        F.totals = reinterpret_cast<SmallBlock *>(r->small)->totals;
-        F.err = &reinterpret_cast<SmallBlock *>(r->small)->err;
-        for (int i = 0; i < kMaxDim; i++) {
-            F.n[i] = j.sh.n[i];
-            F.s[i] = j.sh.s[i];
+        F.lab = static_cast<uint32_t *>(R.lab);
+        F.rec_sid = static_cast<uint32_t *>(h->ws_rec_sid) + rec0;
+        F.rec_info = static_cast<uint64_t *>(h->ws_rec_info) + rec0;
+        F.rec_val = static_cast<float *>(h->ws_rec_val) + rec0;
+        F.bcnt = static_cast<uint4 *>(h->ws_bcnt) + brick0;
+        F.boff = static_cast<uint4 *>(h->ws_boff) + brick0;
+        F.acnt = static_cast<uint32_t *>(h->ws_acnt) + brick0;
+        F.aoff = static_cast<uint64_t *>(h->ws_aoff) + brick0;
+        F.totals = reinterpret_cast<SmallBlock *>(R.small)->totals;
+        F.err = &reinterpret_cast<SmallBlock *>(R.small)->err;
+        for (int q = 0; q < kMaxDim; q++) {
+            F.n[q] = j.sh.n[q];
+            F.s[q] = j.sh.s[q];
         }
         F.N = uint32_t(j.sh.N);
-        F.nbricks = uint32_t(bricks_of(j.sh.N));
-        F.brick0 = G.bricks;
-        F.d = j.sh.d;
+        F.nbricks = ly.nbricks;
+        F.bcap = ly.bcap;
+        F.ty = ly.ty;
+        F.nyb = ly.nyb;
+        F.zc = ly.zc;
+        F.nzc = ly.nzc;
+        F.vec = (j.sh.n[0] % 4 == 0 && (reinterpret_cast<uintptr_t>(j.field) & 15) == 0) ? 1u : 0u;
+        F.brick0 = brick0;
+        F.item0 = G.items;
+        F.stile0 = tile0;
+        F.kd = ly.kd;
         F.flags = j.flags;
-        G.bricks += F.nbricks;
         G.count++;
-        ws_off += F.nbricks;
-        res[order[oi]] = std::move(r);
+        G.bricks += ly.nbricks;
+        G.items += ly.zm ? uint64_t(ly.nyb) * ly.nzc : ly.nbricks;
+        G.smem = std::max(G.smem, ly.smem);
+        brick0 += ly.nbricks;
+        rec0 += uint64_t(ly.nbricks) * ly.bcap;
+        tile0 += scan_tiles(ly.nbricks);
     }
 
-    // the workspace is free once earlier computations' emit kernels finished
+    // the workspace is free once earlier computations' last kernels finished
     if ((e = cudaStreamWaitEvent(st, h->ws_free, 0)) != cudaSuccess) return fail(from_cuda(e));
     for (int i = 0; i < nf; i++)
         if ((e = cudaMemsetAsync(res[i]->small, 0, sizeof(SmallBlock), st)) != cudaSuccess) return fail(from_cuda(e));
+    if ((e = cudaMemsetAsync(h->ws_scan, 0, scan_workspace_bytes(total_tiles), st)) != cudaSuccess)
+        return fail(from_cuda(e));
     if ((e = cudaMemcpyAsync(L->desc_dev, L->desc_host, L->bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return fail(from_cuda(e));
-    const FieldDev *Ddev = static_cast<const FieldDev *>(L->desc_dev);
+    const FieldDev *Dd = static_cast<const FieldDev *>(L->desc_dev);
     if (h->timing) {
         for (auto &ev : L->ev)
             if ((e = cudaEventCreate(&ev)) != cudaSuccess) return fail(from_cuda(e));
         cudaEventRecord(L->ev[0], st);
     }
+    // steps (a)+(c)
     for (auto &G : groups) {
-        if ((e = launch_classify_d(G.d, Ddev + G.first, G.count, G.bricks, st)) != cudaSuccess) return fail(from_cuda(e));
+        if (G.zm)
+            e = launch_classify_zm(G.minimum, Dd + G.first, G.count, G.items, G.smem,
+                                   static_cast<const uint32_t *>(h->lut3), st);
+        else
+            e = launch_classify_flat(G.kd, Dd + G.first, G.count, G.bricks, st);
+        if (e != cudaSuccess) return fail(from_cuda(e));
         h->launches++;
     }
+    // node counts and offsets
+    if ((e = launch_scan(false, Dd, nf, total_tiles, h->ws_scan, st)) != cudaSuccess) return fail(from_cuda(e));
+    h->launches++;
+    if (h->timing) cudaEventRecord(L->ev[1], st);
     cudaEvent_t k1;
     if ((e = cudaEventCreateWithFlags(&k1, cudaEventDisableTiming)) != cudaSuccess) return fail(from_cuda(e));
     cudaEventRecord(k1, st);
-    if (h->timing) cudaEventRecord(L->ev[1], st);
-    for (auto &G : groups) {
-        if ((e = launch_resolve(Ddev + G.first, G.count, G.bricks, st)) != cudaSuccess) {
-            cudaEventDestroy(k1);
-            return fail(from_cuda(e));
-        }
-        h->launches++;
+    // step (b) runs while the host reads the counts back
+    e = launch_resolve(Dd, nf, total_bricks, st);
+    if (e != cudaSuccess) {
+        cudaEventDestroy(k1);
+        return fail(from_cuda(e));
     }
+    h->launches++;
     if (h->timing) cudaEventRecord(L->ev[2], st);
-    // node counts: side stream waits for classify only
     void *hcounts = nullptr;
     if ((e = h->hpool.alloc(&hcounts, sizeof(SmallBlock) * size_t(nf))) != cudaSuccess) {
         cudaEventDestroy(k1);
@@ -406,17 +517,19 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
         r.P = sb.totals[2];
         r.err = sb.err;
         if (sb.err & kErrNaN) first_err = EG_ERR_NAN;
+        else if (sb.err & kErrTimeout) first_err = EG_ERR_TIMEOUT;
     }
     h->hpool.release(hcounts);
     if (first_err != EG_OK) return fail(first_err);
 
-    // exact result buffers
+    // exact result buffers (and the per-result arc staging)
     for (int oi = 0; oi < nf; oi++) {
         Result &r = *res[order[oi]];
-        FieldDev &F = D[oi];
+        FieldDev &F = Dh[oi];
         struct { void **p; size_t b; } want[] = {
             {&r.maxima, r.M * 4}, {&r.max_val, r.M * 4}, {&r.saddles, r.S * 4}, {&r.sad_b0, r.S},
-            {&r.sad_val, r.S * 4}, {&r.row_ptr, (r.S + 1) * 8}, {&r.col, r.P * 4}};
+            {&r.sad_val, r.S * 4}, {&r.row_ptr, (r.S + 1) * 8}, {&r.col, r.P * 4},
+            {&r.ends, r.P * 4}, {&r.ucnt, r.S}};
         for (auto &w : want)
             if ((e = h->pool.alloc(w.p, std::max<size_t>(w.b, 4))) != cudaSuccess) return fail(from_cuda(e));
         F.maxima = static_cast<uint32_t *>(r.maxima);
@@ -426,26 +539,24 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
         F.sad_val = static_cast<float *>(r.sad_val);
         F.row_ptr = static_cast<uint64_t *>(r.row_ptr);
         F.col = static_cast<uint32_t *>(r.col);
+        F.ends = static_cast<uint32_t *>(r.ends);
+        F.ucnt = static_cast<uint8_t *>(r.ucnt);
     }
-    // classify has finished (we waited for it), so the host table may change
+    // classify has finished (we waited for it), so the table may be rewritten;
+    // the copy is ordered after resolve on the stream
     if ((e = cudaMemcpyAsync(L->desc_dev, L->desc_host, L->bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return fail(from_cuda(e));
-    // emit: one ticket counter and look-back array per dimension group, in
-    // consecutive slices of the emit workspace
-    {
-        size_t need = 0;
-        for (auto &G : groups) need += emit_workspace_bytes(G.bricks);
-        if ((e = cudaMemsetAsync(h->ws_emit, 0, need, st)) != cudaSuccess) return fail(from_cuda(e));
-        char *ws = static_cast<char *>(h->ws_emit);
-        size_t pos = 0;
-        if (h->timing) cudaEventRecord(L->ev[3], st);
-        for (auto &G : groups) {
-            if ((e = launch_emit_d(G.d, Ddev + G.first, G.count, G.bricks, ws + pos, h->sm_count, st)) != cudaSuccess)
-                return fail(from_cuda(e));
-            h->launches++;
-            pos += emit_workspace_bytes(G.bricks);
-        }
+    if (h->timing) cudaEventRecord(L->ev[3], st);
+    // steps (d)+(e)
+    for (auto &G : groups) {
+        if ((e = launch_nodes_d(G.kd, Dd + G.first, G.count, G.brick0, G.bricks, st)) != cudaSuccess)
+            return fail(from_cuda(e));
+        h->launches++;
     }
+    if ((e = launch_scan(true, Dd, nf, total_tiles, h->ws_scan, st)) != cudaSuccess) return fail(from_cuda(e));
+    h->launches++;
+    if ((e = launch_csr(Dd, nf, total_bricks, st)) != cudaSuccess) return fail(from_cuda(e));
+    h->launches++;
     if (h->timing) cudaEventRecord(L->ev[4], st);
     cudaEventRecord(h->ws_free, st);
     ids.resize(nf);
@@ -473,6 +584,9 @@ eg_status collect(eg_ctx *h, Result &r)
         r.A = sb.totals[3];
         r.err |= sb.err;
         r.have_A = true;
+        h->pool.release(r.ends);
+        h->pool.release(r.ucnt);
+        r.ends = r.ucnt = nullptr;
         if (r.launch && r.launch.use_count() == 1) release_launch(h, r.launch.get());
     }
     if (r.err & kErrNaN) return EG_ERR_NAN;
@@ -532,6 +646,32 @@ eg_status eg_create(eg_handle *out, int device, const eg_config *cfg)
     if ((e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking)) != cudaSuccess) return from_cuda(e);
     if ((e = cudaEventCreateWithFlags(&h->ws_free, cudaEventDisableTiming)) != cudaSuccess) return from_cuda(e);
     cudaEventRecord(h->ws_free, h->side);
+    {
+        // saddle table of the 3D neighbourhood, 2 bits per upper-link mask m (14
+        // neighbour slots): 0 fewer than two connected components, 1 exactly
+        // two, 2 three or more
+        std::vector<uint32_t> lut(1024, 0u);
+        for (uint32_t m = 0; m < (1u << 14); m++) {
+            uint32_t left = m, comps = 0;
+            while (left) {
+                uint32_t comp = left & (~left + 1u), grow = comp;
+                while (grow) {
+                    const int k = __builtin_ctz(grow);
+                    grow &= grow - 1;
+                    const uint32_t nb = Nbr<3>::adj_mask(k) & m & ~comp;
+                    comp |= nb;
+                    grow |= nb;
+                }
+                left &= ~comp;
+                comps++;
+            }
+            const uint32_t cls = comps < 2 ? 0u : (comps == 2 ? 1u : 2u);
+            lut[m >> 4] |= cls << ((m & 15) * 2);
+        }
+        if ((e = h->pool.alloc(&h->lut3, lut.size() * 4)) != cudaSuccess) return from_cuda(e);
+        if ((e = cudaMemcpy(h->lut3, lut.data(), lut.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+            return from_cuda(e);
+    }
     *out = h.release();
     return EG_OK;
 }
@@ -710,8 +850,12 @@ uint64_t eg_workspace_bytes(int d, const int64_t *extents)
 {
     Shape sh;
     if (!make_shape(d, extents, sh)) return 0;
-    const uint64_t b = bricks_of(sh.N);
-    return b * kBrick * (4 + 8) + b * sizeof(uint4) + emit_workspace_bytes(b) + sh.N * 4;
+    eg_config cfg{};
+    const Layout ly = make_layout(sh, 152, cfg);
+    const uint64_t recs = uint64_t(ly.nbricks) * ly.bcap;
+    // records (id, info, value) + per-brick counts/offsets + scan state + labels
+    return recs * (4 + 8 + 4) + uint64_t(ly.nbricks) * (16 + 16 + 4 + 8) +
+           scan_workspace_bytes(scan_tiles(ly.nbricks)) + sh.N * 4;
 }
 
 eg_status eg_mem_info(eg_handle h, uint64_t *free_bytes, uint64_t *total_bytes, uint64_t *held_bytes)

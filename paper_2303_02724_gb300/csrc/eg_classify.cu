@@ -7,29 +7,27 @@
 // restated on a <= 30-bit register mask); and for a saddle the highest vertex
 // of each component (UpperLinkRep, Sec. 3.4), recorded as its neighbour slot.
 //
-// Work unit: a brick of kBrick consecutive vertex ids.  Every maximum and
-// saddle of a brick is written, in index order, into that brick's record slot,
-// so a later scan over per-brick counts gives global positions directly.
+// This is the general kernel (any d in 1..4, any extents): one CTA per flat
+// brick of kFlatBrick consecutive vertex ids, neighbour values read through
+// the read-only cache.  2D/3D fields with rows of at most 1024 vertices use the
+// plane-marching kernel of eg_classify_zm.cu instead.
+//
+// Every maximum and saddle of a brick is written, in index order, into that
+// brick's record slot, so a scan over per-brick counts gives global positions.
 #include "eg_internal.cuh"
 #include "eg_kernels.h"
 
 namespace eg {
 
 constexpr int kClassifyThreads = 256;
-constexpr int kVpt = kBrick / kClassifyThreads;
+constexpr int kVpt = kFlatBrick / kClassifyThreads;
 
-template <int D>
-__device__ __forceinline__ uint32_t link_flood(uint32_t seed, uint32_t upper, const uint32_t *s_adj)
+// Monotone key of a float: a < b (IEEE, non-NaN) <=> key(a) < key(b); -0 == +0.
+__device__ __forceinline__ uint32_t order_key(float x)
 {
-    uint32_t comp = seed, frontier = seed;
-    while (frontier) {
-        int k = __ffs(frontier) - 1;
-        frontier &= frontier - 1;
-        uint32_t nb = s_adj[k] & upper & ~comp;
-        comp |= nb;
-        frontier |= nb;
-    }
-    return comp;
+    uint32_t u = __float_as_uint(x);
+    u = (u == 0x80000000u) ? 0u : u;
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
 // Classify vertex v of field F.  Returns asc(v); sets b0 and the packed rep
@@ -93,13 +91,13 @@ __device__ __forceinline__ uint32_t classify_vertex(const FieldDev &F, const uin
         b0 = 0;
         return v;
     }
-    uint32_t comp = link_flood<D>(1u << bestk, upper, s_adj);
+    uint32_t comp = link_flood(1u << bestk, upper, s_adj);
     b0 = 1;
     if (comp == upper) return asc;
     codes = uint64_t(bestk);
     uint32_t left = upper & ~comp;
     while (left) {
-        uint32_t c2 = link_flood<D>(left & (~left + 1u), upper, s_adj);
+        uint32_t c2 = link_flood(left & (~left + 1u), upper, s_adj);
         left &= ~c2;
         uint64_t rb = 0;
         int rk = 0;
@@ -126,17 +124,16 @@ k_classify(const FieldDev *__restrict__ fields, int nf)
     const int tid = threadIdx.x;
     if (tid < NB::K) s_adj[tid] = NB::adj_mask(tid);
     if (tid < 3) s_cnt[tid] = 0;
-    const uint64_t g = blockIdx.x;
-    const int fi = find_field(fields, nf, g);
+    const uint64_t g = fields[0].brick0 + blockIdx.x;
+    const int fi = find_field<false>(fields, nf, g);
     const FieldDev &F = fields[fi];
     const uint32_t b = uint32_t(g - F.brick0);
     uint32_t s[kMaxDim];
 #pragma unroll
     for (int i = 0; i < kMaxDim; i++) s[i] = F.s[i];
     const bool minimum = (F.flags & kFlagMinimum) != 0;
-    const uint64_t v0 = uint64_t(b) * kBrick;
-    uint32_t *rsid = F.rec_sid + v0;
-    uint64_t *rinfo = F.rec_info + v0;
+    const uint64_t v0 = uint64_t(b) * kFlatBrick;
+    const uint64_t slot = uint64_t(b) * F.bcap;
     __syncthreads();
 
     uint32_t running = 0, nm = 0, ns = 0, np = 0;
@@ -147,19 +144,22 @@ k_classify(const FieldDev *__restrict__ fields, int nf)
         const bool valid = v64 < F.N;
         int b0 = 1;
         uint64_t codes = 0;
+        float fv = 0.f;
         if (valid) {
             bool nan;
             const uint32_t v = uint32_t(v64);
-            uint32_t asc = classify_vertex<D>(F, s, v, s_adj, minimum, b0, codes, nan);
+            const uint32_t asc = classify_vertex<D>(F, s, v, s_adj, minimum, b0, codes, nan);
             anynan |= nan;
             F.lab[v] = asc;
+            fv = F.f[v];
         }
         const bool crit = valid && b0 != 1;
         uint32_t tot;
         const uint32_t pos = block_excl_scan(crit ? 1u : 0u, s_scan, &tot);
         if (crit) {
-            rsid[running + pos] = uint32_t(v64);
-            rinfo[running + pos] = (uint64_t(b0) << 56) | codes;
+            F.rec_sid[slot + running + pos] = uint32_t(v64);
+            F.rec_info[slot + running + pos] = (uint64_t(b0) << 56) | codes;
+            F.rec_val[slot + running + pos] = fv;
             if (b0 == 0) nm++;
             else {
                 ns++;
@@ -178,29 +178,22 @@ k_classify(const FieldDev *__restrict__ fields, int nf)
         if (np) atomicAdd(&s_cnt[2], np);
     }
     __syncthreads();
-    if (tid == 0) {
-        F.bcnt[b] = make_uint4(s_cnt[0], s_cnt[1], s_cnt[2], 0u);
-        if (s_cnt[0]) atomicAdd(&F.totals[0], (unsigned long long)s_cnt[0]);
-        if (s_cnt[1]) atomicAdd(&F.totals[1], (unsigned long long)s_cnt[1]);
-        if (s_cnt[2]) atomicAdd(&F.totals[2], (unsigned long long)s_cnt[2]);
-    }
+    if (tid == 0) F.bcnt[b] = make_uint4(s_cnt[0], s_cnt[1], s_cnt[2], 0u);
 }
 
 template <int D>
-cudaError_t launch_classify(const FieldDev *fields, int nf, uint64_t total_bricks, cudaStream_t st)
+cudaError_t launch_classify(const FieldDev *fields, int nf, uint64_t bricks, cudaStream_t st)
 {
-    if (total_bricks == 0) return cudaSuccess;
-    k_classify<D><<<dim3(unsigned(total_bricks)), kClassifyThreads, 0, st>>>(fields, nf);
+    if (bricks == 0) return cudaSuccess;
+    k_classify<D><<<dim3(unsigned(bricks)), kClassifyThreads, 0, st>>>(fields, nf);
     return cudaGetLastError();
 }
 
-cudaError_t launch_classify_d(int d, const FieldDev *fields, int nf, uint64_t total_bricks, cudaStream_t st)
+cudaError_t launch_classify_flat(int kd, const FieldDev *fields, int nf, uint64_t bricks, cudaStream_t st)
 {
-    switch (d) {
-    case 1: return launch_classify<1>(fields, nf, total_bricks, st);
-    case 2: return launch_classify<2>(fields, nf, total_bricks, st);
-    case 3: return launch_classify<3>(fields, nf, total_bricks, st);
-    case 4: return launch_classify<4>(fields, nf, total_bricks, st);
+    switch (kd) {
+    case 3: return launch_classify<3>(fields, nf, bricks, st);
+    case 4: return launch_classify<4>(fields, nf, bricks, st);
     default: return cudaErrorInvalidValue;
     }
 }

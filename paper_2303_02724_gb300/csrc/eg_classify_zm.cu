@@ -1,0 +1,489 @@
+// Steps (a) + (c) for 2D and 3D fields whose rows hold at most 1024 vertices:
+// plane-marching classification (Sec. 3.3, Table 1; 2D runs as 3D, n2 = 1).
+//
+// A CTA owns `ty` whole rows of the grid (a row block) and marches along the
+// slowest axis over `zc` planes.  A ring of four plane buffers in shared
+// memory holds planes z-1, z, z+1 while plane z+2 streams in with cp.async;
+// each buffer holds rows y0-1 .. y0+ty of one plane, each row padded by four
+// NaN on both sides.  Out-of-domain rows and planes are NaN as well, and every
+// ordered comparison with NaN is false, so no bounds test is needed: a NaN
+// neighbour is never upper, never the maximum, never equal.
+//
+// Each thread classifies a 4 x 2 block of vertices (x..x+3, y..y+1) of plane z
+// from register copies of the 10 row segments the block's 14-neighbourhoods
+// touch.  Per vertex:
+//   upper   bit k set iff neighbour k is higher (value, then index: ties go to
+//           the positive slots, which have larger indices);
+//   asc     the highest neighbour: max value, ties to the highest slot rank;
+//   saddle  beta0+ >= 2, looked up in a 2^14-bit table indexed by the upper
+//           mask (built on the host from the link graph); the components and
+//           their highest vertices (UpperLinkRep, Sec. 3.4) are then found by
+//           flood fill, for saddles only.
+// The minimum graph negates every value and swaps the tie rule.
+//
+// One row block of one plane is one brick (contiguous ids): its maxima and
+// saddles go, in index order, to the brick's record slot; asc goes to lab.
+#include <atomic>
+
+#include "eg_internal.cuh"
+#include "eg_kernels.h"
+
+namespace eg {
+
+constexpr int kZmThreads = 256;
+
+__device__ __forceinline__ void cp_async16(float *smem, const float *gmem)
+{
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async4(float *smem, const float *gmem)
+{
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Shared-memory geometry of one field's ring buffers (in floats).
+struct ZmGeom {
+    uint32_t n0, n1, n2, ty, rstride, rb;
+};
+
+// Ring buffer: rows of n0 values separated by 8 NaN (each row's trailing pad is
+// the next row's leading pad), 8 more at each end; a thread reads columns
+// x-1 .. x+8 with x < n0, so every read stays inside its buffer.
+__host__ __device__ __forceinline__ uint32_t zm_ring_floats(uint32_t n0, uint32_t ty)
+{
+    return ((ty + 2) * (n0 + 8) + 16 + 3) & ~3u;
+}
+
+// Stream rows [ylo, yhi) of plane z into ring slot `buf` (or NaN-fill the slot
+// when z is past the last plane).  Always commits one cp.async group.
+__device__ __forceinline__ void zm_load_plane(const FieldDev &F, const ZmGeom &G, float *buf, int z, uint32_t y0,
+                                              uint32_t ylo, uint32_t yhi, bool vec)
+{
+    const int tid = threadIdx.x;
+    const uint32_t rows = yhi - ylo;
+    float *dst0 = buf + 8 + (ylo - y0 + 1) * G.rstride;
+    if (z < 0) {
+        cp_async_commit();
+        return;
+    }
+    if (uint32_t(z) >= G.n2) {
+        const float qnan = __int_as_float(0x7fc00000);
+        for (uint32_t c = tid; c < rows * G.n0; c += kZmThreads) {
+            const uint32_t r = c / G.n0, x = c - r * G.n0;
+            dst0[r * G.rstride + x] = qnan;
+        }
+        cp_async_commit();
+        return;
+    }
+    const float *src0 = F.f + (uint64_t(z) * G.n1 + ylo) * G.n0;
+    if (vec) {
+        const uint32_t cpr = G.n0 >> 2;
+        for (uint32_t c = tid; c < rows * cpr; c += kZmThreads) {
+            const uint32_t r = c / cpr, c4 = c - r * cpr;
+            cp_async16(dst0 + r * G.rstride + 4 * c4, src0 + uint64_t(r) * G.n0 + 4 * c4);
+        }
+    } else {
+        for (uint32_t c = tid; c < rows * G.n0; c += kZmThreads) {
+            const uint32_t r = c / G.n0, x = c - r * G.n0;
+            cp_async4(dst0 + r * G.rstride + x, src0 + uint64_t(r) * G.n0 + x);
+        }
+    }
+    cp_async_commit();
+}
+
+// Value as the comparisons see it: negated for the minimum graph.
+template <bool MIN>
+__device__ __forceinline__ float zv(float x)
+{
+    return MIN ? -x : x;
+}
+
+// Highest slot of mask c2 (value, then rank; reversed tie rule for the
+// minimum graph).
+template <bool MIN>
+__device__ __forceinline__ int masked_top(const float (&nb)[14], uint32_t c2)
+{
+    float best = 0.f;
+    int rk = -1;
+#pragma unroll
+    for (int k = 0; k < 14; k++)
+        if ((c2 >> k) & 1u)
+            if (rk < 0 || (MIN ? nb[k] > best : nb[k] >= best)) {
+                best = nb[k];
+                rk = k;
+            }
+    return rk;
+}
+
+// Upper-link components of one saddle and the highest vertex of each
+// (UpperLinkRep, Sec. 3.4), packed as 5-bit slots with beta0+ in bits 56..59.
+// first: the gradient slot (highest of all upper neighbours); cls: 1 when the
+// table says exactly two components, so the second is the rest of the mask.
+template <bool MIN>
+__device__ __forceinline__ uint64_t saddle_info(const float (&nb)[14], uint32_t upper, int first, uint32_t cls,
+                                                const uint32_t *s_adj)
+{
+    const uint32_t comp = link_flood(1u << first, upper, s_adj);
+    uint64_t codes = uint64_t(first);
+    int b0 = 1;
+    uint32_t left = upper & ~comp;
+    if (cls == 1) {
+        codes |= uint64_t(masked_top<MIN>(nb, left)) << 5;
+        return (2ull << 56) | codes;
+    }
+    while (left) {
+        const uint32_t c2 = link_flood(left & (~left + 1u), upper, s_adj);
+        left &= ~c2;
+        codes |= uint64_t(masked_top<MIN>(nb, c2)) << (5 * b0);
+        b0++;
+    }
+    return (uint64_t(b0) << 56) | codes;
+}
+
+// The 14 neighbour values of ring position (row r, column x) of plane buffers
+// D (z-1), C (z), U (z+1), in slot order.
+template <bool MIN>
+__device__ __forceinline__ void gather_nb(const float *Db, const float *Cb, const float *Ub, uint32_t rs, uint32_t r,
+                                          uint32_t x, float (&nb)[14], float &c)
+{
+    const float *d0 = Db + (r - 1) * rs + x, *d1 = Db + r * rs + x;
+    const float *c0 = Cb + (r - 1) * rs + x, *c1 = Cb + r * rs + x, *c2 = Cb + (r + 1) * rs + x;
+    const float *u1 = Ub + r * rs + x, *u2 = Ub + (r + 1) * rs + x;
+    nb[0] = zv<MIN>(d0[-1]);
+    nb[1] = zv<MIN>(d0[0]);
+    nb[2] = zv<MIN>(d1[-1]);
+    nb[3] = zv<MIN>(d1[0]);
+    nb[4] = zv<MIN>(c0[-1]);
+    nb[5] = zv<MIN>(c0[0]);
+    nb[6] = zv<MIN>(c1[-1]);
+    nb[7] = zv<MIN>(c1[1]);
+    nb[8] = zv<MIN>(c2[0]);
+    nb[9] = zv<MIN>(c2[1]);
+    nb[10] = zv<MIN>(u1[0]);
+    nb[11] = zv<MIN>(u1[1]);
+    nb[12] = zv<MIN>(u2[0]);
+    nb[13] = zv<MIN>(u2[1]);
+    c = zv<MIN>(c1[0]);
+}
+
+constexpr int kSaddleQueue = 1024;
+constexpr int kVx = 8;  // vertices per thread along axis 0
+// slots (see the order below) whose offset has a -x / +x / -y / +y / -z / +z component
+constexpr uint32_t kNegX = (1u << 0) | (1u << 2) | (1u << 4) | (1u << 6);
+constexpr uint32_t kPosX = (1u << 7) | (1u << 9) | (1u << 11) | (1u << 13);
+constexpr uint32_t kNegY = (1u << 0) | (1u << 1) | (1u << 4) | (1u << 5);
+constexpr uint32_t kPosY = (1u << 8) | (1u << 9) | (1u << 12) | (1u << 13);
+constexpr uint32_t kNegZ = (1u << 0) | (1u << 1) | (1u << 2) | (1u << 3);
+constexpr uint32_t kPosZ = (1u << 10) | (1u << 11) | (1u << 12) | (1u << 13);
+
+template <bool MIN>
+__global__ void __launch_bounds__(kZmThreads, 3)
+k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__restrict__ lut)
+{
+    extern __shared__ float4 zm_smem4[];
+    float *ring = reinterpret_cast<float *>(zm_smem4);
+    __shared__ uint32_t s_lut[1024];
+    __shared__ uint32_t s_adj[14];
+    __shared__ uint32_t s_off[14];
+    __shared__ uint32_t s_warp[kZmThreads / 32];
+    __shared__ unsigned s_cnt[4];
+    __shared__ uint2 s_queue[kSaddleQueue];  // (record index, x | ring row << 11 | upper << 18)
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint64_t g = blockIdx.x;
+    const int fi = find_field<true>(fields, nf, g);
+    const FieldDev &F = fields[fi];
+    const uint32_t item = uint32_t(g - F.item0);
+    ZmGeom G;
+    G.n0 = F.n[0];
+    G.n1 = F.n[1];
+    G.n2 = F.n[2];
+    G.ty = F.ty;
+    G.rstride = G.n0 + 8;
+    G.rb = zm_ring_floats(G.n0, G.ty);
+    const uint32_t yb = item % F.nyb, zci = item / F.nyb;
+    const uint32_t y0 = yb * G.ty;
+    const uint32_t brows = min(G.ty, G.n1 - y0);  // rows of this row block
+    const uint32_t ylo = y0 > 0 ? y0 - 1 : 0;
+    const uint32_t yhi = min(G.n1, y0 + G.ty + 1);
+    const int zs = int(zci * F.zc);
+    const int ze = int(min(G.n2, zci * F.zc + F.zc));
+    const bool vec = F.vec != 0;
+
+    for (int i = tid; i < 1024; i += kZmThreads) s_lut[i] = __ldg(lut + i);
+    if (tid < 14) {
+        s_adj[tid] = Nbr<3>::adj_mask(tid);
+        const uint32_t p = Nbr<3>::pat(tid);
+        const uint32_t mag = ((p & 1u) ? 1u : 0u) + ((p & 2u) ? G.n0 : 0u) + ((p & 4u) ? G.n0 * G.n1 : 0u);
+        s_off[tid] = Nbr<3>::neg(tid) ? 0u - mag : mag;
+    }
+    if (tid < 4) s_cnt[tid] = 0;
+    {
+        const float qnan = __int_as_float(0x7fc00000);
+        for (uint32_t i = tid; i < 4 * G.rb; i += kZmThreads) ring[i] = qnan;
+    }
+    __syncthreads();
+
+    zm_load_plane(F, G, ring + ((zs - 1) & 3) * G.rb, zs - 1, y0, ylo, yhi, vec);
+    zm_load_plane(F, G, ring + (zs & 3) * G.rb, zs, y0, ylo, yhi, vec);
+    zm_load_plane(F, G, ring + ((zs + 1) & 3) * G.rb, zs + 1, y0, ylo, yhi, vec);
+
+    // thread t owns vertices x .. x+7 of brick row r; threads are in (row, x)
+    // order, which is the brick's index order
+    const uint32_t txn = (G.n0 + kVx - 1) / kVx;
+    const bool active = uint32_t(tid) < txn * G.ty;
+    const uint32_t txt = uint32_t(tid) % txn, r = uint32_t(tid) / txn;
+    const uint32_t x = kVx * txt;
+    const uint32_t rs = G.rstride;
+    const uint32_t rr = r + 1;  // ring row of this thread's grid row
+    bool anynan = false;
+    uint32_t prev_brick = 0xffffffffu;
+
+    for (int z = zs; z < ze; z++) {
+        __syncthreads();  // A: previous step done (ring slot, queue, counters free)
+        if (tid == 0 && prev_brick != 0xffffffffu) {
+            F.bcnt[prev_brick] = make_uint4(s_cnt[0], s_cnt[1] - s_cnt[0], s_cnt[2], 0u);
+            s_cnt[0] = s_cnt[1] = s_cnt[2] = s_cnt[3] = 0;
+        }
+        zm_load_plane(F, G, ring + ((z + 2) & 3) * G.rb, z + 2, y0, ylo, yhi, vec);
+        cp_async_wait1();
+        __syncthreads();  // B: plane z+1 visible, counters reset
+
+        const float *Db = ring + ((z - 1) & 3) * G.rb + 8;
+        const float *Cb = ring + (z & 3) * G.rb + 8;
+        const float *Ub = ring + ((z + 1) & 3) * G.rb + 8;
+        const uint32_t brick = uint32_t(z) * F.nyb + yb;
+        const uint64_t slot0 = uint64_t(brick) * F.bcap;
+        const bool rowok = active && r < brows;
+        const uint32_t vrow = uint32_t((uint64_t(z) * G.n1 + y0 + r) * G.n0) + x;
+        uint32_t um[kVx];  // upper mask | gradient slot << 14 | class << 18
+        uint32_t crit = 0, nm = 0;
+        // in-bounds slots (NaN pads already fail every ordered comparison; the
+        // mask keeps the result independent of that)
+        const uint32_t gy = y0 + r;
+        uint32_t out = 0;
+        if (gy == 0) out |= kNegY;
+        if (gy + 1 >= G.n1) out |= kPosY;
+        if (z == 0) out |= kNegZ;
+        if (uint32_t(z) + 1 >= G.n2) out |= kPosZ;
+        const uint32_t inbm = ~out & 0x3fffu;
+        const uint32_t inb0 = x == 0 ? (inbm & ~kNegX) : inbm;
+        // ---- phase 1: gradient pointer, upper mask, saddle test
+        if (rowok) {
+            // row segments: C rows r-1..r+1 at x-1..x+8, D rows r-1..r at
+            // x-1..x+7, U rows r..r+1 at x..x+8 (ring rows are r-1+1 .. )
+            float C[3][kVx + 2], D[2][kVx + 1], U[2][kVx + 1];
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                const float *row = Cb + (rr - 1 + a) * rs + x;
+                C[a][0] = row[-1];
+                if (vec) {
+                    const float4 q0 = *reinterpret_cast<const float4 *>(row);
+                    const float4 q1 = *reinterpret_cast<const float4 *>(row + 4);
+                    C[a][1] = q0.x; C[a][2] = q0.y; C[a][3] = q0.z; C[a][4] = q0.w;
+                    C[a][5] = q1.x; C[a][6] = q1.y; C[a][7] = q1.z; C[a][8] = q1.w;
+                } else {
+#pragma unroll
+                    for (int b = 0; b < kVx; b++) C[a][1 + b] = row[b];
+                }
+                C[a][kVx + 1] = row[kVx];
+            }
+#pragma unroll
+            for (int a = 0; a < 2; a++) {
+                const float *drow = Db + (rr - 1 + a) * rs + x;
+                const float *urow = Ub + (rr + a) * rs + x;
+                D[a][0] = drow[-1];
+                if (vec) {
+                    const float4 q0 = *reinterpret_cast<const float4 *>(drow);
+                    const float4 q1 = *reinterpret_cast<const float4 *>(drow + 4);
+                    D[a][1] = q0.x; D[a][2] = q0.y; D[a][3] = q0.z; D[a][4] = q0.w;
+                    D[a][5] = q1.x; D[a][6] = q1.y; D[a][7] = q1.z; D[a][8] = q1.w;
+                    const float4 u0 = *reinterpret_cast<const float4 *>(urow);
+                    const float4 u1 = *reinterpret_cast<const float4 *>(urow + 4);
+                    U[a][0] = u0.x; U[a][1] = u0.y; U[a][2] = u0.z; U[a][3] = u0.w;
+                    U[a][4] = u1.x; U[a][5] = u1.y; U[a][6] = u1.z; U[a][7] = u1.w;
+                } else {
+#pragma unroll
+                    for (int b = 0; b < kVx; b++) {
+                        D[a][1 + b] = drow[b];
+                        U[a][b] = urow[b];
+                    }
+                }
+                U[a][kVx] = urow[kVx];
+            }
+            uint32_t asc[kVx];
+#pragma unroll
+            for (int i = 0; i < kVx; i++) {
+                const float cr = C[1][i + 1];
+                const float c = zv<MIN>(cr);
+                // slot order: (-1,-1,-1) (0,-1,-1) (-1,0,-1) (0,0,-1) (-1,-1,0) (0,-1,0)
+                // (-1,0,0) | (1,0,0) (0,1,0) (1,1,0) (0,0,1) (1,0,1) (0,1,1) (1,1,1)
+                const float nb[14] = {zv<MIN>(D[0][i]),     zv<MIN>(D[0][i + 1]), zv<MIN>(D[1][i]),
+                                      zv<MIN>(D[1][i + 1]), zv<MIN>(C[0][i]),     zv<MIN>(C[0][i + 1]),
+                                      zv<MIN>(C[1][i]),     zv<MIN>(C[1][i + 2]), zv<MIN>(C[2][i + 1]),
+                                      zv<MIN>(C[2][i + 2]), zv<MIN>(U[0][i]),     zv<MIN>(U[0][i + 1]),
+                                      zv<MIN>(U[1][i]),     zv<MIN>(U[1][i + 1])};
+                // upper: negative slots (smaller index) need a strictly higher
+                // value, positive slots a higher or equal one (maximum graph); the
+                // minimum graph swaps the two rules.  NaN (outside) is never upper.
+                uint32_t upper = 0;
+#pragma unroll
+                for (int k = 0; k < 14; k++) {
+                    const bool up = (k < 7) == MIN ? (nb[k] >= c) : (nb[k] > c);
+                    upper |= up ? (1u << k) : 0u;
+                }
+                // gradient: tournament in rank order, ties to the higher rank
+                // (maximum graph) or the lower rank (minimum graph)
+                uint32_t eq;
+                {
+                    float best = -__int_as_float(0x7f800000);
+                    int bk = 0;
+#pragma unroll
+                    for (int q = 0; q < 14; q++) {
+                        const int k = MIN ? 13 - q : q;
+                        const bool w = nb[k] >= best;
+                        best = w ? nb[k] : best;
+                        bk = w ? k : bk;
+                    }
+                    eq = 1u << bk;
+                }
+                uint32_t inb = i == 0 ? inb0 : inbm;
+                if (x + kVx >= G.n0 && x + i + 1 >= G.n0) inb &= ~kPosX;
+                upper &= inb;
+                eq &= inb;
+                const bool ok = x + i < G.n0;
+                const uint32_t v = vrow + i;
+                uint32_t a = v;
+                bool cv = false;
+                uint32_t cls = 0, slot = 0;
+                if (upper) {
+                    const uint32_t cand = eq & upper;
+                    slot = MIN ? uint32_t(__ffs(cand) - 1) : uint32_t(31 - __clz(cand));
+                    a = v + s_off[slot];
+                    cls = (s_lut[upper >> 4] >> ((upper & 15) << 1)) & 3u;
+                    cv = cls != 0;
+                } else {
+                    cv = true;
+                    nm += ok ? 1u : 0u;
+                }
+                asc[i] = a;
+                um[i] = upper | (slot << 14) | (cls << 18);
+                if (ok) {
+                    anynan |= (cr != cr);
+                    crit |= cv ? (1u << i) : 0u;
+                }
+            }
+            uint32_t *dst = F.lab + vrow;
+            if (vec) {
+                // n0 is a multiple of 4, so x+3 < n0; the second half may be past the row
+                *reinterpret_cast<uint4 *>(dst) = make_uint4(asc[0], asc[1], asc[2], asc[3]);
+                if (x + 7 < G.n0) *reinterpret_cast<uint4 *>(dst + 4) = make_uint4(asc[4], asc[5], asc[6], asc[7]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < kVx; i++)
+                    if (x + i < G.n0) dst[i] = asc[i];
+            }
+        }
+        // ---- order-preserving compaction: threads are in index order
+        const uint32_t cnt = __popc(crit);
+        uint32_t inc = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) s_warp[warp] = inc;
+        nm = __reduce_add_sync(0xffffffffu, nm);
+        if (lane == 0 && nm) atomicAdd(&s_cnt[0], nm);
+        __syncthreads();  // C: warp totals visible
+        uint32_t pos = inc - cnt;
+        for (int w = 0; w < warp; w++) pos += s_warp[w];
+        uint32_t np = 0;
+        if (crit) {
+#pragma unroll
+            for (int i = 0; i < kVx; i++)
+                if ((crit >> i) & 1u) {
+                    const uint64_t q = slot0 + pos;
+                    F.rec_sid[q] = vrow + i;
+                    F.rec_val[q] = Cb[rr * rs + x + i];
+                    const uint32_t upper = um[i] & 0x3fffu, sl = um[i] >> 14;
+                    if (upper == 0) {
+                        F.rec_info[q] = 0;
+                    } else {
+                        const uint32_t at = atomicAdd(&s_cnt[3], 1u);
+                        if (at < kSaddleQueue) {
+                            s_queue[at] = make_uint2(pos | (sl << 16), (x + i) | (rr << 11) | (upper << 18));
+                        } else {
+                            // queue full: resolve this saddle in place
+                            float nb[14], c;
+                            gather_nb<MIN>(Db, Cb, Ub, rs, rr, x + i, nb, c);
+                            const uint64_t inf = saddle_info<MIN>(nb, upper, int(sl & 15u), sl >> 4, s_adj);
+                            F.rec_info[q] = inf;
+                            np += uint32_t(inf >> 56);
+                        }
+                    }
+                    pos++;
+                }
+        }
+        __syncthreads();  // D: queue complete
+        // ---- phase 2: saddle components, one queued saddle per thread
+        const uint32_t nq = min(s_cnt[3], uint32_t(kSaddleQueue));
+        for (uint32_t e = tid; e < nq; e += kZmThreads) {
+            const uint2 w = s_queue[e];
+            const uint32_t xx = w.y & 0x7ffu, qr = (w.y >> 11) & 0x7fu, upper = w.y >> 18;
+            float nb[14], c;
+            gather_nb<MIN>(Db, Cb, Ub, rs, qr, xx, nb, c);
+            const uint64_t inf = saddle_info<MIN>(nb, upper, int((w.x >> 16) & 15u), (w.x >> 20) & 3u, s_adj);
+            F.rec_info[slot0 + (w.x & 0xffffu)] = inf;
+            np += uint32_t(inf >> 56);
+        }
+        np = __reduce_add_sync(0xffffffffu, np);
+        if (lane == 0 && np) atomicAdd(&s_cnt[2], np);
+        if (tid == 0) {
+            uint32_t tot = 0;
+            for (int w = 0; w < kZmThreads / 32; w++) tot += s_warp[w];
+            atomicAdd(&s_cnt[1], tot);  // critical vertices; maxima subtracted below
+        }
+        prev_brick = brick;
+    }
+    __syncthreads();
+    if (tid == 0 && prev_brick != 0xffffffffu)
+        F.bcnt[prev_brick] = make_uint4(s_cnt[0], s_cnt[1] - s_cnt[0], s_cnt[2], 0u);
+    if (anynan) atomicOr(F.err, kErrNaN);
+}
+
+size_t zm_smem_bytes(uint32_t n0, uint32_t ty) { return size_t(4) * zm_ring_floats(n0, ty) * sizeof(float); }
+
+cudaError_t launch_classify_zm(bool minimum, const FieldDev *fields, int nf, uint64_t total_items, size_t smem,
+                               const uint32_t *lut, cudaStream_t st)
+{
+    if (total_items == 0) return cudaSuccess;
+    auto kern = minimum ? k_classify_zm<true> : k_classify_zm<false>;
+    // allow the opt-in maximum of dynamic shared memory, once per device
+    static std::atomic<uint64_t> done_mask[2];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = 1ull << (dev & 63);
+    if (!(done_mask[minimum].load() & bit)) {
+        int optin = 0;
+        cudaFuncAttributes fa{};
+        if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+        if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
+        const int dyn = optin - int(fa.sharedSizeBytes);
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn)) != cudaSuccess) return e;
+        done_mask[minimum].fetch_or(bit);
+    }
+    // (the row layout bounds the ring at 4 x (4 rows x 1032 + 16) floats = 66 KB)
+    kern<<<dim3(unsigned(total_items)), kZmThreads, smem, st>>>(fields, nf, lut);
+    return cudaGetLastError();
+}
+
+}  // namespace eg

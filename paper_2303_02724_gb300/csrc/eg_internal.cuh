@@ -17,10 +17,17 @@
 //   opposite sign  : p and q disjoint.
 //
 // Order (simulation of simplicity, Sec. 3.3): w is higher than v iff
-// f[w] > f[v], or f[w] == f[v] and w > v.  Values become monotone uint32 keys
-// (-0 folded onto +0); inside one neighbourhood the index tie-break is the slot
-// rank, so "higher" is a comparison of the 64-bit composite (key << 8 | rank).
-// The minimum graph reverses the order: key -> ~key and rank -> 2H - rank.
+// f[w] > f[v], or f[w] == f[v] and w > v.  Inside one neighbourhood the index
+// tie-break is the slot rank.  The minimum graph reverses the order.
+//
+// A 2D field is processed as a 3D field with n2 = 1: the 3D neighbourhood
+// restricted to the plane is exactly the 2D one (patterns without the z bit),
+// with the same link edges and the same index order.
+//
+// Bricks: every kernel after classification works on bricks, contiguous
+// ranges of linear vertex ids, in index order.  Flat layout: 1024 ids per
+// brick.  Row layout (2D/3D, axis-0 extent <= 1024): `ty` whole rows of one
+// plane per brick, so brick b = plane b / nyb, row block b % nyb.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -28,7 +35,9 @@
 namespace eg {
 
 constexpr int kMaxDim = 4;
-constexpr int kBrick = 1024;  // vertices per brick: a contiguous range of linear ids
+constexpr int kFlatBrick = 1024;
+constexpr int kMaxBrick = 4096;  // largest brick of any layout (slot capacity bound)
+constexpr int kMaxComp = 10;     // max upper-link components (4D link graph independence number)
 
 // device status word bits (reported by eg_get_graph)
 enum : uint32_t {
@@ -43,35 +52,58 @@ enum : uint32_t { kFlagMinimum = 1u, kFlagNoLabels = 2u };
 
 // One field as the kernels see it.  Plain pointers; filled on the host.
 struct FieldDev {
-    const float *f;        // [N] input values
-    uint32_t *lab;         // [N] gradient pointer, then the label (maximum reached)
-    uint32_t *rec_sid;     // [nbricks * kBrick] critical-vertex records, per brick slot
-    uint64_t *rec_info;    // [nbricks * kBrick] beta0+ (bits 56..59) | rep slots (5 bits each)
-    uint4 *bcnt;           // [nbricks] maxima, saddles, paths per brick
-    uint32_t *maxima;      // [M]
-    float *max_val;        // [M]
-    uint32_t *saddles;     // [S]
-    uint8_t *sad_b0;       // [S]
-    float *sad_val;        // [S]
-    uint64_t *row_ptr;     // [S+1]
-    uint32_t *col;         // [A] (capacity P)
+    const float *f;          // [N] input values
+    uint32_t *lab;           // [N] gradient pointer, then the label (maximum reached)
+    // classification records: one slot of bcap entries per brick, index order
+    uint32_t *rec_sid;       // vertex id
+    uint64_t *rec_info;      // beta0+ (bits 56..59) | rep slots (5 bits each)
+    float *rec_val;          // f at the vertex
+    uint4 *bcnt;             // [nbricks] maxima, saddles, paths in the brick
+    uint4 *boff;             // [nbricks] exclusive offsets: maxima, saddles, paths (lo, hi)
+    uint32_t *acnt;          // [nbricks] unique arcs in the brick
+    uint64_t *aoff;          // [nbricks] exclusive offsets of unique arcs
+    uint32_t *ends;          // [P] sorted unique arc ends, at each saddle's path offset
+    uint8_t *ucnt;           // [S] unique arc count per saddle
+    // outputs
+    uint32_t *maxima;        // [M]
+    float *max_val;          // [M]
+    uint32_t *saddles;       // [S]
+    uint8_t *sad_b0;         // [S]
+    float *sad_val;          // [S]
+    uint64_t *row_ptr;       // [S+1]
+    uint32_t *col;           // [A]
     unsigned long long *totals;  // [4] M, S, P, A
-    uint32_t *err;         // device status word
-    uint32_t n[kMaxDim];   // extents (1 beyond d)
-    uint32_t s[kMaxDim];   // strides
-    uint32_t N;            // vertex count (< 2^32)
-    uint32_t nbricks;      // ceil(N / kBrick)
-    uint64_t brick0;       // first global brick id of this field in its launch
-    int32_t d;
+    uint32_t *err;           // device status word
+    uint32_t n[kMaxDim];     // extents (1 beyond the kernel dimension)
+    uint32_t s[kMaxDim];     // strides
+    uint32_t N;              // vertex count (< 2^32)
+    uint32_t nbricks;
+    uint32_t bcap;           // record slot capacity per brick (= brick size)
+    uint32_t ty;             // rows per brick (0: flat layout)
+    uint32_t nyb;            // row blocks per plane (row layout)
+    uint32_t zc;             // planes per classification work item (row layout)
+    uint32_t nzc;            // work items along the slowest axis (row layout)
+    uint32_t vec;            // axis-0 extent is a multiple of 4 and f is 16-byte aligned
+    uint64_t brick0;         // first global brick id of this field in its launch
+    uint64_t item0;          // first classification work item of this field in its launch
+    uint64_t stile0;         // first scan tile of this field (all fields of a call)
+    int32_t kd;              // kernel dimension (2D fields run as 3D)
     uint32_t flags;
 };
 
-// Monotone key of a float: a < b (IEEE, non-NaN) <=> key(a) < key(b); -0 == +0.
-__device__ __forceinline__ uint32_t order_key(float x)
+__host__ __device__ __forceinline__ void brick_range(const FieldDev &F, uint32_t b, uint64_t &v0, uint32_t &len)
 {
-    uint32_t u = __float_as_uint(x);
-    u = (u == 0x80000000u) ? 0u : u;
-    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    if (F.ty == 0) {
+        v0 = uint64_t(b) * kFlatBrick;
+        const uint64_t rem = uint64_t(F.N) - v0;
+        len = rem < kFlatBrick ? uint32_t(rem) : uint32_t(kFlatBrick);
+    } else {
+        const uint32_t p = b / F.nyb, yb = b - p * F.nyb;
+        const uint32_t y0 = yb * F.ty;
+        const uint32_t rows = (F.n[1] - y0) < F.ty ? (F.n[1] - y0) : F.ty;
+        v0 = (uint64_t(p) * F.n[1] + y0) * F.n[0];
+        len = rows * F.n[0];
+    }
 }
 
 template <int D>
@@ -97,7 +129,7 @@ struct Nbr {
 };
 
 // Linear offset (magnitude) of pattern p under strides s (runtime p).
-__device__ __forceinline__ uint32_t pattern_offset(uint32_t p, const uint32_t *s)
+__host__ __device__ __forceinline__ uint32_t pattern_offset(uint32_t p, const uint32_t *s)
 {
     uint32_t o = 0;
 #pragma unroll
@@ -114,6 +146,21 @@ __device__ __forceinline__ uint32_t slot_vertex(uint32_t v, int k, const uint32_
     uint32_t p = k < NB::H ? uint32_t(NB::H - k) : uint32_t(k - NB::H + 1);
     uint32_t o = pattern_offset(p, s);
     return k < NB::H ? v - o : v + o;
+}
+
+// Connected component of `seed` inside `upper` over the link edges (bitmask
+// flood fill; each member is expanded once).
+__device__ __forceinline__ uint32_t link_flood(uint32_t seed, uint32_t upper, const uint32_t *s_adj)
+{
+    uint32_t comp = seed, frontier = seed;
+    while (frontier) {
+        const int k = __ffs(frontier) - 1;
+        frontier &= frontier - 1;
+        const uint32_t nb = s_adj[k] & upper & ~comp;
+        comp |= nb;
+        frontier |= nb;
+    }
+    return comp;
 }
 
 // ---------------------------------------------------------------------------
@@ -154,9 +201,9 @@ __device__ __forceinline__ uint64_t warp_lookback(uint64_t *st, uint64_t item, u
     uint32_t spins = 0;
     unsigned ns = 8;
     while (true) {
-        int64_t j = base - lane;
-        uint64_t w = (j >= int64_t(first)) ? ld_volatile_u64(st + j) : kLbPre;
-        bool empty = (w >> 62) == 0;
+        const int64_t j = base - lane;
+        const uint64_t w = (j >= int64_t(first)) ? ld_volatile_u64(st + j) : kLbPre;
+        const bool empty = (w >> 62) == 0;
         if (__any_sync(0xffffffffu, empty)) {
             if (++spins > kSpinLimit) {
                 if (lane == 0) atomicOr(err, kErrTimeout);
@@ -166,8 +213,8 @@ __device__ __forceinline__ uint64_t warp_lookback(uint64_t *st, uint64_t item, u
             ns = ns < 256 ? ns * 2 : 256;
             continue;
         }
-        unsigned pmask = __ballot_sync(0xffffffffu, (w >> 62) == 2);
-        int stop = pmask ? (__ffs(pmask) - 1) : 31;
+        const unsigned pmask = __ballot_sync(0xffffffffu, (w >> 62) == 2);
+        const int stop = pmask ? (__ffs(pmask) - 1) : 31;
         uint64_t val = (lane <= stop) ? (w & kLbVal) : 0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
@@ -179,13 +226,16 @@ __device__ __forceinline__ uint64_t warp_lookback(uint64_t *st, uint64_t item, u
     return excl;
 }
 
-// Locate the field that owns global brick g (fields sorted by brick0).
+// Locate the field that owns global item g, given each field's first item
+// (ascending).  `key` selects brick0 or item0.
+template <bool kItems>
 __device__ __forceinline__ int find_field(const FieldDev *fields, int nf, uint64_t g)
 {
     int lo = 0, hi = nf - 1;
     while (lo < hi) {
-        int mid = (lo + hi + 1) >> 1;
-        if (fields[mid].brick0 <= g) lo = mid;
+        const int mid = (lo + hi + 1) >> 1;
+        const uint64_t first = kItems ? fields[mid].item0 : fields[mid].brick0;
+        if (first <= g) lo = mid;
         else hi = mid - 1;
     }
     return lo;
@@ -200,24 +250,24 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t *scratc
     uint32_t inc = x;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+        const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
         if (lane >= o) inc += y;
     }
     if (lane == 31) scratch[warp] = inc;
     __syncthreads();
     if (warp == 0) {
-        uint32_t w = lane < nw ? scratch[lane] : 0;
+        const uint32_t w = lane < nw ? scratch[lane] : 0;
         uint32_t wi = w;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
+            const uint32_t y = __shfl_up_sync(0xffffffffu, wi, o);
             if (lane >= o) wi += y;
         }
         if (lane < nw) scratch[lane] = wi - w;
         if (lane == nw - 1) scratch[32] = wi;
     }
     __syncthreads();
-    uint32_t r = scratch[warp] + inc - x;
+    const uint32_t r = scratch[warp] + inc - x;
     *total = scratch[32];
     __syncthreads();
     return r;

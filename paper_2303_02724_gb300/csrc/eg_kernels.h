@@ -6,17 +6,27 @@
 
 namespace eg {
 
-// Steps (a)+(c): gradient pointers into lab, critical-vertex records, counts.
-cudaError_t launch_classify_d(int d, const FieldDev *fields, int nf, uint64_t total_bricks,
-                              cudaStream_t st);
+// Steps (a)+(c), general kernel: one CTA per flat brick (any d, any extents).
+// fields: the slice of descriptors using this kernel dimension; the grid
+// covers their bricks, global ids from fields[0].brick0.
+cudaError_t launch_classify_flat(int kd, const FieldDev *fields, int nf, uint64_t bricks, cudaStream_t st);
 
-// Step (b): labels = fixed points of the gradient pointers.
+// Steps (a)+(c), plane-marching kernel for 2D/3D fields with rows of at most
+// 1024 vertices.  lut: 2^14-bit saddle table (eg_saddle_lut3).
+size_t zm_smem_bytes(uint32_t n0, uint32_t ty);
+cudaError_t launch_classify_zm(bool minimum, const FieldDev *fields, int nf, uint64_t total_items, size_t smem,
+                               const uint32_t *lut, cudaStream_t st);
+
+// Scan A (arcs = false) / scan B (arcs = true) over all bricks of all fields.
+uint64_t scan_tiles(uint32_t nbricks);
+size_t scan_workspace_bytes(uint64_t total_tiles);
+cudaError_t launch_scan(bool arcs, const FieldDev *fields, int nf, uint64_t total_tiles, void *ws, cudaStream_t st);
+
+// Step (b): labels = fixed points of the gradient pointers (all fields).
 cudaError_t launch_resolve(const FieldDev *fields, int nf, uint64_t total_bricks, cudaStream_t st);
 
-// Steps (d)+(e): arcs and the sorted CSR graph.  ws: zeroed workspace of
-// emit_workspace_bytes(total_bricks) bytes.
-size_t emit_workspace_bytes(uint64_t total_bricks);
-cudaError_t launch_emit_d(int d, const FieldDev *fields, int nf, uint64_t total_bricks, void *ws,
-                          int sm_count, cudaStream_t st);
+// Steps (d)+(e): nodes and arc ends per brick (one kernel dimension), then CSR.
+cudaError_t launch_nodes_d(int kd, const FieldDev *fields, int nf, uint64_t base, uint64_t bricks, cudaStream_t st);
+cudaError_t launch_csr(const FieldDev *fields, int nf, uint64_t total_bricks, cudaStream_t st);
 
 }  // namespace eg

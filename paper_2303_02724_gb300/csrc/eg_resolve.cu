@@ -2,9 +2,10 @@
 // reaches (Algorithm 2's inner loop, run for all vertices at once).
 //
 // lab[] holds the gradient pointers on entry and the labels on exit.  Each
-// thread follows the pointers from its vertex to a fixed point (a maximum,
-// lab[m] == m) and stores it.  Threads write only their own vertex; a reader
-// that meets an already-finished vertex sees its maximum instead of its
+// thread follows the pointers from its vertices to a fixed point (a maximum,
+// lab[m] == m) and stores it; kIlp walks per thread advance in lock-step so
+// their dependent loads overlap.  Threads write only their own vertices; a
+// reader that meets an already-finished vertex sees its maximum instead of its
 // gradient pointer, which lies on the same path, so the races are benign and
 // later walks get shorter.  A walk longer than N steps is impossible (the
 // order strictly increases along a path); the bound is a guard that reports
@@ -15,32 +16,52 @@
 namespace eg {
 
 constexpr int kResolveThreads = 256;
+constexpr int kIlp = 4;
 
 __global__ void __launch_bounds__(kResolveThreads)
 k_resolve_chase(const FieldDev *__restrict__ fields, int nf)
 {
     const uint64_t g = blockIdx.x;
-    const int fi = find_field(fields, nf, g);
+    const int fi = find_field<false>(fields, nf, g);
     const FieldDev &F = fields[fi];
-    const uint64_t v0 = (g - F.brick0) * kBrick;
+    uint64_t v0;
+    uint32_t len;
+    brick_range(F, uint32_t(g - F.brick0), v0, len);
     uint32_t *lab = F.lab;
-    for (int i = threadIdx.x; i < kBrick; i += kResolveThreads) {
-        const uint64_t v64 = v0 + i;
-        if (v64 >= F.N) break;
-        const uint32_t v = uint32_t(v64);
-        uint32_t u = lab[v];
-        if (u == v) continue;
-        uint64_t steps = 0;
-        while (true) {
-            uint32_t w = lab[u];
-            if (w == u) break;
-            u = w;
+    for (uint32_t base = threadIdx.x; base < len; base += kIlp * kResolveThreads) {
+        uint32_t v[kIlp], u[kIlp];
+        uint32_t live = 0;
+#pragma unroll
+        for (int q = 0; q < kIlp; q++) {
+            const uint32_t i = base + q * kResolveThreads;
+            v[q] = uint32_t(v0) + i;
+            u[q] = v[q];
+            if (i < len) {
+                u[q] = lab[v[q]];
+                if (u[q] != v[q]) live |= 1u << q;
+            }
+        }
+        uint32_t moved = 0, steps = 0;
+        while (live) {
+#pragma unroll
+            for (int q = 0; q < kIlp; q++)
+                if ((live >> q) & 1u) {
+                    const uint32_t w = lab[u[q]];
+                    if (w == u[q]) {
+                        live &= ~(1u << q);
+                    } else {
+                        u[q] = w;
+                        moved |= 1u << q;
+                    }
+                }
             if (++steps > F.N) {
                 atomicOr(F.err, kErrNotConverged);
                 break;
             }
         }
-        lab[v] = u;
+#pragma unroll
+        for (int q = 0; q < kIlp; q++)
+            if ((moved >> q) & 1u) lab[v[q]] = u[q];
     }
 }
 

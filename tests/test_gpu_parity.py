@@ -88,6 +88,29 @@ def test_multi_brick(handle, case):
     assert_same(run_gpu(handle, f.values), oracle.compute(f.values))
 
 
+@pytest.mark.parametrize("case", ["flat_2d_wide", "flat_3d_wide", "long_1d", "tall_2d", "thin_3d"])
+def test_layouts(handle, case):
+    """Rows longer than 1024 vertices take the flat-brick classifier; others the
+    plane-marching one, including degenerate row/plane counts."""
+    f = {
+        "flat_2d_wide": lambda: F.config_2d_256(side=1500),
+        "flat_3d_wide": lambda: F.white_noise((1100, 5, 3), 4),
+        "long_1d": lambda: F.white_noise((5000,), 6),
+        "tall_2d": lambda: F.white_noise((3, 2000), 7),
+        "thin_3d": lambda: F.integer_ties((7, 1, 40), 2, 3),
+    }[case]()
+    assert_same(run_gpu(handle, f.values), oracle.compute(f.values))
+
+
+def test_unaligned_field_pointer(handle):
+    f = F.config_3d_256(side=36)
+    flat = torch.from_numpy(np.concatenate([[0.0], f.values.reshape(-1)]).astype(np.float32)).cuda()
+    t = flat[1:].view(f.values.shape)
+    assert t.data_ptr() % 16 != 0
+    g = handle.graph_of(t)
+    assert_same(g, oracle.compute(f.values))
+
+
 def test_config_2d_256_full(handle):
     f = F.config_2d_256()
     assert_same(run_gpu(handle, f.values), oracle.compute(f.values))
@@ -95,6 +118,16 @@ def test_config_2d_256_full(handle):
 
 def test_special_values(handle):
     v = np.array([[0.0, -0.0, np.inf, -np.inf, 1e-42, -1e-42, 3.4e38, 0.0]], np.float32)
+    assert_same(run_gpu(handle, v), oracle.compute(v))
+
+
+@pytest.mark.parametrize("shape", [(40, 30), (20, 17, 13), (6, 5, 4, 3)])
+def test_infinities_and_signed_zeros(handle, shape):
+    """Adjacent equal infinities and mixed -0/+0 everywhere: the comparisons
+    must treat them as ties broken by index, exactly like the oracle."""
+    rng = np.random.default_rng(11)
+    pool = np.array([-np.inf, -1.0, -0.0, 0.0, 1.0, np.inf], np.float32)
+    v = pool[rng.integers(0, len(pool), size=shape[::-1])]
     assert_same(run_gpu(handle, v), oracle.compute(v))
 
 
