@@ -179,6 +179,34 @@ EG_API eg_status eg_mem_info(eg_handle h, uint64_t *free_bytes, uint64_t *total_
 EG_API eg_status eg_set_timing(eg_handle h, int enable);
 EG_API eg_status eg_step_times(eg_handle h, eg_result_id id, float ms[4]);
 
+/* Largest field (in vertices) that eg_labels_static accepts. */
+#define EG_STATIC_MAX_VERTICES (1u << 20)
+
+/* Per-vertex labels (the maximum each vertex's gradient path reaches, or the
+ * minimum with EG_FLAG_MINIMUM_GRAPH in flags) WITHOUT allocating any memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot let a library call cudaMalloc or cudaFree -- for example when another
+ * allocator owns all device memory, under a fixed memory budget, or in a
+ * latency-critical loop where those calls may synchronise the whole device.
+ *
+ * field: device float32[N]; labels: device uint32[N] (written); d in 1..4;
+ * extents as for eg_compute, with N <= EG_STATIC_MAX_VERTICES.  Larger fields
+ * are rejected with EG_ERR_ARG before any work is enqueued.
+ * Work runs on `stream`; the call returns after it has finished (it reads back
+ * a status word), so labels are ready on return.
+ * Scratch: a fixed array compiled into the library (about 16 bytes per vertex
+ * of EG_STATIC_MAX_VERTICES, ~17 MB) that every GPU loading the library holds
+ * until the process exits.  Its device address is looked up on the FIRST call
+ * made on each device, with that device current; make that first call before
+ * any stream capture begins.  All calls on a device share the one array, and
+ * it keeps the last call's contents (the call clears what must start at
+ * zero): calls that overlap on the GPU -- from several host threads or on
+ * several streams -- race on it and must be serialised by the caller.
+ * Needs no handle.  Errors: EG_ERR_ARG, EG_ERR_NAN, EG_ERR_NOT_CONVERGED,
+ * EG_ERR_CUDA. */
+EG_API eg_status eg_labels_static(const float *field, int d, const int64_t *extents, uint32_t flags,
+                                  uint32_t *labels, void *stream);
+
 /* Kernel launches issued by the handle since its creation (for accounting). */
 EG_API uint64_t eg_launch_count(eg_handle h);
 

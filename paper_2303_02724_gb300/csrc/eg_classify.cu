@@ -113,9 +113,9 @@ __device__ __forceinline__ uint32_t classify_vertex(const FieldDev &F, const uin
     return asc;
 }
 
+// Classification of brick b of field F (one CTA, kClassifyThreads threads).
 template <int D>
-__global__ void __launch_bounds__(kClassifyThreads)
-k_classify(const FieldDev *__restrict__ fields, int nf)
+__device__ __forceinline__ void classify_brick(const FieldDev &F, uint32_t b)
 {
     using NB = Nbr<D>;
     __shared__ uint32_t s_adj[NB::K];
@@ -124,10 +124,6 @@ k_classify(const FieldDev *__restrict__ fields, int nf)
     const int tid = threadIdx.x;
     if (tid < NB::K) s_adj[tid] = NB::adj_mask(tid);
     if (tid < 3) s_cnt[tid] = 0;
-    const uint64_t g = fields[0].brick0 + blockIdx.x;
-    const int fi = find_field<false>(fields, nf, g);
-    const FieldDev &F = fields[fi];
-    const uint32_t b = uint32_t(g - F.brick0);
     uint32_t s[kMaxDim];
 #pragma unroll
     for (int i = 0; i < kMaxDim; i++) s[i] = F.s[i];
@@ -182,10 +178,38 @@ k_classify(const FieldDev *__restrict__ fields, int nf)
 }
 
 template <int D>
+__global__ void __launch_bounds__(kClassifyThreads)
+k_classify(const FieldDev *__restrict__ fields, int nf)
+{
+    const uint64_t g = fields[0].brick0 + blockIdx.x;
+    const int fi = find_field<false>(fields, nf, g);
+    const FieldDev &F = fields[fi];
+    classify_brick<D>(F, uint32_t(g - F.brick0));
+}
+
+// Single-field variant with the descriptor passed by value (no descriptor
+// table in device memory); used by the allocation-free entry point.
+template <int D>
+__global__ void __launch_bounds__(kClassifyThreads)
+k_classify_one(const FieldDev F)
+{
+    classify_brick<D>(F, blockIdx.x);
+}
+
+template <int D>
 cudaError_t launch_classify(const FieldDev *fields, int nf, uint64_t bricks, cudaStream_t st)
 {
     if (bricks == 0) return cudaSuccess;
     k_classify<D><<<dim3(unsigned(bricks)), kClassifyThreads, 0, st>>>(fields, nf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_classify_one(int kd, const FieldDev &F, cudaStream_t st)
+{
+    if (F.nbricks == 0) return cudaSuccess;
+    if (kd == 4) k_classify_one<4><<<dim3(F.nbricks), kClassifyThreads, 0, st>>>(F);
+    else if (kd == 3) k_classify_one<3><<<dim3(F.nbricks), kClassifyThreads, 0, st>>>(F);
+    else return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

@@ -22,6 +22,11 @@ uint64_t scan_tiles(uint32_t nbricks);
 size_t scan_workspace_bytes(uint64_t total_tiles);
 cudaError_t launch_scan(bool arcs, const FieldDev *fields, int nf, uint64_t total_tiles, void *ws, cudaStream_t st);
 
+// Single-field, descriptor-by-value variants of the flat classifier and of the
+// resolver (flat brick layout).
+cudaError_t launch_classify_one(int kd, const FieldDev &F, cudaStream_t st);
+cudaError_t launch_resolve_one(const FieldDev &F, cudaStream_t st);
+
 // Step (b): labels = fixed points of the gradient pointers (all fields).
 cudaError_t launch_resolve(const FieldDev *fields, int nf, uint64_t total_bricks, cudaStream_t st);
 

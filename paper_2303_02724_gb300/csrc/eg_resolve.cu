@@ -18,15 +18,12 @@ namespace eg {
 constexpr int kResolveThreads = 256;
 constexpr int kIlp = 4;
 
-__global__ void __launch_bounds__(kResolveThreads)
-k_resolve_chase(const FieldDev *__restrict__ fields, int nf)
+// Resolve the labels of brick b of field F.
+__device__ __forceinline__ void resolve_brick(const FieldDev &F, uint32_t b)
 {
-    const uint64_t g = blockIdx.x;
-    const int fi = find_field<false>(fields, nf, g);
-    const FieldDev &F = fields[fi];
     uint64_t v0;
     uint32_t len;
-    brick_range(F, uint32_t(g - F.brick0), v0, len);
+    brick_range(F, b, v0, len);
     uint32_t *lab = F.lab;
     for (uint32_t base = threadIdx.x; base < len; base += kIlp * kResolveThreads) {
         uint32_t v[kIlp], u[kIlp];
@@ -63,6 +60,29 @@ k_resolve_chase(const FieldDev *__restrict__ fields, int nf)
         for (int q = 0; q < kIlp; q++)
             if ((moved >> q) & 1u) lab[v[q]] = u[q];
     }
+}
+
+__global__ void __launch_bounds__(kResolveThreads)
+k_resolve_chase(const FieldDev *__restrict__ fields, int nf)
+{
+    const uint64_t g = blockIdx.x;
+    const int fi = find_field<false>(fields, nf, g);
+    const FieldDev &F = fields[fi];
+    resolve_brick(F, uint32_t(g - F.brick0));
+}
+
+// Single-field variant with the descriptor passed by value.
+__global__ void __launch_bounds__(kResolveThreads)
+k_resolve_one(const FieldDev F)
+{
+    resolve_brick(F, blockIdx.x);
+}
+
+cudaError_t launch_resolve_one(const FieldDev &F, cudaStream_t st)
+{
+    if (F.nbricks == 0) return cudaSuccess;
+    k_resolve_one<<<dim3(F.nbricks), kResolveThreads, 0, st>>>(F);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_resolve(const FieldDev *fields, int nf, uint64_t total_bricks, cudaStream_t st)

@@ -75,7 +75,10 @@ SIGNATURES = {
     "eg_launch_count": (ctypes.c_uint64, [_P]),
     "eg_debug_fail_alloc": (ctypes.c_int, [_P, ctypes.c_int]),
     "eg_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "eg_labels_static": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_uint32, _P, _P]),
 }
+
+STATIC_MAX_VERTICES = 1 << 20
 
 
 def load(path: str = LIB_PATH):
@@ -281,6 +284,20 @@ class Handle:
             return self.get_graph(rid, labels)
         finally:
             self.release(rid)
+
+
+def labels_static(field, labels, minimum: bool = False, stream=None):
+    """Allocation-free labels (eg_labels_static): field and labels are CUDA
+    tensors (float32 / int32-sized, same shape); returns the status code."""
+    lib = load()
+    if not field.is_cuda or not labels.is_cuda or field.dtype.itemsize != 4 or labels.dtype.itemsize != 4:
+        raise ValueError("field and labels must be 4-byte CUDA tensors")
+    ext = _extents_of(field.shape)
+    e = (ctypes.c_int64 * max(1, len(ext)))(*ext)
+    return int(lib.eg_labels_static(ctypes.c_void_p(field.data_ptr()), len(ext), e,
+                                    EG_FLAG_MINIMUM_GRAPH if minimum else 0,
+                                    ctypes.c_void_p(labels.data_ptr()),
+                                    ctypes.c_void_p(_stream_ptr(stream))))
 
 
 def workspace_bytes(extents) -> int:
