@@ -61,7 +61,7 @@ def _load():
         lib.eo_compute.restype = ctypes.c_int
         lib.eo_counts.argtypes = [P, P]
         lib.eo_counts.restype = None
-        lib.eo_copy.argtypes = [P] * 11
+        lib.eo_copy.argtypes = [P] * 12
         lib.eo_copy.restype = None
         lib.eo_free.argtypes = [P]
         lib.eo_free.restype = None
@@ -87,6 +87,12 @@ class OracleGraph:
     row_ptr: np.ndarray  # uint64[S+1]
     col: np.ndarray      # uint32[A]
     n_paths: int         # sum of beta0+ over saddles
+    reps: np.ndarray = None  # uint32[P] UpperLinkRep per saddle (ascending ids, saddles in order)
+
+    def saddle_reps(self, i):
+        """Upper-link representatives of saddle number i."""
+        off = int(self.sad_b0[:i].sum())
+        return self.reps[off:off + int(self.sad_b0[i])]
 
     def arcs(self):
         """Set of (saddle, maximum) pairs."""
@@ -127,11 +133,11 @@ def compute(field: np.ndarray, extents=None, naive: bool = False,
             max_val=np.empty(nm, np.float32), saddles=np.empty(ns, np.uint32),
             sad_b0=np.empty(ns, np.uint8), sad_val=np.empty(ns, np.float32),
             row_ptr=np.empty(ns + 1, np.uint64), col=np.empty(na, np.uint32),
-            n_paths=npaths)
+            n_paths=npaths, reps=np.empty(npaths, np.uint32))
         lib.eo_copy(h, g.asc.ctypes.data, g.label.ctypes.data, g.beta0p.ctypes.data,
                     g.maxima.ctypes.data, g.max_val.ctypes.data, g.saddles.ctypes.data,
                     g.sad_b0.ctypes.data, g.sad_val.ctypes.data, g.row_ptr.ctypes.data,
-                    g.col.ctypes.data)
+                    g.col.ctypes.data, g.reps.ctypes.data)
         return g
     finally:
         lib.eo_free(h)

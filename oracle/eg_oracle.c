@@ -32,7 +32,7 @@
  *               inner loop), i.e. the descending manifold of that maximum
  *               (Sec. 2).
  *   reps        UpperLinkRep: the highest vertex of each upper-link component
- *               (Sec. 3.4).
+ *               (Sec. 3.4), reported per saddle in ascending id order.
  *   arcs        (s, label(rep)) for every saddle s and every component,
  *               duplicates removed, sorted by (s, m) (Sec. 2: arc (s,m) iff s
  *               bounds the descending manifold of m).
@@ -65,6 +65,8 @@ typedef struct eo_result {
     float *sad_val;    /* [n_sad] */
     uint64_t *row_ptr; /* [n_sad+1] */
     uint32_t *col;     /* [n_arcs] */
+    uint32_t *reps;    /* [n_paths] UpperLinkRep of every saddle, saddles in order,
+                          each saddle's representatives in ascending id order */
 } eo_result;
 
 /* ---- order (simulated perturbation, Sec. 3.3) ----------------------------- */
@@ -215,7 +217,7 @@ void eo_free(eo_result *r)
     free(r->asc); free(r->label); free(r->beta0p);
     free(r->maxima); free(r->max_val);
     free(r->saddles); free(r->sad_b0); free(r->sad_val);
-    free(r->row_ptr); free(r->col);
+    free(r->row_ptr); free(r->col); free(r->reps);
     free(r);
 }
 
@@ -298,10 +300,11 @@ int eo_compute(const float *f, int d, const int64_t *ext, int naive, int reverse
     r->sad_val = (float *)malloc((n_sad ? n_sad : 1) * sizeof(float));
     r->row_ptr = (uint64_t *)malloc((n_sad + 1) * sizeof(uint64_t));
     r->col = (uint32_t *)malloc((n_paths ? n_paths : 1) * sizeof(uint32_t));
+    r->reps = (uint32_t *)malloc((n_paths ? n_paths : 1) * sizeof(uint32_t));
     if (!r->maxima || !r->max_val || !r->saddles || !r->sad_b0 || !r->sad_val ||
-        !r->row_ptr || !r->col) { eo_free(r); return EO_ERR_OOM; }
+        !r->row_ptr || !r->col || !r->reps) { eo_free(r); return EO_ERR_OOM; }
 
-    int64_t im = 0, is = 0, ia = 0;
+    int64_t im = 0, is = 0, ia = 0, ip = 0;
     r->row_ptr[0] = 0;
     for (uint64_t v = 0; v < n; v++) {
         if (r->beta0p[v] == 0) {
@@ -311,6 +314,8 @@ int eo_compute(const float *f, int d, const int64_t *ext, int naive, int reverse
         } else if (r->beta0p[v] >= 2) {
             uint32_t g;
             int b = eo_classify_vertex(f, d, ext, nnb, off, (uint32_t)v, reverse, reps, &g);
+            qsort(reps, (size_t)b, sizeof(uint32_t), eo_cmp_u32);
+            for (int c = 0; c < b; c++) r->reps[ip++] = reps[c];
             uint32_t ends[EO_MAXNB];
             for (int c = 0; c < b; c++) ends[c] = r->label[reps[c]];
             qsort(ends, (size_t)b, sizeof(uint32_t), eo_cmp_u32);
@@ -336,7 +341,7 @@ void eo_counts(const eo_result *r, int64_t *c5)
 
 void eo_copy(const eo_result *r, uint32_t *asc, uint32_t *label, uint8_t *beta0p,
              uint32_t *maxima, float *max_val, uint32_t *saddles, uint8_t *sad_b0,
-             float *sad_val, uint64_t *row_ptr, uint32_t *col)
+             float *sad_val, uint64_t *row_ptr, uint32_t *col, uint32_t *reps)
 {
     size_t n = (size_t)r->n;
     if (asc) memcpy(asc, r->asc, n * sizeof(uint32_t));
@@ -349,6 +354,7 @@ void eo_copy(const eo_result *r, uint32_t *asc, uint32_t *label, uint8_t *beta0p
     if (sad_val) memcpy(sad_val, r->sad_val, (size_t)r->n_sad * sizeof(float));
     if (row_ptr) memcpy(row_ptr, r->row_ptr, (size_t)(r->n_sad + 1) * sizeof(uint64_t));
     if (col) memcpy(col, r->col, (size_t)r->n_arcs * sizeof(uint32_t));
+    if (reps) memcpy(reps, r->reps, (size_t)r->n_paths * sizeof(uint32_t));
 }
 
 /* Neighbour offsets kept by Algorithm 1 (for tests of the adjacency itself). */

@@ -126,6 +126,8 @@ def test_brute_force(shape, kind, minimum):
     assert g.saddles.tolist() == b["saddles"]
     assert g.arcs() == b["arcs"]
     assert g.n_paths == sum(len(b["reps"][s]) for s in b["saddles"])
+    for i, s_ in enumerate(b["saddles"]):
+        assert g.saddle_reps(i).tolist() == sorted(int(x) for x in b["reps"][s_])
     assert n == g.label.size
 
 
