@@ -37,6 +37,9 @@ WORKLOADS = {
                    "N(0,0.01) noise, seed 0"),
     "grf384": ("3D 384^3 float32 Gaussian random field, P(k)~k^-11/3, seed 2 (profiling case: larger than "
                "L2, a few GB on the device)"),
+    "batch": ("Batched: 256 float32 fields, 2D (side log-uniform 64..2048) or 3D (side log-uniform 32..256) "
+              "50/50, sums of U{4..64} Gaussians + 1e-3 uniform noise, seed 3; one submission vs per-field "
+              "plain launches"),
 }
 
 
@@ -180,15 +183,27 @@ def run_reference(args, ws, rank):
         return
     import numpy as np
     import oracle
-    fld = make_field(args.workload)
-    sample, desc = oracle_slab(fld, args.ref_sample_vertices)
-    n = int(sample.size)
+    if args.workload == "batch":
+        from paper_2303_02724_gb300 import fields as F
+        samples, n = [], 0
+        for (e, sd, g) in F.batch_specs(3, args.batch_count):
+            if n + int(np.prod(e)) > args.ref_sample_vertices:
+                continue
+            samples.append(F.batch_field(e, sd, g).values)
+            n += int(np.prod(e))
+        desc = f"{len(samples)} fields of the batch mix ({n} vertices)"
+    else:
+        fld = make_field(args.workload)
+        sample, desc = oracle_slab(fld, args.ref_sample_vertices)
+        samples, n = [sample], int(sample.size)
     for _ in range(args.warmup):
-        oracle.compute(sample)
+        for smp in samples:
+            oracle.compute(smp)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.compute(sample)
+        for smp in samples:
+            oracle.compute(smp)
         times.append(time.perf_counter() - t0)
     total = sum(times)
     value = n * args.steps / total / 1e6
@@ -205,6 +220,62 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args, ws, rank, local):
+    """Batched submission of the uneven 256-field mix vs per-field plain launches."""
+    import torch
+    from paper_2303_02724_gb300 import _build, eg, fields as F
+    _build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    specs = F.batch_specs(3, args.batch_count)
+    flds = [F.batch_field(e, sd, g) for (e, sd, g) in specs]
+    ts = [torch.from_numpy(x.values).to(dev) for x in flds]
+    nv = sum(x.n for x in flds)
+    del flds
+    stream = torch.cuda.current_stream(dev)
+    h = eg.Handle(local)
+
+    def batched():
+        ids = h.batch_submit(ts, stream)
+        for rid in ids:
+            h.get_graph_device(rid)
+        for rid in ids:
+            h.release(rid)
+
+    def plain():
+        for t in ts:
+            rid = h.compute(t, stream)
+            h.get_graph_device(rid)
+            h.release(rid)
+
+    out = {}
+    for name, fn in [("batched", batched), ("plain", plain)]:
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        l0 = h.launch_count()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / args.steps
+        out[name] = {"ms_per_step": ms, "value": nv / (ms / 1e3) / 1e6,
+                     "gpu_launches": int(h.launch_count() - l0)}
+    if rank == 0:
+        line = {"metric": "Mvertices/s full extremum graph (bit-exact), batched vs plain",
+                "value": out["batched"]["value"], "unit": "Mvertices/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": out["batched"]["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOADS["batch"], "fields": len(ts), "vertices": nv},
+                "plain": out["plain"], "speedup_vs_plain": out["batched"]["value"] / out["plain"]["value"],
+                "gpu_launches": out["batched"]["gpu_launches"]}
+        print(json.dumps(line), flush=True)
+    h.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -216,12 +287,16 @@ def main():
     ap.add_argument("--ref-sample-vertices", type=int, default=2 * 1024 * 1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=256)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, ws, rank)
+        return
+    if args.workload == "batch":
+        run_batch(args, ws, rank, local)
         return
 
     import numpy as np
