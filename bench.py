@@ -37,6 +37,9 @@ WORKLOADS = {
                    "N(0,0.01) noise, seed 0"),
     "grf384": ("3D 384^3 float32 Gaussian random field, P(k)~k^-11/3, seed 2 (profiling case: larger than "
                "L2, a few GB on the device)"),
+    "serve": ("Served stream: requests with Poisson arrivals, each a float32 2D/3D/4D field (vertex count "
+              "log-uniform 1e4..1e7, sums of U{4..64} Gaussians + 1e-3 uniform noise), seed 4; admission by "
+              "free HBM, continuous batching on two engines"),
     "batch": ("Batched: 256 float32 fields, 2D (side log-uniform 64..2048) or 3D (side log-uniform 32..256) "
               "50/50, sums of U{4..64} Gaussians + 1e-3 uniform noise, seed 3; one submission vs per-field "
               "plain launches"),
@@ -192,6 +195,14 @@ def run_reference(args, ws, rank):
             samples.append(F.batch_field(e, sd, g).values)
             n += int(np.prod(e))
         desc = f"{len(samples)} fields of the batch mix ({n} vertices)"
+    elif args.workload == "serve":
+        samples, n = [], 0
+        for v in serve_fields(64):
+            if n + int(v.size) > args.ref_sample_vertices:
+                continue
+            samples.append(v)
+            n += int(v.size)
+        desc = f"{len(samples)} requests of the served stream ({n} vertices)"
     else:
         fld = make_field(args.workload)
         sample, desc = oracle_slab(fld, args.ref_sample_vertices)
@@ -276,6 +287,67 @@ def run_batch(args, ws, rank, local):
     h.close()
 
 
+def serve_fields(count, seed=4):
+    """Request fields: the seeded request shapes, values cropped at seeded
+    offsets from a few large sum-of-Gaussian fields per dimension."""
+    import numpy as np
+    from paper_2303_02724_gb300 import fields as F
+    specs = F.serve_requests(seed, count)
+    rng = np.random.default_rng(seed + 1000)
+    pools = {}
+    out = []
+    for (ext, fseed, ng) in specs:
+        d = len(ext)
+        if d not in pools:
+            side = int(round(1e7 ** (1.0 / d))) + 2
+            pools[d] = [F.serve_field((side,) * d, int(rng.integers(1 << 31)), 48).values for _ in range(3)]
+        src = pools[d][fseed % 3]
+        sl = tuple(slice(int(o), int(o) + int(e)) for o, e in
+                   zip([rng.integers(0, src.shape[k] - e + 1) for k, e in enumerate(reversed(ext))], reversed(ext)))
+        out.append(np.ascontiguousarray(src[sl]))
+    return out
+
+
+def run_serve(args, ws, rank, local):
+    import numpy as np
+    import torch
+    from paper_2303_02724_gb300 import _build, serve
+    _build.build()
+    torch.cuda.set_device(local)
+    vals = serve_fields(args.serve_requests)
+    nv = sum(int(v.size) for v in vals)
+    free, _total = torch.cuda.mem_get_info(local)
+    engines = [serve.GpuEngine(local), serve.GpuEngine(local)]
+    budget = int(free * 0.6)
+
+    def run(offsets):
+        srv = serve.Server(engines, budget_bytes=budget, max_batch=64, max_batch_vertices=1 << 27)
+        serve.replay(srv, vals, offsets)
+        srv.drain(3600)
+        srv.close()
+        return srv.stats()
+
+    run(np.zeros(min(len(vals), 64)))  # warm-up (pools, kernels)
+    cap = run(np.zeros(len(vals)))  # everything queued at once: capacity
+    rate_v = cap["throughput_mvps"] * 1e6
+    mean_n = nv / len(vals)
+    res = {}
+    for frac in args.serve_fractions:
+        offs = serve.poisson_arrivals(frac * rate_v / mean_n, len(vals), 4)
+        res[str(frac)] = run(offs)
+    for e in engines:
+        e.close()
+    if rank == 0:
+        line = {"metric": "served throughput (Mvertices/s) and latency", "value": cap["throughput_mvps"],
+                "unit": "Mvertices/s", "n_gpus": ws, "steps": len(args.serve_fractions) + 1, "warmup": 1,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": WORKLOADS["serve"], "requests": len(vals), "vertices": nv,
+                           "budget_bytes": budget, "engines": len(engines)},
+                "capacity": cap, "poisson": res}
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -288,6 +360,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--serve-requests", type=int, default=1024)
+    ap.add_argument("--serve-fractions", type=float, nargs="+", default=[0.5, 0.8, 0.95])
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -297,6 +371,9 @@ def main():
         return
     if args.workload == "batch":
         run_batch(args, ws, rank, local)
+        return
+    if args.workload == "serve":
+        run_serve(args, ws, rank, local)
         return
 
     import numpy as np
