@@ -70,13 +70,17 @@ typedef enum eg_status {
 #define EG_FLAG_MINIMUM_GRAPH 0x1u  /* minimum graph: the same order reversed (Sec. 2) */
 #define EG_FLAG_NO_LABELS     0x2u  /* do not keep per-vertex labels in the result    */
 
-/* Tuning knobs.  Zero in any field means "library default / autotuned". */
+/* Tuning knobs.  Zero in any field means "library default" (or the value a
+ * previous eg_autotune chose for this handle).  The neighbourhood halo is one
+ * vertex wide by construction (Algorithm 1 offsets are in {-1,0,1}^d) and is
+ * not a knob. */
 typedef struct eg_config {
     uint32_t flags;
-    int32_t classify_rows;   /* 2D/3D classification: grid rows per tile step      */
-    int32_t jump_tile;       /* tile edge (vertices) for tile-local path jumping   */
-    int32_t jump_rounds;     /* upper bound on global jump rounds (0 = automatic)  */
-    int32_t persistent_ctas; /* CTAs per SM for the persistent work-queue kernels  */
+    int32_t classify_rows;    /* 2D/3D classification tile: grid rows per tile (brick)   */
+    int32_t classify_planes;  /* planes one work item of the classifier marches over     */
+    int32_t resolve_walks;    /* gradient walks each resolver thread keeps in flight:
+                                 2, 4 or 8                                               */
+    int32_t persistent_ctas;  /* CTAs per SM of the persistent classifier work queue     */
     int32_t reserved[3];
 } eg_config;
 
@@ -156,6 +160,13 @@ EG_API eg_status eg_get_graph(eg_handle h, eg_result_id id, eg_graph *out);
 /* Same as eg_get_graph but fills the array pointers with the library-owned
  * DEVICE buffers instead of copying (valid until eg_release). */
 EG_API eg_status eg_get_graph_device(eg_handle h, eg_result_id id, eg_graph *out);
+
+/* Autotuner: time candidate values of every eg_config knob on this batch of
+ * fields (coordinate descent over the knobs, each candidate a full run of the
+ * pipeline timed with CUDA events on `stream`), keep the fastest in the
+ * handle's configuration for later calls, and return it in *best (may be
+ * NULL).  Results of the trial runs are discarded.  Errors as eg_batch_submit. */
+EG_API eg_status eg_autotune(eg_handle h, const eg_field_desc *fields, int n, void *stream, eg_config *best);
 
 /* Free a result's buffers (they return to the handle's pool). */
 EG_API eg_status eg_release(eg_handle h, eg_result_id id);

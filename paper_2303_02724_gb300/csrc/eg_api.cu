@@ -259,10 +259,14 @@ Layout make_layout(const Shape &sh, int sm_count, const eg_config &cfg)
         L.nyb = (n1 + ty - 1) / ty;
         L.nbricks = L.nyb * n2;
         L.bcap = ty * n0;
-        // enough work items to fill the GPU a few times over
-        const uint64_t want = uint64_t(std::max(sm_count, 1)) * 8;
-        uint32_t nzc = uint32_t(std::min<uint64_t>(n2, std::max<uint64_t>(1, (want + L.nyb - 1) / L.nyb)));
-        L.zc = (n2 + nzc - 1) / nzc;
+        if (cfg.classify_planes > 0) {
+            L.zc = std::min<uint32_t>(n2, uint32_t(cfg.classify_planes));
+        } else {
+            // enough work items to fill the GPU a few times over
+            const uint64_t want = uint64_t(std::max(sm_count, 1)) * 8;
+            const uint32_t nzc = uint32_t(std::min<uint64_t>(n2, std::max<uint64_t>(1, (want + L.nyb - 1) / L.nyb)));
+            L.zc = (n2 + nzc - 1) / nzc;
+        }
         L.nzc = (n2 + L.zc - 1) / L.zc;
         L.smem = zm_smem_bytes(n0, ty);
     } else {
@@ -354,11 +358,12 @@ struct Job {
 };
 
 // Run a set of fields (all of one call) through the pipeline.
-eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std::vector<uint64_t> &ids)
+eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std::vector<uint64_t> &ids,
+                   const eg_config &cfg)
 {
     const int nf = int(jobs.size());
     std::vector<Layout> lay(nf);
-    for (int i = 0; i < nf; i++) lay[i] = make_layout(jobs[i].sh, h->sm_count, h->cfg);
+    for (int i = 0; i < nf; i++) lay[i] = make_layout(jobs[i].sh, h->sm_count, cfg);
     // group fields by classifier kind so every launch covers a contiguous slice
     auto key = [&](int i) {
         return (lay[i].zm ? 0 : 2) * 16 + lay[i].kd * 2 + ((jobs[i].flags & kFlagMinimum) ? 1 : 0);
@@ -472,7 +477,9 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
     for (auto &G : groups) {
         if (G.zm)
             e = launch_classify_zm(G.minimum, Dd + G.first, G.count, G.items, G.smem,
-                                   static_cast<const uint32_t *>(h->lut3), st);
+                                   static_cast<const uint32_t *>(h->lut3),
+                                   reinterpret_cast<unsigned long long *>(h->ws_scan) + 2 + (&G - &groups[0]),
+                                   h->sm_count, cfg.persistent_ctas, st);
         else
             e = launch_classify_flat(G.kd, Dd + G.first, G.count, G.bricks, st);
         if (e != cudaSuccess) return fail(from_cuda(e));
@@ -486,7 +493,7 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
     if ((e = cudaEventCreateWithFlags(&k1, cudaEventDisableTiming)) != cudaSuccess) return fail(from_cuda(e));
     cudaEventRecord(k1, st);
     // step (b) runs while the host reads the counts back
-    e = launch_resolve(Dd, nf, total_bricks, st);
+    e = launch_resolve(Dd, nf, total_bricks, cfg.resolve_walks > 0 ? cfg.resolve_walks : 4, st);
     if (e != cudaSuccess) {
         cudaEventDestroy(k1);
         return fail(from_cuda(e));
@@ -707,7 +714,7 @@ eg_status eg_compute(eg_handle h, const float *field, int d, const int64_t *exte
     cudaSetDevice(h->device);
     std::vector<Job> jobs{{field, sh, h->cfg.flags & (kFlagMinimum | kFlagNoLabels)}};
     std::vector<uint64_t> ids;
-    eg_status s = run_jobs(h, jobs, static_cast<cudaStream_t>(stream), ids);
+    eg_status s = run_jobs(h, jobs, static_cast<cudaStream_t>(stream), ids, h->cfg);
     if (s == EG_OK) *out = ids[0];
     return s;
 }
@@ -758,7 +765,7 @@ eg_status eg_compute_host(eg_handle h, const float *field, int d, const int64_t 
     if (e != cudaSuccess) return from_cuda(e);
     std::vector<Job> jobs{{static_cast<const float *>(h->stage), sh, h->cfg.flags & (kFlagMinimum | kFlagNoLabels)}};
     std::vector<uint64_t> ids;
-    eg_status s = run_jobs(h, jobs, st, ids);
+    eg_status s = run_jobs(h, jobs, st, ids, h->cfg);
     if (s == EG_OK) *out = ids[0];
     return s;
 }
@@ -776,10 +783,106 @@ eg_status eg_batch_submit(eg_handle h, const eg_field_desc *fields, int n, void 
     std::lock_guard<std::mutex> g(h->mu);
     cudaSetDevice(h->device);
     std::vector<uint64_t> ids;
-    eg_status s = run_jobs(h, jobs, static_cast<cudaStream_t>(stream), ids);
+    eg_status s = run_jobs(h, jobs, static_cast<cudaStream_t>(stream), ids, h->cfg);
     if (s == EG_OK)
         for (int i = 0; i < n; i++) out_ids[i] = ids[i];
     return s;
+}
+
+namespace {
+
+// Device milliseconds of the steps of one launch (timing must have been on).
+eg_status launch_times(const Launch &L, float ms[4])
+{
+    if (!L.ev[0]) return EG_ERR_ARG;
+    cudaError_t e = cudaEventSynchronize(L.ev[4]);
+    if (e != cudaSuccess) return from_cuda(e);
+    // ev: start | classify | resolve | (count read-back, buffer set-up) | emit
+    cudaEventElapsedTime(&ms[0], L.ev[0], L.ev[1]);
+    cudaEventElapsedTime(&ms[1], L.ev[1], L.ev[2]);
+    cudaEventElapsedTime(&ms[2], L.ev[3], L.ev[4]);
+    cudaEventElapsedTime(&ms[3], L.ev[0], L.ev[4]);
+    return EG_OK;
+}
+
+// One timed run of the whole pipeline on `jobs` with configuration c; the
+// results are released.  *ms receives the step times of the fastest of `reps`
+// repetitions (by total).
+eg_status timed_trial(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, const eg_config &c, int reps,
+                      float ms[4])
+{
+    ms[0] = ms[1] = ms[2] = ms[3] = 1e30f;
+    for (int r = 0; r < reps; r++) {
+        std::vector<uint64_t> ids;
+        eg_status s = run_jobs(h, jobs, st, ids, c);
+        if (s != EG_OK) return s;
+        float t[4] = {0, 0, 0, 0};
+        eg_status ts = launch_times(*h->results[ids[0]]->launch, t);
+        for (uint64_t id : ids) {
+            Result &R = *h->results[id];
+            eg_status cs = collect(h, R);
+            if (R.done) cudaEventDestroy(R.done);
+            free_result_buffers(h, &R);
+            if (R.launch && R.launch.use_count() == 1) release_launch(h, R.launch.get());
+            h->results.erase(id);
+            if (cs != EG_OK) return cs;
+        }
+        if (ts != EG_OK) return ts;
+        if (t[3] < ms[3])
+            for (int k = 0; k < 4; k++) ms[k] = t[k];
+    }
+    return EG_OK;
+}
+
+}  // namespace
+
+eg_status eg_autotune(eg_handle h, const eg_field_desc *fields, int n, void *stream, eg_config *best)
+{
+    if (!h || n <= 0 || !fields) return EG_ERR_ARG;
+    std::vector<Job> jobs(n);
+    for (int i = 0; i < n; i++) {
+        if (!fields[i].field || !make_shape(fields[i].d, fields[i].extents, jobs[i].sh)) return EG_ERR_ARG;
+        jobs[i].field = fields[i].field;
+        jobs[i].flags = (h->cfg.flags | uint32_t(fields[i].flags)) & (kFlagMinimum | kFlagNoLabels);
+    }
+    std::lock_guard<std::mutex> g(h->mu);
+    cudaSetDevice(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool saved_timing = h->timing;
+    h->timing = true;
+    eg_config cur = h->cfg;
+    if (cur.resolve_walks <= 0) cur.resolve_walks = 4;
+    if (cur.persistent_ctas <= 0) cur.persistent_ctas = 3;
+    float ms[4];
+    eg_status s = timed_trial(h, jobs, st, cur, 2, ms);  // also warms the workspace
+    float cur_total = ms[3];
+    // coordinate descent: one knob at a time, the others at their current best
+    struct Knob { int32_t eg_config::*field; std::vector<int32_t> values; };
+    const std::vector<Knob> knobs = {
+        {&eg_config::classify_planes, {0, 16, 32, 64, 128}},
+        {&eg_config::classify_rows, {0, 8, 4, 2}},
+        {&eg_config::persistent_ctas, {2, 3}},
+        {&eg_config::resolve_walks, {2, 4, 8}},
+    };
+    for (const Knob &k : knobs) {
+        if (s != EG_OK) break;
+        for (int32_t v : k.values) {
+            if (cur.*(k.field) == v) continue;
+            eg_config c = cur;
+            c.*(k.field) = v;
+            s = timed_trial(h, jobs, st, c, 2, ms);
+            if (s != EG_OK) break;
+            if (ms[3] < cur_total) {
+                cur = c;
+                cur_total = ms[3];
+            }
+        }
+    }
+    h->timing = saved_timing;
+    if (s != EG_OK) return s;
+    h->cfg = cur;
+    if (best) *best = cur;
+    return EG_OK;
 }
 
 eg_status eg_get_graph(eg_handle h, eg_result_id id, eg_graph *out)

@@ -185,7 +185,8 @@ constexpr uint32_t kPosZ = (1u << 10) | (1u << 11) | (1u << 12) | (1u << 13);
 
 template <bool MIN>
 __global__ void __launch_bounds__(kZmThreads, 3)
-k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__restrict__ lut)
+k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__restrict__ lut, uint64_t total_items,
+              unsigned long long *ticket)
 {
     extern __shared__ float4 zm_smem4[];
     float *ring = reinterpret_cast<float *>(zm_smem4);
@@ -196,8 +197,17 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
     __shared__ unsigned s_cnt[4];
     __shared__ uint2 s_queue[kSaddleQueue];  // (record index, x | ring row << 11 | upper << 18)
 
+    __shared__ unsigned long long s_item;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint64_t g = blockIdx.x;
+    for (int i = tid; i < 1024; i += kZmThreads) s_lut[i] = __ldg(lut + i);
+    if (tid < 14) s_adj[tid] = Nbr<3>::adj_mask(tid);
+    // persistent work queue: take items in ticket order until none are left
+    while (true) {
+    __syncthreads();
+    if (tid == 0) s_item = atomicAdd(ticket, 1ull);
+    __syncthreads();
+    const uint64_t g = s_item;
+    if (g >= total_items) break;
     const int fi = find_field<true>(fields, nf, g);
     const FieldDev &F = fields[fi];
     const uint32_t item = uint32_t(g - F.item0);
@@ -217,9 +227,7 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
     const int ze = int(min(G.n2, zci * F.zc + F.zc));
     const bool vec = F.vec != 0;
 
-    for (int i = tid; i < 1024; i += kZmThreads) s_lut[i] = __ldg(lut + i);
     if (tid < 14) {
-        s_adj[tid] = Nbr<3>::adj_mask(tid);
         const uint32_t p = Nbr<3>::pat(tid);
         const uint32_t mag = ((p & 1u) ? 1u : 0u) + ((p & 2u) ? G.n0 : 0u) + ((p & 4u) ? G.n0 * G.n1 : 0u);
         s_off[tid] = Nbr<3>::neg(tid) ? 0u - mag : mag;
@@ -457,12 +465,16 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
     if (tid == 0 && prev_brick != 0xffffffffu)
         F.bcnt[prev_brick] = make_uint4(s_cnt[0], s_cnt[1] - s_cnt[0], s_cnt[2], 0u);
     if (anynan) atomicOr(F.err, kErrNaN);
+    // drain this item's outstanding (empty) copy groups before the ring is reused
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    }
 }
 
 size_t zm_smem_bytes(uint32_t n0, uint32_t ty) { return size_t(4) * zm_ring_floats(n0, ty) * sizeof(float); }
 
 cudaError_t launch_classify_zm(bool minimum, const FieldDev *fields, int nf, uint64_t total_items, size_t smem,
-                               const uint32_t *lut, cudaStream_t st)
+                               const uint32_t *lut, unsigned long long *ticket, int sm_count, int ctas_per_sm,
+                               cudaStream_t st)
 {
     if (total_items == 0) return cudaSuccess;
     auto kern = minimum ? k_classify_zm<true> : k_classify_zm<false>;
@@ -482,7 +494,9 @@ cudaError_t launch_classify_zm(bool minimum, const FieldDev *fields, int nf, uin
         done_mask[minimum].fetch_or(bit);
     }
     // (the row layout bounds the ring at 4 x (4 rows x 1032 + 16) floats = 66 KB)
-    kern<<<dim3(unsigned(total_items)), kZmThreads, smem, st>>>(fields, nf, lut);
+    uint64_t grid = uint64_t(sm_count > 0 ? sm_count : 1) * uint64_t(ctas_per_sm > 0 ? ctas_per_sm : 3);
+    if (grid > total_items) grid = total_items;
+    kern<<<dim3(unsigned(grid)), kZmThreads, smem, st>>>(fields, nf, lut, total_items, ticket);
     return cudaGetLastError();
 }
 

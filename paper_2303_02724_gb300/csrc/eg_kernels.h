@@ -14,8 +14,11 @@ cudaError_t launch_classify_flat(int kd, const FieldDev *fields, int nf, uint64_
 // Steps (a)+(c), plane-marching kernel for 2D/3D fields with rows of at most
 // 1024 vertices.  lut: 2^14-bit saddle table (eg_saddle_lut3).
 size_t zm_smem_bytes(uint32_t n0, uint32_t ty);
+// Persistent: grid = min(total_items, sm_count * ctas_per_sm) CTAs take work
+// items from *ticket (zeroed before the launch).
 cudaError_t launch_classify_zm(bool minimum, const FieldDev *fields, int nf, uint64_t total_items, size_t smem,
-                               const uint32_t *lut, cudaStream_t st);
+                               const uint32_t *lut, unsigned long long *ticket, int sm_count, int ctas_per_sm,
+                               cudaStream_t st);
 
 // Scan A (arcs = false) / scan B (arcs = true) over all bricks of all fields.
 uint64_t scan_tiles(uint32_t nbricks);
@@ -28,7 +31,7 @@ cudaError_t launch_classify_one(int kd, const FieldDev &F, cudaStream_t st);
 cudaError_t launch_resolve_one(const FieldDev &F, cudaStream_t st);
 
 // Step (b): labels = fixed points of the gradient pointers (all fields).
-cudaError_t launch_resolve(const FieldDev *fields, int nf, uint64_t total_bricks, cudaStream_t st);
+cudaError_t launch_resolve(const FieldDev *fields, int nf, uint64_t total_bricks, int walks, cudaStream_t st);
 
 // Steps (d)+(e): nodes and arc ends per brick (one kernel dimension), then CSR.
 cudaError_t launch_nodes_d(int kd, const FieldDev *fields, int nf, uint64_t base, uint64_t bricks, cudaStream_t st);

@@ -16,9 +16,9 @@
 namespace eg {
 
 constexpr int kResolveThreads = 256;
-constexpr int kIlp = 4;
 
-// Resolve the labels of brick b of field F.
+// Resolve the labels of brick b of field F, kIlp walks in flight per thread.
+template <int kIlp>
 __device__ __forceinline__ void resolve_brick(const FieldDev &F, uint32_t b)
 {
     uint64_t v0;
@@ -62,20 +62,21 @@ __device__ __forceinline__ void resolve_brick(const FieldDev &F, uint32_t b)
     }
 }
 
+template <int kIlp>
 __global__ void __launch_bounds__(kResolveThreads)
 k_resolve_chase(const FieldDev *__restrict__ fields, int nf)
 {
     const uint64_t g = blockIdx.x;
     const int fi = find_field<false>(fields, nf, g);
     const FieldDev &F = fields[fi];
-    resolve_brick(F, uint32_t(g - F.brick0));
+    resolve_brick<kIlp>(F, uint32_t(g - F.brick0));
 }
 
 // Single-field variant with the descriptor passed by value.
 __global__ void __launch_bounds__(kResolveThreads)
 k_resolve_one(const FieldDev F)
 {
-    resolve_brick(F, blockIdx.x);
+    resolve_brick<4>(F, blockIdx.x);
 }
 
 cudaError_t launch_resolve_one(const FieldDev &F, cudaStream_t st)
@@ -85,10 +86,13 @@ cudaError_t launch_resolve_one(const FieldDev &F, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_resolve(const FieldDev *fields, int nf, uint64_t total_bricks, cudaStream_t st)
+cudaError_t launch_resolve(const FieldDev *fields, int nf, uint64_t total_bricks, int walks, cudaStream_t st)
 {
     if (total_bricks == 0) return cudaSuccess;
-    k_resolve_chase<<<dim3(unsigned(total_bricks)), kResolveThreads, 0, st>>>(fields, nf);
+    const dim3 grid = dim3(static_cast<unsigned>(total_bricks));
+    if (walks <= 2) k_resolve_chase<2><<<grid, kResolveThreads, 0, st>>>(fields, nf);
+    else if (walks <= 4) k_resolve_chase<4><<<grid, kResolveThreads, 0, st>>>(fields, nf);
+    else k_resolve_chase<8><<<grid, kResolveThreads, 0, st>>>(fields, nf);
     return cudaGetLastError();
 }
 

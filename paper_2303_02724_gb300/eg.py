@@ -32,8 +32,12 @@ class EGError(RuntimeError):
 
 class EGConfig(ctypes.Structure):
     _fields_ = [("flags", ctypes.c_uint32), ("classify_rows", ctypes.c_int32),
-                ("jump_tile", ctypes.c_int32), ("jump_rounds", ctypes.c_int32),
+                ("classify_planes", ctypes.c_int32), ("resolve_walks", ctypes.c_int32),
                 ("persistent_ctas", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k in ["flags", "classify_rows", "classify_planes",
+                                               "resolve_walks", "persistent_ctas"]}
 
 
 class EGFieldDesc(ctypes.Structure):
@@ -76,6 +80,7 @@ SIGNATURES = {
     "eg_debug_fail_alloc": (ctypes.c_int, [_P, ctypes.c_int]),
     "eg_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "eg_labels_static": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_uint32, _P, _P]),
+    "eg_autotune": (ctypes.c_int, [_P, ctypes.POINTER(EGFieldDesc), ctypes.c_int, _P, ctypes.POINTER(EGConfig)]),
 }
 
 STATIC_MAX_VERTICES = 1 << 20
@@ -205,6 +210,22 @@ class Handle:
 
     def batch_submit(self, fields: Sequence, stream=None, flags: Sequence[int] = ()) -> list:
         n = len(fields)
+        descs = self._descs(fields, flags)
+        ids = (ctypes.c_uint64 * max(1, n))()
+        _check(self._lib.eg_batch_submit(self._h, descs, n, ctypes.c_void_p(_stream_ptr(stream)), ids),
+               "eg_batch_submit")
+        return [ids[i] for i in range(n)]
+
+    def autotune(self, fields: Sequence, stream=None) -> dict:
+        """Pick the fastest knob values on these fields; returns them."""
+        descs = self._descs(fields)
+        best = EGConfig()
+        _check(self._lib.eg_autotune(self._h, descs, len(fields), ctypes.c_void_p(_stream_ptr(stream)),
+                                     ctypes.byref(best)), "eg_autotune")
+        return best.as_dict()
+
+    def _descs(self, fields, flags=()):
+        n = len(fields)
         descs = (EGFieldDesc * max(1, n))()
         for i, f in enumerate(fields):
             if not f.is_cuda or f.dtype.itemsize != 4 or not f.is_contiguous():
@@ -215,10 +236,7 @@ class Handle:
             descs[i].flags = int(flags[i]) if i < len(flags) else 0
             for k, x in enumerate(ext):
                 descs[i].extents[k] = x
-        ids = (ctypes.c_uint64 * max(1, n))()
-        _check(self._lib.eg_batch_submit(self._h, descs, n, ctypes.c_void_p(_stream_ptr(stream)), ids),
-               "eg_batch_submit")
-        return [ids[i] for i in range(n)]
+        return descs
 
     # --------------------------------------------------------------- results
     def counts(self, rid: int) -> dict:

@@ -160,3 +160,39 @@ def test_batch_uneven(handle):
         g = handle.get_graph(rid)
         handle.release(rid)
         assert_same(g, oracle.compute(x.values))
+
+
+@pytest.mark.parametrize("knobs", [
+    dict(classify_rows=2, classify_planes=16, resolve_walks=8, persistent_ctas=2),
+    dict(classify_rows=8, classify_planes=128, resolve_walks=2, persistent_ctas=3),
+    dict(classify_rows=1, classify_planes=1, resolve_walks=4, persistent_ctas=1),
+])
+def test_knobs_do_not_change_results(knobs):
+    from paper_2303_02724_gb300 import eg
+    cfg = eg.EGConfig()
+    for k, v in knobs.items():
+        setattr(cfg, k, v)
+    flds = [F.grf((40, 36, 32), 2), F.config_2d_256(side=200), F.white_noise((7, 6, 5, 4), 1),
+            F.config_3d_256(side=30)]
+    with eg.Handle(0, config=cfg) as h:
+        ids = h.batch_submit([torch.from_numpy(x.values).cuda() for x in flds])
+        for x, rid in zip(flds, ids):
+            g = h.get_graph(rid)
+            h.release(rid)
+            assert_same(g, oracle.compute(x.values))
+
+
+def test_autotune_keeps_parity():
+    from paper_2303_02724_gb300 import eg
+    specs = F.batch_specs(3, 12, scale=0.1)
+    flds = [F.batch_field(e, s, gn) for (e, s, gn) in specs]
+    ts = [torch.from_numpy(x.values).cuda() for x in flds]
+    with eg.Handle(0) as h:
+        best = h.autotune(ts)
+        assert best["resolve_walks"] in (2, 4, 8) and best["persistent_ctas"] in (2, 3)
+        assert best["classify_planes"] in (0, 16, 32, 64, 128) and best["classify_rows"] in (0, 8, 4, 2)
+        ids = h.batch_submit(ts)
+        for x, rid in zip(flds, ids):
+            g = h.get_graph(rid)
+            h.release(rid)
+            assert_same(g, oracle.compute(x.values))
