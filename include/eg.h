@@ -69,6 +69,8 @@ typedef enum eg_status {
 /* eg_config.flags */
 #define EG_FLAG_MINIMUM_GRAPH 0x1u  /* minimum graph: the same order reversed (Sec. 2) */
 #define EG_FLAG_NO_LABELS     0x2u  /* do not keep per-vertex labels in the result    */
+#define EG_FLAG_NO_GRAPH      0x4u  /* eg_batch_submit: launch the steps directly
+                                       instead of replaying captured CUDA graphs    */
 
 /* Tuning knobs.  Zero in any field means "library default" (or the value a
  * previous eg_autotune chose for this handle).  The neighbourhood halo is one
@@ -143,9 +145,12 @@ EG_API eg_status eg_compute_host(eg_handle h, const float *field, int d,
                                  const int64_t *extents, void *stream, eg_result_id *out);
 
 /* Many fields of uneven sizes and dimensions in one launch per step: the
- * classification and output kernels drain a device work queue of
- * (field, tile) items, and the whole step sequence is replayed from a
- * captured CUDA graph when the batch layout repeats.  out_ids[n] receives one
+ * persistent classifier drains a device work queue of (field, tile) items and
+ * every other step covers all fields' bricks in one grid.  The steps are
+ * captured once per batch layout (shapes, flags, configuration) into CUDA
+ * graphs and replayed for every later batch with the same layout; the
+ * per-field pointers reach the kernels through a descriptor table uploaded by
+ * the graph itself.  out_ids[n] receives one
  * result per field, in order.  Field pointers must stay valid until their
  * results are read.  Errors as eg_compute; on error no result is created. */
 EG_API eg_status eg_batch_submit(eg_handle h, const eg_field_desc *fields, int n, void *stream,

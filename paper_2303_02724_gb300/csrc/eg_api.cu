@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <string>
 #include <memory>
 #include <mutex>
 #include <unordered_map>
@@ -200,6 +201,9 @@ struct eg_ctx {
     uint64_t next_id = 1;
     std::atomic<uint64_t> launches{0};
     bool timing = false;
+    cudaStream_t cap = nullptr;  // private stream for graph capture
+    std::unique_ptr<struct eg_graph_cache> graphs;
+    uint64_t ws_gen = 0;  // bumped whenever the workspace is reallocated
 };
 
 namespace {
@@ -300,6 +304,7 @@ eg_status ensure_workspace(eg_ctx *h, uint64_t recs, uint64_t bricks, uint64_t t
     if (recs <= h->ws_rec_cap && bricks <= h->ws_bricks && tiles <= h->ws_tiles) return EG_OK;
     // earlier computations may still use the old workspace
     cudaEventSynchronize(h->ws_free);
+    h->ws_gen++;
     eg_status s;
     uint64_t cap = h->ws_rec_cap;
     if (recs > h->ws_rec_cap) {
@@ -357,9 +362,156 @@ struct Job {
     uint32_t flags;
 };
 
-// Run a set of fields (all of one call) through the pipeline.
+// One launch slice: fields of one classifier kind, contiguous in the table.
+struct Group {
+    int key, first, count;
+    uint64_t brick0, bricks, items;
+    size_t smem;
+    bool zm, minimum;
+    int kd;
+};
+
+// Everything the enqueue phases of one call need besides the table contents.
+struct Plan {
+    int nf = 0;
+    std::vector<Group> groups;
+    uint64_t total_bricks = 0, total_tiles = 0;
+    size_t desc_bytes = 0;
+    int walks = 4, ctas = 3;
+    std::string signature;  // identical for calls that can share a captured graph
+};
+
+// Enqueue one phase of the pipeline on st, reading descriptors from Dd:
+//   0: descriptor upload, scan state reset, counters reset, classification
+//      (steps a+c), scan A;   1: resolution (step b);
+//   2: descriptor upload, nodes and arc ends, scan B, CSR (steps d+e).
+// Only stream-ordered operations: the same calls are captured into graphs.
+eg_status enqueue_part(eg_ctx *h, int part, const Plan &P, const FieldDev *Dd, const void *desc_host,
+                       cudaStream_t st, int *launches)
+{
+    cudaError_t e = cudaSuccess;
+    int nl = 0;
+    if (part == 0) {
+        if ((e = cudaMemcpyAsync(const_cast<FieldDev *>(Dd), desc_host, P.desc_bytes, cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess)
+            return from_cuda(e);
+        if ((e = cudaMemsetAsync(h->ws_scan, 0, scan_workspace_bytes(P.total_tiles), st)) != cudaSuccess)
+            return from_cuda(e);
+        if ((e = launch_init_fields(Dd, P.nf, st)) != cudaSuccess) return from_cuda(e);
+        nl++;
+        for (size_t gi = 0; gi < P.groups.size(); gi++) {
+            const Group &G = P.groups[gi];
+            if (G.zm)
+                e = launch_classify_zm(G.minimum, Dd + G.first, G.count, G.items, G.smem,
+                                       static_cast<const uint32_t *>(h->lut3),
+                                       reinterpret_cast<unsigned long long *>(h->ws_scan) + 2 + gi, h->sm_count,
+                                       P.ctas, st);
+            else
+                e = launch_classify_flat(G.kd, Dd + G.first, G.count, G.bricks, st);
+            if (e != cudaSuccess) return from_cuda(e);
+            nl++;
+        }
+        if ((e = launch_scan(false, Dd, P.nf, P.total_tiles, h->ws_scan, st)) != cudaSuccess) return from_cuda(e);
+        nl++;
+    } else if (part == 1) {
+        if ((e = launch_resolve(Dd, P.nf, P.total_bricks, P.walks, st)) != cudaSuccess) return from_cuda(e);
+        nl++;
+    } else {
+        if ((e = cudaMemcpyAsync(const_cast<FieldDev *>(Dd), desc_host, P.desc_bytes, cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess)
+            return from_cuda(e);
+        for (const Group &G : P.groups) {
+            if ((e = launch_nodes_d(G.kd, Dd + G.first, G.count, G.brick0, G.bricks, st)) != cudaSuccess)
+                return from_cuda(e);
+            nl++;
+        }
+        if ((e = launch_scan(true, Dd, P.nf, P.total_tiles, h->ws_scan, st)) != cudaSuccess) return from_cuda(e);
+        if ((e = launch_csr(Dd, P.nf, P.total_bricks, st)) != cudaSuccess) return from_cuda(e);
+        nl += 2;
+    }
+    if (launches) *launches = nl;
+    return EG_OK;
+}
+
+// Captured graphs of the three phases for one plan signature.
+struct GraphEntry {
+    cudaGraph_t g[3] = {nullptr, nullptr, nullptr};
+    cudaGraphExec_t x[3] = {nullptr, nullptr, nullptr};
+    cudaGraphNode_t upload[3] = {nullptr, nullptr, nullptr};  // descriptor memcpy of phases 0 and 2
+    int launches[3] = {0, 0, 0};
+    void *desc_dev = nullptr;
+    uint64_t ws_gen = 0, last_use = 0;
+};
+
+void destroy_graph(eg_ctx *h, GraphEntry &E);
+
+}  // namespace
+
+// (graph cache lives in the handle)
+struct eg_graph_cache {
+    std::map<std::string, GraphEntry> entries;
+    uint64_t clock = 0;
+};
+
+namespace {
+
+eg_graph_cache &graph_cache(eg_ctx *h)
+{
+    if (!h->graphs) h->graphs.reset(new eg_graph_cache());
+    return *h->graphs;
+}
+
+uint64_t &ws_generation(eg_ctx *h) { return h->ws_gen; }
+
+void destroy_graph(eg_ctx *h, GraphEntry &E)
+{
+    for (int p = 0; p < 3; p++) {
+        if (E.x[p]) cudaGraphExecDestroy(E.x[p]);
+        if (E.g[p]) cudaGraphDestroy(E.g[p]);
+        E.x[p] = nullptr;
+        E.g[p] = nullptr;
+    }
+    h->pool.release(E.desc_dev);
+    E.desc_dev = nullptr;
+}
+
+// Capture the three phases of plan P (descriptor upload source: desc_host).
+eg_status capture_graphs(eg_ctx *h, const Plan &P, const void *desc_host, GraphEntry &E, cudaStream_t cap)
+{
+    cudaError_t e = h->pool.alloc(&E.desc_dev, P.desc_bytes);
+    if (e != cudaSuccess) return from_cuda(e);
+    if ((e = prepare_classify_zm()) != cudaSuccess) return from_cuda(e);
+    for (int p = 0; p < 3; p++) {
+        if ((e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return from_cuda(e);
+        eg_status s = enqueue_part(h, p, P, static_cast<const FieldDev *>(E.desc_dev), desc_host, cap, &E.launches[p]);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(cap, &g);
+        if (s != EG_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        if (e != cudaSuccess) return from_cuda(e);
+        E.g[p] = g;
+        if (p != 1) {
+            size_t nn = 0;
+            cudaGraphGetNodes(g, nullptr, &nn);
+            std::vector<cudaGraphNode_t> nodes(nn);
+            cudaGraphGetNodes(g, nodes.data(), &nn);
+            for (auto n : nodes) {
+                cudaGraphNodeType t;
+                if (cudaGraphNodeGetType(n, &t) == cudaSuccess && t == cudaGraphNodeTypeMemcpy) E.upload[p] = n;
+            }
+            if (!E.upload[p]) return EG_ERR_INTERNAL;
+        }
+        if ((e = cudaGraphInstantiate(&E.x[p], g, 0)) != cudaSuccess) return from_cuda(e);
+    }
+    return EG_OK;
+}
+
+// Run a set of fields (all of one call) through the pipeline.  use_graph:
+// replay (capturing on first use) the graphs of this call's layout.
 eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std::vector<uint64_t> &ids,
-                   const eg_config &cfg)
+                   const eg_config &cfg, bool use_graph = false)
 {
     const int nf = int(jobs.size());
     std::vector<Layout> lay(nf);
@@ -372,17 +524,22 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
     for (int i = 0; i < nf; i++) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key(a) < key(b); });
 
-    uint64_t total_bricks = 0, total_recs = 0, total_tiles = 0;
+    Plan P;
+    P.nf = nf;
+    P.walks = cfg.resolve_walks > 0 ? cfg.resolve_walks : 4;
+    P.ctas = cfg.persistent_ctas > 0 ? cfg.persistent_ctas : 3;
+    uint64_t total_recs = 0;
     for (int i = 0; i < nf; i++) {
-        total_bricks += lay[i].nbricks;
+        P.total_bricks += lay[i].nbricks;
         total_recs += uint64_t(lay[i].nbricks) * lay[i].bcap;
-        total_tiles += scan_tiles(lay[i].nbricks);
+        P.total_tiles += scan_tiles(lay[i].nbricks);
     }
-    eg_status es = ensure_workspace(h, total_recs, total_bricks, total_tiles);
+    P.desc_bytes = sizeof(FieldDev) * size_t(nf);
+    eg_status es = ensure_workspace(h, total_recs, P.total_bricks, P.total_tiles);
     if (es != EG_OK) return es;
 
     auto L = std::make_shared<Launch>();
-    L->bytes = sizeof(FieldDev) * size_t(nf);
+    L->bytes = P.desc_bytes;
     cudaError_t e;
     std::vector<std::unique_ptr<Result>> res(nf);
     auto fail = [&](eg_status s) {
@@ -395,21 +552,23 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
         release_launch(h, L.get());
         return s;
     };
-    if ((e = h->pool.alloc(&L->desc_dev, L->bytes)) != cudaSuccess) return fail(from_cuda(e));
+    if (!use_graph && (e = h->pool.alloc(&L->desc_dev, L->bytes)) != cudaSuccess) return fail(from_cuda(e));
     if ((e = h->hpool.alloc(&L->desc_host, L->bytes)) != cudaSuccess) return fail(from_cuda(e));
     FieldDev *Dh = reinterpret_cast<FieldDev *>(L->desc_host);
     std::memset(Dh, 0, L->bytes);
 
-    struct Group { int key, first, count; uint64_t brick0, bricks, items; size_t smem; bool zm, minimum; int kd; };
-    std::vector<Group> groups;
     uint64_t brick0 = 0, rec0 = 0, tile0 = 0;
+    char sig[128];
+    std::snprintf(sig, sizeof sig, "c%d/%d/%d/%d/%u|", cfg.classify_rows, cfg.classify_planes, P.walks, P.ctas,
+                  cfg.flags);
+    P.signature = sig;
     for (int oi = 0; oi < nf; oi++) {
         const int i = order[oi];
         const Job &j = jobs[i];
         const Layout &ly = lay[i];
-        if (groups.empty() || groups.back().key != key(i))
-            groups.push_back({key(i), oi, 0, brick0, 0, 0, 0, ly.zm, (j.flags & kFlagMinimum) != 0, ly.kd});
-        Group &G = groups.back();
+        if (P.groups.empty() || P.groups.back().key != key(i))
+            P.groups.push_back({key(i), oi, 0, brick0, 0, 0, 0, ly.zm, (j.flags & kFlagMinimum) != 0, ly.kd});
+        Group &G = P.groups.back();
         auto r = std::make_unique<Result>();
         r->d = j.sh.d;
         for (int q = 0; q < kMaxDim; q++) r->ext[q] = q < j.sh.d ? j.sh.n[q] : 0;
@@ -457,48 +616,82 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
         brick0 += ly.nbricks;
         rec0 += uint64_t(ly.nbricks) * ly.bcap;
         tile0 += scan_tiles(ly.nbricks);
+        char fs[96];
+        std::snprintf(fs, sizeof fs, "%d,%d,%u,%u,%u,%u,%u,%u,%u,%u;", key(i), ly.kd, F.N, ly.ty, ly.nyb, ly.nbricks,
+                      ly.zc, ly.nzc, F.vec, F.n[0]);
+        P.signature += fs;
     }
+
+    // graphs for this layout (captured on first use; the workspace generation
+    // is part of their validity because scan-state pointers are baked in)
+    GraphEntry *GE = nullptr;
+    if (use_graph) {
+        eg_graph_cache &C = graph_cache(h);
+        auto it = C.entries.find(P.signature);
+        if (it != C.entries.end() && it->second.ws_gen != ws_generation(h)) {
+            cudaEventSynchronize(h->ws_free);
+            destroy_graph(h, it->second);
+            C.entries.erase(it);
+            it = C.entries.end();
+        }
+        if (it == C.entries.end()) {
+            if (C.entries.size() >= 16) {  // evict the least recently used
+                auto lru = C.entries.begin();
+                for (auto jt = C.entries.begin(); jt != C.entries.end(); ++jt)
+                    if (jt->second.last_use < lru->second.last_use) lru = jt;
+                cudaEventSynchronize(h->ws_free);
+                destroy_graph(h, lru->second);
+                C.entries.erase(lru);
+            }
+            GraphEntry E;
+            E.ws_gen = ws_generation(h);
+            eg_status cs = capture_graphs(h, P, L->desc_host, E, h->cap);
+            if (cs != EG_OK) {
+                destroy_graph(h, E);
+                return fail(cs);
+            }
+            it = C.entries.emplace(P.signature, E).first;
+        }
+        GE = &it->second;
+        GE->last_use = ++C.clock;
+    }
+    const FieldDev *Dd = static_cast<const FieldDev *>(GE ? GE->desc_dev : L->desc_dev);
+    auto run_part = [&](int p) -> eg_status {
+        if (!GE) {
+            int nl = 0;
+            eg_status s = enqueue_part(h, p, P, Dd, L->desc_host, st, &nl);
+            h->launches += uint64_t(nl);
+            return s;
+        }
+        if (p != 1) {
+            cudaError_t x = cudaGraphExecMemcpyNodeSetParams1D(GE->x[p], GE->upload[p], GE->desc_dev, L->desc_host,
+                                                               P.desc_bytes, cudaMemcpyHostToDevice);
+            if (x != cudaSuccess) return from_cuda(x);
+        }
+        cudaError_t x = cudaGraphLaunch(GE->x[p], st);
+        if (x != cudaSuccess) return from_cuda(x);
+        h->launches += uint64_t(GE->launches[p]);
+        return EG_OK;
+    };
 
     // the workspace is free once earlier computations' last kernels finished
     if ((e = cudaStreamWaitEvent(st, h->ws_free, 0)) != cudaSuccess) return fail(from_cuda(e));
-    for (int i = 0; i < nf; i++)
-        if ((e = cudaMemsetAsync(res[i]->small, 0, sizeof(SmallBlock), st)) != cudaSuccess) return fail(from_cuda(e));
-    if ((e = cudaMemsetAsync(h->ws_scan, 0, scan_workspace_bytes(total_tiles), st)) != cudaSuccess)
-        return fail(from_cuda(e));
-    if ((e = cudaMemcpyAsync(L->desc_dev, L->desc_host, L->bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
-        return fail(from_cuda(e));
-    const FieldDev *Dd = static_cast<const FieldDev *>(L->desc_dev);
     if (h->timing) {
         for (auto &ev : L->ev)
             if ((e = cudaEventCreate(&ev)) != cudaSuccess) return fail(from_cuda(e));
         cudaEventRecord(L->ev[0], st);
     }
-    // steps (a)+(c)
-    for (auto &G : groups) {
-        if (G.zm)
-            e = launch_classify_zm(G.minimum, Dd + G.first, G.count, G.items, G.smem,
-                                   static_cast<const uint32_t *>(h->lut3),
-                                   reinterpret_cast<unsigned long long *>(h->ws_scan) + 2 + (&G - &groups[0]),
-                                   h->sm_count, cfg.persistent_ctas, st);
-        else
-            e = launch_classify_flat(G.kd, Dd + G.first, G.count, G.bricks, st);
-        if (e != cudaSuccess) return fail(from_cuda(e));
-        h->launches++;
-    }
-    // node counts and offsets
-    if ((e = launch_scan(false, Dd, nf, total_tiles, h->ws_scan, st)) != cudaSuccess) return fail(from_cuda(e));
-    h->launches++;
+    // steps (a)+(c) and the node counts
+    if ((es = run_part(0)) != EG_OK) return fail(es);
     if (h->timing) cudaEventRecord(L->ev[1], st);
     cudaEvent_t k1;
     if ((e = cudaEventCreateWithFlags(&k1, cudaEventDisableTiming)) != cudaSuccess) return fail(from_cuda(e));
     cudaEventRecord(k1, st);
     // step (b) runs while the host reads the counts back
-    e = launch_resolve(Dd, nf, total_bricks, cfg.resolve_walks > 0 ? cfg.resolve_walks : 4, st);
-    if (e != cudaSuccess) {
+    if ((es = run_part(1)) != EG_OK) {
         cudaEventDestroy(k1);
-        return fail(from_cuda(e));
+        return fail(es);
     }
-    h->launches++;
     if (h->timing) cudaEventRecord(L->ev[2], st);
     void *hcounts = nullptr;
     if ((e = h->hpool.alloc(&hcounts, sizeof(SmallBlock) * size_t(nf))) != cudaSuccess) {
@@ -549,21 +742,10 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
         F.ends = static_cast<uint32_t *>(r.ends);
         F.ucnt = static_cast<uint8_t *>(r.ucnt);
     }
-    // classify has finished (we waited for it), so the table may be rewritten;
-    // the copy is ordered after resolve on the stream
-    if ((e = cudaMemcpyAsync(L->desc_dev, L->desc_host, L->bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
-        return fail(from_cuda(e));
+    // phase 0 has finished (we waited for it), so the host table may change;
+    // phase 2 uploads it again, ordered after resolution on the stream
     if (h->timing) cudaEventRecord(L->ev[3], st);
-    // steps (d)+(e)
-    for (auto &G : groups) {
-        if ((e = launch_nodes_d(G.kd, Dd + G.first, G.count, G.brick0, G.bricks, st)) != cudaSuccess)
-            return fail(from_cuda(e));
-        h->launches++;
-    }
-    if ((e = launch_scan(true, Dd, nf, total_tiles, h->ws_scan, st)) != cudaSuccess) return fail(from_cuda(e));
-    h->launches++;
-    if ((e = launch_csr(Dd, nf, total_bricks, st)) != cudaSuccess) return fail(from_cuda(e));
-    h->launches++;
+    if ((es = run_part(2)) != EG_OK) return fail(es);
     if (h->timing) cudaEventRecord(L->ev[4], st);
     cudaEventRecord(h->ws_free, st);
     ids.resize(nf);
@@ -651,6 +833,7 @@ eg_status eg_create(eg_handle *out, int device, const eg_config *cfg)
     if (e != cudaSuccess) return from_cuda(e);
     cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, device);
     if ((e = cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking)) != cudaSuccess) return from_cuda(e);
+    if ((e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking)) != cudaSuccess) return from_cuda(e);
     if ((e = cudaEventCreateWithFlags(&h->ws_free, cudaEventDisableTiming)) != cudaSuccess) return from_cuda(e);
     cudaEventRecord(h->ws_free, h->side);
     {
@@ -693,6 +876,11 @@ eg_status eg_destroy(eg_handle h)
         for (auto &kv : h->results)
             if (kv.second->done) cudaEventDestroy(kv.second->done);
         h->results.clear();
+        if (h->graphs) {
+            for (auto &kv : h->graphs->entries) destroy_graph(h, kv.second);
+            h->graphs.reset();
+        }
+        if (h->cap) cudaStreamDestroy(h->cap);
         h->pool.destroy();
         h->hpool.destroy();
         if (h->stage) cudaFree(h->stage);
@@ -783,7 +971,8 @@ eg_status eg_batch_submit(eg_handle h, const eg_field_desc *fields, int n, void 
     std::lock_guard<std::mutex> g(h->mu);
     cudaSetDevice(h->device);
     std::vector<uint64_t> ids;
-    eg_status s = run_jobs(h, jobs, static_cast<cudaStream_t>(stream), ids, h->cfg);
+    const bool graph = !(h->cfg.flags & EG_FLAG_NO_GRAPH);
+    eg_status s = run_jobs(h, jobs, static_cast<cudaStream_t>(stream), ids, h->cfg, graph);
     if (s == EG_OK)
         for (int i = 0; i < n; i++) out_ids[i] = ids[i];
     return s;

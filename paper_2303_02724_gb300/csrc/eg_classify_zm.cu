@@ -470,6 +470,27 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
     }
 }
 
+cudaError_t prepare_classify_zm()
+{
+    // allow the opt-in maximum of dynamic shared memory, once per device
+    static std::atomic<uint64_t> done_mask{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = 1ull << (dev & 63);
+    if (done_mask.load() & bit) return cudaSuccess;
+    int optin = 0;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+    for (auto kern : {k_classify_zm<false>, k_classify_zm<true>}) {
+        cudaFuncAttributes fa{};
+        if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
+        const int dyn = optin - int(fa.sharedSizeBytes);
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn)) != cudaSuccess) return e;
+    }
+    done_mask.fetch_or(bit);
+    return cudaSuccess;
+}
+
 size_t zm_smem_bytes(uint32_t n0, uint32_t ty) { return size_t(4) * zm_ring_floats(n0, ty) * sizeof(float); }
 
 cudaError_t launch_classify_zm(bool minimum, const FieldDev *fields, int nf, uint64_t total_items, size_t smem,
@@ -478,21 +499,8 @@ cudaError_t launch_classify_zm(bool minimum, const FieldDev *fields, int nf, uin
 {
     if (total_items == 0) return cudaSuccess;
     auto kern = minimum ? k_classify_zm<true> : k_classify_zm<false>;
-    // allow the opt-in maximum of dynamic shared memory, once per device
-    static std::atomic<uint64_t> done_mask[2];
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    cudaError_t e = prepare_classify_zm();
     if (e != cudaSuccess) return e;
-    const uint64_t bit = 1ull << (dev & 63);
-    if (!(done_mask[minimum].load() & bit)) {
-        int optin = 0;
-        cudaFuncAttributes fa{};
-        if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
-        if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
-        const int dyn = optin - int(fa.sharedSizeBytes);
-        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn)) != cudaSuccess) return e;
-        done_mask[minimum].fetch_or(bit);
-    }
     // (the row layout bounds the ring at 4 x (4 rows x 1032 + 16) floats = 66 KB)
     uint64_t grid = uint64_t(sm_count > 0 ? sm_count : 1) * uint64_t(ctas_per_sm > 0 ? ctas_per_sm : 3);
     if (grid > total_items) grid = total_items;

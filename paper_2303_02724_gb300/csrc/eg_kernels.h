@@ -20,6 +20,12 @@ cudaError_t launch_classify_zm(bool minimum, const FieldDev *fields, int nf, uin
                                const uint32_t *lut, unsigned long long *ticket, int sm_count, int ctas_per_sm,
                                cudaStream_t st);
 
+// Zero the totals and status word of every field of a launch.
+cudaError_t launch_init_fields(const FieldDev *fields, int nf, cudaStream_t st);
+// Set the classifier's shared-memory attribute on the current device (also
+// done lazily by launch_classify_zm; call it before capturing a graph).
+cudaError_t prepare_classify_zm();
+
 // Scan A (arcs = false) / scan B (arcs = true) over all bricks of all fields.
 uint64_t scan_tiles(uint32_t nbricks);
 size_t scan_workspace_bytes(uint64_t total_tiles);

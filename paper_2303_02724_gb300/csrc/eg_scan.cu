@@ -131,6 +131,24 @@ k_scan_bricks(const FieldDev *__restrict__ fields, int nf, uint64_t total_tiles,
     }
 }
 
+// Zero every field's totals and status word (through the descriptor table, so
+// a captured graph can replay it for new result buffers).
+__global__ void k_init_fields(const FieldDev *__restrict__ fields, int nf)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf) return;
+    const FieldDev &F = fields[i];
+    F.totals[0] = F.totals[1] = F.totals[2] = F.totals[3] = 0;
+    *F.err = 0;
+}
+
+cudaError_t launch_init_fields(const FieldDev *fields, int nf, cudaStream_t st)
+{
+    if (nf <= 0) return cudaSuccess;
+    k_init_fields<<<dim3(unsigned((nf + 127) / 128)), 128, 0, st>>>(fields, nf);
+    return cudaGetLastError();
+}
+
 uint64_t scan_tiles(uint32_t nbricks) { return (uint64_t(nbricks) + kScanTile - 1) / kScanTile; }
 
 size_t scan_workspace_bytes(uint64_t total_tiles) { return 256 + 4 * total_tiles * sizeof(uint64_t); }

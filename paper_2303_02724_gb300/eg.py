@@ -22,6 +22,7 @@ EG_OK, EG_ERR_ARG, EG_ERR_NAN, EG_ERR_OOM, EG_ERR_CUDA = 0, 1, 2, 3, 4
 EG_ERR_NOT_CONVERGED, EG_ERR_TIMEOUT, EG_ERR_BUSY, EG_ERR_INTERNAL = 5, 6, 7, 8
 EG_FLAG_MINIMUM_GRAPH = 0x1
 EG_FLAG_NO_LABELS = 0x2
+EG_FLAG_NO_GRAPH = 0x4
 
 
 class EGError(RuntimeError):

@@ -196,3 +196,24 @@ def test_autotune_keeps_parity():
             g = h.get_graph(rid)
             h.release(rid)
             assert_same(g, oracle.compute(x.values))
+
+
+def test_batch_graph_replay_with_new_fields():
+    """The second and later batches with the same layout replay captured
+    graphs; new field pointers and new result buffers must reach the kernels."""
+    from paper_2303_02724_gb300 import eg
+    shapes = [(33, 29, 17), (64, 50), (40, 36, 32), (300,)]
+    with eg.Handle(0) as h, eg.Handle(0, config=eg.EGConfig(flags=eg.EG_FLAG_NO_GRAPH)) as hd:
+        for seed in range(3):
+            flds = [F.white_noise(s, 100 * seed + i) for i, s in enumerate(shapes)]
+            ts = [torch.from_numpy(x.values).cuda() for x in flds]
+            ids = h.batch_submit(ts)
+            idd = hd.batch_submit(ts)
+            for x, rid, rd in zip(flds, ids, idd):
+                g = h.get_graph(rid)
+                gd = hd.get_graph(rd)
+                h.release(rid)
+                hd.release(rd)
+                o = oracle.compute(x.values)
+                assert_same(g, o)
+                assert_same(gd, o)
