@@ -230,6 +230,12 @@ EG_API uint64_t eg_launch_count(eg_handle h);
  * EG_ERR_OOM (k = 0 disables).  Host-side fault injection only. */
 EG_API eg_status eg_debug_fail_alloc(eg_handle h, int k);
 
+/* Test hook: run one bounded device-side wait (the look-back used by the
+ * scans) on a predecessor that never publishes.  The wait gives up after its
+ * spin budget (about a second) and the call returns EG_ERR_TIMEOUT; the CUDA
+ * context stays usable.  Blocks until done. */
+EG_API eg_status eg_debug_wait_timeout(eg_handle h, void *stream);
+
 /* Human-readable name of a status code (static string). */
 EG_API const char *eg_status_str(eg_status s);
 

@@ -1197,6 +1197,27 @@ eg_status eg_step_times(eg_handle h, eg_result_id id, float ms[4])
 
 uint64_t eg_launch_count(eg_handle h) { return h ? h->launches.load() : 0; }
 
+eg_status eg_debug_wait_timeout(eg_handle h, void *stream)
+{
+    if (!h) return EG_ERR_ARG;
+    std::lock_guard<std::mutex> g(h->mu);
+    cudaSetDevice(h->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    void *buf = nullptr;
+    cudaError_t e = h->pool.alloc(&buf, 256);
+    if (e != cudaSuccess) return from_cuda(e);
+    uint64_t *status = static_cast<uint64_t *>(buf);   // two look-back words, both empty
+    uint32_t *err = reinterpret_cast<uint32_t *>(static_cast<char *>(buf) + 64);
+    uint32_t herr = 0;
+    e = cudaMemsetAsync(buf, 0, 256, st);
+    if (e == cudaSuccess) e = launch_lookback_orphan(status, err, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    h->pool.release(buf);
+    if (e != cudaSuccess) return from_cuda(e);
+    return (herr & kErrTimeout) ? EG_ERR_TIMEOUT : EG_OK;
+}
+
 eg_status eg_debug_fail_alloc(eg_handle h, int k)
 {
     if (!h || k < 0) return EG_ERR_ARG;

@@ -26,6 +26,9 @@ cudaError_t launch_init_fields(const FieldDev *fields, int nf, cudaStream_t st);
 // done lazily by launch_classify_zm; call it before capturing a graph).
 cudaError_t prepare_classify_zm();
 
+// Test hook: a look-back wait whose predecessor never publishes.
+cudaError_t launch_lookback_orphan(uint64_t *st, uint32_t *err, cudaStream_t s);
+
 // Scan A (arcs = false) / scan B (arcs = true) over all bricks of all fields.
 uint64_t scan_tiles(uint32_t nbricks);
 size_t scan_workspace_bytes(uint64_t total_tiles);

@@ -149,6 +149,19 @@ cudaError_t launch_init_fields(const FieldDev *fields, int nf, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// Test hook: one warp waits, through the look-back, for a predecessor that
+// never publishes; the bounded wait must give up and report kErrTimeout.
+__global__ void k_lookback_orphan(uint64_t *st, uint32_t *err)
+{
+    warp_lookback(st, 1, 0, 1, err);
+}
+
+cudaError_t launch_lookback_orphan(uint64_t *st, uint32_t *err, cudaStream_t s)
+{
+    k_lookback_orphan<<<1, 32, 0, s>>>(st, err);
+    return cudaGetLastError();
+}
+
 uint64_t scan_tiles(uint32_t nbricks) { return (uint64_t(nbricks) + kScanTile - 1) / kScanTile; }
 
 size_t scan_workspace_bytes(uint64_t total_tiles) { return 256 + 4 * total_tiles * sizeof(uint64_t); }

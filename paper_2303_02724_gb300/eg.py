@@ -79,6 +79,7 @@ SIGNATURES = {
     "eg_step_times": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_float)]),
     "eg_launch_count": (ctypes.c_uint64, [_P]),
     "eg_debug_fail_alloc": (ctypes.c_int, [_P, ctypes.c_int]),
+    "eg_debug_wait_timeout": (ctypes.c_int, [_P, _P]),
     "eg_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "eg_labels_static": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_uint32, _P, _P]),
     "eg_autotune": (ctypes.c_int, [_P, ctypes.POINTER(EGFieldDesc), ctypes.c_int, _P, ctypes.POINTER(EGConfig)]),
@@ -295,6 +296,10 @@ class Handle:
 
     def debug_fail_alloc(self, k: int):
         _check(self._lib.eg_debug_fail_alloc(self._h, int(k)), "eg_debug_fail_alloc")
+
+    def debug_wait_timeout(self, stream=None) -> int:
+        """Status of a device wait that is made to run out (EG_ERR_TIMEOUT)."""
+        return int(self._lib.eg_debug_wait_timeout(self._h, ctypes.c_void_p(_stream_ptr(stream))))
 
     # ------------------------------------------------------------- one shot
     def graph_of(self, field, labels: bool = True, stream=None) -> Graph:
