@@ -41,14 +41,22 @@ def _headers():
     return sorted(hs)
 
 
-def _fingerprint() -> str:
+def _fingerprint(files=None) -> str:
+    """SHA-256 over file names (not paths: the tree moves between machines),
+    contents and compiler flags.  Default: every source and header."""
     h = hashlib.sha256()
-    for p in sources() + _headers():
-        h.update(p.encode())
+    for p in (sources() + _headers()) if files is None else files:
+        h.update(os.path.basename(p).encode())
         with open(p, "rb") as f:
             h.update(f.read())
     h.update(" ".join(ARCH + NVCC_FLAGS).encode())
     return h.hexdigest()
+
+
+def kernel_fingerprint(source: str) -> str:
+    """Fingerprint of one translation unit (basename under csrc/) and the
+    headers every unit includes: it changes when that kernel's code does."""
+    return _fingerprint([os.path.join(CSRC, source)] + _headers())
 
 
 def build(force: bool = False, verbose: bool = False) -> str:

@@ -4,22 +4,24 @@
 // A CTA owns `ty` whole rows of the grid (a row block) and marches along the
 // slowest axis over `zc` planes.  A ring of four plane buffers in shared
 // memory holds planes z-1, z, z+1 while plane z+2 streams in with cp.async;
-// each buffer holds rows y0-1 .. y0+ty of one plane, each row padded by four
-// NaN on both sides.  Out-of-domain rows and planes are NaN as well, and every
-// ordered comparison with NaN is false, so no bounds test is needed: a NaN
-// neighbour is never upper, never the maximum, never equal.
+// each buffer holds rows y0-1 .. y0+ty of one plane, rows separated by eight
+// NaN.  Out-of-domain rows and planes are NaN as well, and NaN fails every
+// ordered comparison, is skipped by min/max and equals nothing, so no bounds
+// test is needed.
 //
-// Each thread classifies a 4 x 2 block of vertices (x..x+3, y..y+1) of plane z
-// from register copies of the 10 row segments the block's 14-neighbourhoods
-// touch.  Per vertex:
+// Each thread classifies 8 consecutive vertices of one row of plane z from
+// register copies of the 7 row segments their 14-neighbourhoods touch.  Per
+// vertex:
 //   upper   bit k set iff neighbour k is higher (value, then index: ties go to
-//           the positive slots, which have larger indices);
-//   asc     the highest neighbour: max value, ties to the highest slot rank;
-//   saddle  beta0+ >= 2, looked up in a 2^14-bit table indexed by the upper
-//           mask (built on the host from the link graph); the components and
-//           their highest vertices (UpperLinkRep, Sec. 3.4) are then found by
-//           flood fill, for saddles only.
-// The minimum graph negates every value and swaps the tie rule.
+//           the positive slots, which have larger indices); 14 set-compares
+//           whose 0/1 results are accumulated with FMAs;
+//   asc     the highest neighbour: the largest value (three-operand max), then
+//           the highest slot rank holding it;
+//   saddle  beta0+ >= 2, looked up in a table of 2-bit classes indexed by the
+//           upper mask (built on the host from the link graph); the components
+//           and their highest vertices (UpperLinkRep, Sec. 3.4) are then found
+//           by flood fill, for saddles only, after the plane.
+// The minimum graph mirrors every comparison and the tie rule.
 //
 // One row block of one plane is one brick (contiguous ids): its maxima and
 // saddles go, in index order, to the brick's record slot; asc goes to lab.
@@ -61,41 +63,121 @@ __host__ __device__ __forceinline__ uint32_t zm_ring_floats(uint32_t n0, uint32_
     return ((ty + 2) * (n0 + 8) + 16 + 3) & ~3u;
 }
 
+// This thread's first copy unit (row r0, unit c0 of the row) and the stride
+// between its units (dr rows + dc units), for units of 16 bytes (vec) or 4
+// bytes per row; fixed for a work item, so no division per plane.
+struct ZmCopy {
+    uint32_t r0, c0, dr, dc, upr;
+};
+
+__device__ __forceinline__ ZmCopy zm_copy_plan(uint32_t n0, bool vec)
+{
+    ZmCopy P;
+    P.upr = vec ? (n0 >> 2) : n0;
+    P.r0 = uint32_t(threadIdx.x) / P.upr;
+    P.c0 = uint32_t(threadIdx.x) - P.r0 * P.upr;
+    P.dr = uint32_t(kZmThreads) / P.upr;
+    P.dc = uint32_t(kZmThreads) - P.dr * P.upr;
+    return P;
+}
+
 // Stream rows [ylo, yhi) of plane z into ring slot `buf` (or NaN-fill the slot
 // when z is past the last plane).  Always commits one cp.async group.
-__device__ __forceinline__ void zm_load_plane(const FieldDev &F, const ZmGeom &G, float *buf, int z, uint32_t y0,
-                                              uint32_t ylo, uint32_t yhi, bool vec)
+__device__ __forceinline__ void zm_load_plane(const FieldDev &F, const ZmGeom &G, const ZmCopy &P, float *buf, int z,
+                                              uint32_t y0, uint32_t ylo, uint32_t yhi, bool vec)
 {
-    const int tid = threadIdx.x;
     const uint32_t rows = yhi - ylo;
     float *dst0 = buf + 8 + (ylo - y0 + 1) * G.rstride;
     if (z < 0) {
         cp_async_commit();
         return;
     }
-    if (uint32_t(z) >= G.n2) {
-        const float qnan = __int_as_float(0x7fc00000);
-        for (uint32_t c = tid; c < rows * G.n0; c += kZmThreads) {
-            const uint32_t r = c / G.n0, x = c - r * G.n0;
-            dst0[r * G.rstride + x] = qnan;
+    const bool fill = uint32_t(z) >= G.n2;
+    const float *src0 = F.f + (uint64_t(fill ? 0 : z) * G.n1 + ylo) * G.n0;
+    const uint32_t w = vec ? 4u : 1u;  // floats per unit
+    for (uint32_t r = P.r0, c = P.c0; r < rows;) {
+        float *d = dst0 + r * G.rstride + w * c;
+        if (fill) {
+            const float qnan = __int_as_float(0x7fc00000);
+            if (vec)
+                *reinterpret_cast<float4 *>(d) = make_float4(qnan, qnan, qnan, qnan);
+            else
+                *d = qnan;
+        } else {
+            const float *g = src0 + uint64_t(r) * G.n0 + w * c;
+            if (vec)
+                cp_async16(d, g);
+            else
+                cp_async4(d, g);
         }
-        cp_async_commit();
-        return;
-    }
-    const float *src0 = F.f + (uint64_t(z) * G.n1 + ylo) * G.n0;
-    if (vec) {
-        const uint32_t cpr = G.n0 >> 2;
-        for (uint32_t c = tid; c < rows * cpr; c += kZmThreads) {
-            const uint32_t r = c / cpr, c4 = c - r * cpr;
-            cp_async16(dst0 + r * G.rstride + 4 * c4, src0 + uint64_t(r) * G.n0 + 4 * c4);
-        }
-    } else {
-        for (uint32_t c = tid; c < rows * G.n0; c += kZmThreads) {
-            const uint32_t r = c / G.n0, x = c - r * G.n0;
-            cp_async4(dst0 + r * G.rstride + x, src0 + uint64_t(r) * G.n0 + x);
+        r += P.dr;
+        c += P.dc;
+        if (c >= P.upr) {
+            c -= P.upr;
+            r++;
         }
     }
     cp_async_commit();
+}
+
+// Float comparisons that return 1.0f / 0.0f (false for NaN operands).
+__device__ __forceinline__ float set_gt(float a, float b)
+{
+    float d;
+    asm("set.gt.f32.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+__device__ __forceinline__ float set_ge(float a, float b)
+{
+    float d;
+    asm("set.ge.f32.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+__device__ __forceinline__ float set_lt(float a, float b)
+{
+    float d;
+    asm("set.lt.f32.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+__device__ __forceinline__ float set_le(float a, float b)
+{
+    float d;
+    asm("set.le.f32.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+__device__ __forceinline__ float set_eq(float a, float b)
+{
+    float d;
+    asm("set.eq.f32.f32 %0, %1, %2;" : "=f"(d) : "f"(a), "f"(b));
+    return d;
+}
+
+// Three-operand max / min (NaN operands are ignored unless all are NaN).
+__device__ __forceinline__ float max3f(float a, float b, float c)
+{
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ float min3f(float a, float b, float c)
+{
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// Largest / smallest of 14 values in seven three-operand steps.
+__device__ __forceinline__ float max7x2(const float (&v)[14])
+{
+    const float a = max3f(v[0], v[1], v[2]), b = max3f(v[3], v[4], v[5]);
+    const float c = max3f(v[6], v[7], v[8]), d = max3f(v[9], v[10], v[11]);
+    return fmaxf(max3f(a, b, v[12]), max3f(c, d, v[13]));
+}
+__device__ __forceinline__ float min7x2(const float (&v)[14])
+{
+    const float a = min3f(v[0], v[1], v[2]), b = min3f(v[3], v[4], v[5]);
+    const float c = min3f(v[6], v[7], v[8]), d = min3f(v[9], v[10], v[11]);
+    return fminf(min3f(a, b, v[12]), min3f(c, d, v[13]));
 }
 
 // Value as the comparisons see it: negated for the minimum graph.
@@ -175,13 +257,6 @@ __device__ __forceinline__ void gather_nb(const float *Db, const float *Cb, cons
 
 constexpr int kSaddleQueue = 1024;
 constexpr int kVx = 8;  // vertices per thread along axis 0
-// slots (see the order below) whose offset has a -x / +x / -y / +y / -z / +z component
-constexpr uint32_t kNegX = (1u << 0) | (1u << 2) | (1u << 4) | (1u << 6);
-constexpr uint32_t kPosX = (1u << 7) | (1u << 9) | (1u << 11) | (1u << 13);
-constexpr uint32_t kNegY = (1u << 0) | (1u << 1) | (1u << 4) | (1u << 5);
-constexpr uint32_t kPosY = (1u << 8) | (1u << 9) | (1u << 12) | (1u << 13);
-constexpr uint32_t kNegZ = (1u << 0) | (1u << 1) | (1u << 2) | (1u << 3);
-constexpr uint32_t kPosZ = (1u << 10) | (1u << 11) | (1u << 12) | (1u << 13);
 
 template <bool MIN>
 __global__ void __launch_bounds__(kZmThreads, 3)
@@ -226,6 +301,7 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
     const int zs = int(zci * F.zc);
     const int ze = int(min(G.n2, zci * F.zc + F.zc));
     const bool vec = F.vec != 0;
+    const ZmCopy P = zm_copy_plan(G.n0, vec);
 
     if (tid < 14) {
         const uint32_t p = Nbr<3>::pat(tid);
@@ -239,9 +315,9 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
     }
     __syncthreads();
 
-    zm_load_plane(F, G, ring + ((zs - 1) & 3) * G.rb, zs - 1, y0, ylo, yhi, vec);
-    zm_load_plane(F, G, ring + (zs & 3) * G.rb, zs, y0, ylo, yhi, vec);
-    zm_load_plane(F, G, ring + ((zs + 1) & 3) * G.rb, zs + 1, y0, ylo, yhi, vec);
+    zm_load_plane(F, G, P, ring + ((zs - 1) & 3) * G.rb, zs - 1, y0, ylo, yhi, vec);
+    zm_load_plane(F, G, P, ring + (zs & 3) * G.rb, zs, y0, ylo, yhi, vec);
+    zm_load_plane(F, G, P, ring + ((zs + 1) & 3) * G.rb, zs + 1, y0, ylo, yhi, vec);
 
     // thread t owns vertices x .. x+7 of brick row r; threads are in (row, x)
     // order, which is the brick's index order
@@ -260,7 +336,7 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
             F.bcnt[prev_brick] = make_uint4(s_cnt[0], s_cnt[1] - s_cnt[0], s_cnt[2], 0u);
             s_cnt[0] = s_cnt[1] = s_cnt[2] = s_cnt[3] = 0;
         }
-        zm_load_plane(F, G, ring + ((z + 2) & 3) * G.rb, z + 2, y0, ylo, yhi, vec);
+        zm_load_plane(F, G, P, ring + ((z + 2) & 3) * G.rb, z + 2, y0, ylo, yhi, vec);
         cp_async_wait1();
         __syncthreads();  // B: plane z+1 visible, counters reset
 
@@ -273,17 +349,9 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
         const uint32_t vrow = uint32_t((uint64_t(z) * G.n1 + y0 + r) * G.n0) + x;
         uint32_t um[kVx];  // upper mask | gradient slot << 14 | class << 18
         uint32_t crit = 0, nm = 0;
-        // in-bounds slots (NaN pads already fail every ordered comparison; the
-        // mask keeps the result independent of that)
-        const uint32_t gy = y0 + r;
-        uint32_t out = 0;
-        if (gy == 0) out |= kNegY;
-        if (gy + 1 >= G.n1) out |= kPosY;
-        if (z == 0) out |= kNegZ;
-        if (uint32_t(z) + 1 >= G.n2) out |= kPosZ;
-        const uint32_t inbm = ~out & 0x3fffu;
-        const uint32_t inb0 = x == 0 ? (inbm & ~kNegX) : inbm;
-        // ---- phase 1: gradient pointer, upper mask, saddle test
+        // ---- phase 1: gradient pointer, upper mask, saddle test.  Out-of-domain
+        // neighbours read NaN pads, which fail every ordered comparison, are
+        // ignored by min/max and never equal anything.
         if (rowok) {
             // row segments: C rows r-1..r+1 at x-1..x+8, D rows r-1..r at
             // x-1..x+7, U rows r..r+1 at x..x+8 (ring rows are r-1+1 .. )
@@ -329,50 +397,41 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
             uint32_t asc[kVx];
 #pragma unroll
             for (int i = 0; i < kVx; i++) {
-                const float cr = C[1][i + 1];
-                const float c = zv<MIN>(cr);
+                const float c = C[1][i + 1];
                 // slot order: (-1,-1,-1) (0,-1,-1) (-1,0,-1) (0,0,-1) (-1,-1,0) (0,-1,0)
                 // (-1,0,0) | (1,0,0) (0,1,0) (1,1,0) (0,0,1) (1,0,1) (0,1,1) (1,1,1)
-                const float nb[14] = {zv<MIN>(D[0][i]),     zv<MIN>(D[0][i + 1]), zv<MIN>(D[1][i]),
-                                      zv<MIN>(D[1][i + 1]), zv<MIN>(C[0][i]),     zv<MIN>(C[0][i + 1]),
-                                      zv<MIN>(C[1][i]),     zv<MIN>(C[1][i + 2]), zv<MIN>(C[2][i + 1]),
-                                      zv<MIN>(C[2][i + 2]), zv<MIN>(U[0][i]),     zv<MIN>(U[0][i + 1]),
-                                      zv<MIN>(U[1][i]),     zv<MIN>(U[1][i + 1])};
+                const float nb[14] = {D[0][i], D[0][i + 1], D[1][i], D[1][i + 1], C[0][i],     C[0][i + 1],
+                                      C[1][i], C[1][i + 2], C[2][i + 1], C[2][i + 2], U[0][i], U[0][i + 1],
+                                      U[1][i], U[1][i + 1]};
                 // upper: negative slots (smaller index) need a strictly higher
                 // value, positive slots a higher or equal one (maximum graph); the
-                // minimum graph swaps the two rules.  NaN (outside) is never upper.
-                uint32_t upper = 0;
+                // minimum graph mirrors both.  Each test yields 0.0 or 1.0 and is
+                // accumulated as bit k of a float whose exponent pins the
+                // integer part (2^23 + mask is exact), on the FMA pipe.
+                float au = 8388608.f;
 #pragma unroll
                 for (int k = 0; k < 14; k++) {
-                    const bool up = (k < 7) == MIN ? (nb[k] >= c) : (nb[k] > c);
-                    upper |= up ? (1u << k) : 0u;
+                    const float t = MIN ? (k < 7 ? set_le(nb[k], c) : set_lt(nb[k], c))
+                                        : (k < 7 ? set_gt(nb[k], c) : set_ge(nb[k], c));
+                    au = __fmaf_rn(t, float(1u << k), au);
                 }
-                // gradient: tournament in rank order, ties to the higher rank
-                // (maximum graph) or the lower rank (minimum graph)
-                uint32_t eq;
-                {
-                    float best = -__int_as_float(0x7f800000);
-                    int bk = 0;
+                uint32_t upper = __float_as_uint(au) & 0x3fffu;
+                // gradient: the extreme neighbour value, then the highest (maximum
+                // graph) or lowest (minimum graph) slot holding it among the upper
+                // neighbours
+                const float m = MIN ? min7x2(nb) : max7x2(nb);
+                float ae = 8388608.f;
 #pragma unroll
-                    for (int q = 0; q < 14; q++) {
-                        const int k = MIN ? 13 - q : q;
-                        const bool w = nb[k] >= best;
-                        best = w ? nb[k] : best;
-                        bk = w ? k : bk;
-                    }
-                    eq = 1u << bk;
-                }
-                uint32_t inb = i == 0 ? inb0 : inbm;
-                if (x + kVx >= G.n0 && x + i + 1 >= G.n0) inb &= ~kPosX;
-                upper &= inb;
-                eq &= inb;
+                for (int k = 0; k < 14; k++) ae = __fmaf_rn(set_eq(nb[k], m), float(1u << k), ae);
+                const uint32_t eq = __float_as_uint(ae) & 0x3fffu;
                 const bool ok = x + i < G.n0;
                 const uint32_t v = vrow + i;
                 uint32_t a = v;
                 bool cv = false;
                 uint32_t cls = 0, slot = 0;
                 if (upper) {
-                    const uint32_t cand = eq & upper;
+                    uint32_t cand = eq & upper;
+                    cand = cand ? cand : upper;  // (never empty; keeps the slot in range)
                     slot = MIN ? uint32_t(__ffs(cand) - 1) : uint32_t(31 - __clz(cand));
                     a = v + s_off[slot];
                     cls = (s_lut[upper >> 4] >> ((upper & 15) << 1)) & 3u;
@@ -380,13 +439,11 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
                 } else {
                     cv = true;
                     nm += ok ? 1u : 0u;
+                    anynan |= ok && (c != c);  // a NaN value has no upper neighbour
                 }
                 asc[i] = a;
                 um[i] = upper | (slot << 14) | (cls << 18);
-                if (ok) {
-                    anynan |= (cr != cr);
-                    crit |= cv ? (1u << i) : 0u;
-                }
+                if (ok) crit |= cv ? (1u << i) : 0u;
             }
             uint32_t *dst = F.lab + vrow;
             if (vec) {
