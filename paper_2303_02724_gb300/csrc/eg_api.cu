@@ -192,7 +192,7 @@ struct eg_ctx {
     uint64_t ws_bricks = 0;
     void *ws_scan = nullptr;
     uint64_t ws_tiles = 0;
-    void *lut3 = nullptr;  // 2^14-bit saddle table of the 3D link graph
+    void *lut3 = nullptr;  // saddle class table of the 3D link graph + two-component table
     void *stage = nullptr;  // device staging for eg_compute_host
     size_t stage_bytes = 0;
     void *hstage = nullptr;  // pinned staging for pageable host fields
@@ -839,10 +839,12 @@ eg_status eg_create(eg_handle *out, int device, const eg_config *cfg)
     {
         // saddle table of the 3D neighbourhood, 2 bits per upper-link mask m (14
         // neighbour slots): 0 fewer than two connected components, 1 exactly
-        // two, 2 three or more
-        std::vector<uint32_t> lut(1024, 0u);
+        // two, 2 three or more; then, as 16-bit words, the component holding
+        // the lowest set bit of every two-component mask
+        std::vector<uint32_t> lut(1024 + 8192, 0u);
+        uint16_t *comp2 = reinterpret_cast<uint16_t *>(lut.data() + 1024);
         for (uint32_t m = 0; m < (1u << 14); m++) {
-            uint32_t left = m, comps = 0;
+            uint32_t left = m, comps = 0, first_comp = 0;
             while (left) {
                 uint32_t comp = left & (~left + 1u), grow = comp;
                 while (grow) {
@@ -853,10 +855,12 @@ eg_status eg_create(eg_handle *out, int device, const eg_config *cfg)
                     grow |= nb;
                 }
                 left &= ~comp;
+                if (comps == 0) first_comp = comp;
                 comps++;
             }
             const uint32_t cls = comps < 2 ? 0u : (comps == 2 ? 1u : 2u);
             lut[m >> 4] |= cls << ((m & 15) * 2);
+            if (comps == 2) comp2[m] = uint16_t(first_comp);
         }
         if ((e = h->pool.alloc(&h->lut3, lut.size() * 4)) != cudaSuccess) return from_cuda(e);
         if ((e = cudaMemcpy(h->lut3, lut.data(), lut.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)

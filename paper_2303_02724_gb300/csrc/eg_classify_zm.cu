@@ -23,8 +23,11 @@
 //           by flood fill, for saddles only, after the plane.
 // The minimum graph mirrors every comparison and the tie rule.
 //
-// One row block of one plane is one brick (contiguous ids): its maxima and
-// saddles go, in index order, to the brick's record slot; asc goes to lab.
+// One row block of one plane is one brick (contiguous ids): asc goes to lab;
+// its maxima and saddles go, in index order, to the brick's record slot.  The
+// records are written by each warp cooperatively after a block scan of the
+// counts: lane j writes the warp's j-th record (coalesced) and, for a saddle,
+// also resolves its components, so the saddle work is spread over the lanes.
 #include <atomic>
 
 #include "eg_internal.cuh"
@@ -55,13 +58,21 @@ struct ZmGeom {
     uint32_t n0, n1, n2, ty, rstride, rb;
 };
 
-// Ring buffer: rows of n0 values separated by 8 NaN (each row's trailing pad is
-// the next row's leading pad), 8 more at each end; a thread reads columns
-// x-1 .. x+8 with x < n0, so every read stays inside its buffer.
+// Ring buffer: rows of n0 values rounded up to a multiple of 8 and followed by
+// 8 NaN (each row's trailing pad is the next row's leading pad), 8 more at each
+// end; reads of columns -1 .. n0+7 stay inside the buffer.
+__host__ __device__ __forceinline__ uint32_t zm_rstride(uint32_t n0) { return ((n0 + 7) & ~7u) + 8; }
+
 __host__ __device__ __forceinline__ uint32_t zm_ring_floats(uint32_t n0, uint32_t ty)
 {
-    return ((ty + 2) * (n0 + 8) + 16 + 3) & ~3u;
+    return ((ty + 2) * zm_rstride(n0) + 16 + 3) & ~3u;
 }
+
+// Stored position of column x in a ring row: in every group of 8 columns the
+// two halves trade places when bit 2 of the group index is set, so that the
+// 16-byte loads of the eight lanes of a quarter-warp (consecutive groups) hit
+// distinct banks.  A permutation inside each group; pads stay pads.
+__device__ __forceinline__ int zm_col(int x) { return x ^ (((x >> 5) & 1) << 2); }
 
 // This thread's first copy unit (row r0, unit c0 of the row) and the stride
 // between its units (dr rows + dc units), for units of 16 bytes (vec) or 4
@@ -96,7 +107,7 @@ __device__ __forceinline__ void zm_load_plane(const FieldDev &F, const ZmGeom &G
     const float *src0 = F.f + (uint64_t(fill ? 0 : z) * G.n1 + ylo) * G.n0;
     const uint32_t w = vec ? 4u : 1u;  // floats per unit
     for (uint32_t r = P.r0, c = P.c0; r < rows;) {
-        float *d = dst0 + r * G.rstride + w * c;
+        float *d = dst0 + r * G.rstride + zm_col(int(w * c));
         if (fill) {
             const float qnan = __int_as_float(0x7fc00000);
             if (vec)
@@ -180,82 +191,57 @@ __device__ __forceinline__ float min7x2(const float (&v)[14])
     return fminf(min3f(a, b, v[12]), min3f(c, d, v[13]));
 }
 
-// Value as the comparisons see it: negated for the minimum graph.
+// Highest slot of `mask` (value, then rank; the minimum graph takes the
+// lowest value and the lowest rank), reading the values straight from the
+// ring: neighbour k of column xx of ring row `row` is at row + roff[k] (plane
+// and row step), column xx + rdx[k].
 template <bool MIN>
-__device__ __forceinline__ float zv(float x)
-{
-    return MIN ? -x : x;
-}
-
-// Highest slot of mask c2 (value, then rank; reversed tie rule for the
-// minimum graph).
-template <bool MIN>
-__device__ __forceinline__ int masked_top(const float (&nb)[14], uint32_t c2)
+__device__ __forceinline__ int masked_top(const float *row, int xx, uint32_t mask, const int *roff, const int *rdx)
 {
     float best = 0.f;
     int rk = -1;
-#pragma unroll
-    for (int k = 0; k < 14; k++)
-        if ((c2 >> k) & 1u)
-            if (rk < 0 || (MIN ? nb[k] > best : nb[k] >= best)) {
-                best = nb[k];
-                rk = k;
-            }
+    while (mask) {
+        const int k = __ffs(mask) - 1;
+        mask &= mask - 1u;
+        const float v = row[roff[k] + zm_col(xx + rdx[k])];
+        if (rk < 0 || (MIN ? v < best : v >= best)) {
+            best = v;
+            rk = k;
+        }
+    }
     return rk;
 }
 
 // Upper-link components of one saddle and the highest vertex of each
 // (UpperLinkRep, Sec. 3.4), packed as 5-bit slots with beta0+ in bits 56..59.
-// first: the gradient slot (highest of all upper neighbours); cls: 1 when the
-// table says exactly two components, so the second is the rest of the mask.
+// first: the gradient slot (highest of all upper neighbours, hence the
+// representative of its component); cls: 1 when the table says exactly two
+// components.  comp2[m]: for a mask with exactly two components, the
+// component holding the lowest set bit (host-built table).
 template <bool MIN>
-__device__ __forceinline__ uint64_t saddle_info(const float (&nb)[14], uint32_t upper, int first, uint32_t cls,
-                                                const uint32_t *s_adj)
+__device__ __forceinline__ uint64_t saddle_info(const float *row, int xx, const int *roff, const int *rdx,
+                                                uint32_t upper, int first, uint32_t cls, const uint32_t *s_adj,
+                                                const uint16_t *comp2)
 {
-    const uint32_t comp = link_flood(1u << first, upper, s_adj);
     uint64_t codes = uint64_t(first);
-    int b0 = 1;
-    uint32_t left = upper & ~comp;
     if (cls == 1) {
-        codes |= uint64_t(masked_top<MIN>(nb, left)) << 5;
+        const uint32_t a = __ldg(comp2 + upper);
+        const uint32_t other = ((a >> first) & 1u) ? (upper ^ a) : a;
+        codes |= uint64_t(masked_top<MIN>(row, xx, other, roff, rdx)) << 5;
         return (2ull << 56) | codes;
     }
+    const uint32_t comp = link_flood(1u << first, upper, s_adj);
+    int b0 = 1;
+    uint32_t left = upper & ~comp;
     while (left) {
         const uint32_t c2 = link_flood(left & (~left + 1u), upper, s_adj);
         left &= ~c2;
-        codes |= uint64_t(masked_top<MIN>(nb, c2)) << (5 * b0);
+        codes |= uint64_t(masked_top<MIN>(row, xx, c2, roff, rdx)) << (5 * b0);
         b0++;
     }
     return (uint64_t(b0) << 56) | codes;
 }
 
-// The 14 neighbour values of ring position (row r, column x) of plane buffers
-// D (z-1), C (z), U (z+1), in slot order.
-template <bool MIN>
-__device__ __forceinline__ void gather_nb(const float *Db, const float *Cb, const float *Ub, uint32_t rs, uint32_t r,
-                                          uint32_t x, float (&nb)[14], float &c)
-{
-    const float *d0 = Db + (r - 1) * rs + x, *d1 = Db + r * rs + x;
-    const float *c0 = Cb + (r - 1) * rs + x, *c1 = Cb + r * rs + x, *c2 = Cb + (r + 1) * rs + x;
-    const float *u1 = Ub + r * rs + x, *u2 = Ub + (r + 1) * rs + x;
-    nb[0] = zv<MIN>(d0[-1]);
-    nb[1] = zv<MIN>(d0[0]);
-    nb[2] = zv<MIN>(d1[-1]);
-    nb[3] = zv<MIN>(d1[0]);
-    nb[4] = zv<MIN>(c0[-1]);
-    nb[5] = zv<MIN>(c0[0]);
-    nb[6] = zv<MIN>(c1[-1]);
-    nb[7] = zv<MIN>(c1[1]);
-    nb[8] = zv<MIN>(c2[0]);
-    nb[9] = zv<MIN>(c2[1]);
-    nb[10] = zv<MIN>(u1[0]);
-    nb[11] = zv<MIN>(u1[1]);
-    nb[12] = zv<MIN>(u2[0]);
-    nb[13] = zv<MIN>(u2[1]);
-    c = zv<MIN>(c1[0]);
-}
-
-constexpr int kSaddleQueue = 1024;
 constexpr int kVx = 8;  // vertices per thread along axis 0
 
 template <bool MIN>
@@ -268,12 +254,17 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
     __shared__ uint32_t s_lut[1024];
     __shared__ uint32_t s_adj[14];
     __shared__ uint32_t s_off[14];
+    __shared__ int s_roff[14];  // ring offset (plane, row) of neighbour slot k from the centre row (this step)
+    __shared__ int s_rdx[14];   // column step of neighbour slot k
     __shared__ uint32_t s_warp[kZmThreads / 32];
     __shared__ unsigned s_cnt[4];
-    __shared__ uint2 s_queue[kSaddleQueue];  // (record index, x | ring row << 11 | upper << 18)
+    // per-vertex classification of this step (upper mask | gradient slot << 14 |
+    // class << 18), thread-major, read back by the record writers
+    __shared__ __align__(16) uint32_t s_um[kZmThreads * kVx];
 
     __shared__ unsigned long long s_item;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint16_t *comp2 = reinterpret_cast<const uint16_t *>(lut + 1024);
     for (int i = tid; i < 1024; i += kZmThreads) s_lut[i] = __ldg(lut + i);
     if (tid < 14) s_adj[tid] = Nbr<3>::adj_mask(tid);
     // persistent work queue: take items in ticket order until none are left
@@ -291,7 +282,7 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
     G.n1 = F.n[1];
     G.n2 = F.n[2];
     G.ty = F.ty;
-    G.rstride = G.n0 + 8;
+    G.rstride = zm_rstride(G.n0);
     G.rb = zm_ring_floats(G.n0, G.ty);
     const uint32_t yb = item % F.nyb, zci = item / F.nyb;
     const uint32_t y0 = yb * G.ty;
@@ -331,10 +322,17 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
     uint32_t prev_brick = 0xffffffffu;
 
     for (int z = zs; z < ze; z++) {
-        __syncthreads();  // A: previous step done (ring slot, queue, counters free)
+        __syncthreads();  // A: previous step done (ring slot, counters final)
         if (tid == 0 && prev_brick != 0xffffffffu) {
             F.bcnt[prev_brick] = make_uint4(s_cnt[0], s_cnt[1] - s_cnt[0], s_cnt[2], 0u);
             s_cnt[0] = s_cnt[1] = s_cnt[2] = s_cnt[3] = 0;
+        }
+        if (tid < 14) {
+            const uint32_t p = Nbr<3>::pat(tid);
+            const int plane = (p & 4u) ? int(((Nbr<3>::neg(tid) ? z - 1 : z + 1) & 3) - (z & 3)) * int(G.rb) : 0;
+            const int dy = (p & 2u) ? int(rs) : 0, dx = (p & 1u) ? 1 : 0;
+            s_roff[tid] = plane + (Nbr<3>::neg(tid) ? -dy : dy);
+            s_rdx[tid] = Nbr<3>::neg(tid) ? -dx : dx;
         }
         zm_load_plane(F, G, P, ring + ((z + 2) & 3) * G.rb, z + 2, y0, ylo, yhi, vec);
         cp_async_wait1();
@@ -352,48 +350,58 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
         // ---- phase 1: gradient pointer, upper mask, saddle test.  Out-of-domain
         // neighbours read NaN pads, which fail every ordered comparison, are
         // ignored by min/max and never equal anything.
-        if (rowok) {
-            // row segments: C rows r-1..r+1 at x-1..x+8, D rows r-1..r at
-            // x-1..x+7, U rows r..r+1 at x..x+8 (ring rows are r-1+1 .. )
-            float C[3][kVx + 2], D[2][kVx + 1], U[2][kVx + 1];
-#pragma unroll
-            for (int a = 0; a < 3; a++) {
-                const float *row = Cb + (rr - 1 + a) * rs + x;
-                C[a][0] = row[-1];
+        // row segments: C rows r-1..r+1 at x-1..x+8, D rows r-1..r at
+        // x-1..x+7, U rows r..r+1 at x..x+8.  Every lane loads (lanes without
+        // vertices read ring row 1 and discard it) so that the end columns
+        // can come from the neighbouring lanes.
+        float C[3][kVx + 2], D[2][kVx + 1], U[2][kVx + 1];
+        {
+            const uint32_t rl = rowok ? rr : 1u;
+            const float qnan = __int_as_float(0x7fc00000);
+            const bool first_t = txt == 0, last_t = txt + 1 == txn;
+            // 8 values of columns x..x+7 of ring row `row`
+            auto seg = [&](const float *row, float *v) {
                 if (vec) {
-                    const float4 q0 = *reinterpret_cast<const float4 *>(row);
-                    const float4 q1 = *reinterpret_cast<const float4 *>(row + 4);
-                    C[a][1] = q0.x; C[a][2] = q0.y; C[a][3] = q0.z; C[a][4] = q0.w;
-                    C[a][5] = q1.x; C[a][6] = q1.y; C[a][7] = q1.z; C[a][8] = q1.w;
+                    const uint32_t h = (x >> 3) & 4u;  // stored order of the two halves
+                    const float4 q0 = *reinterpret_cast<const float4 *>(row + x + h);
+                    const float4 q1 = *reinterpret_cast<const float4 *>(row + x + (h ^ 4u));
+                    v[0] = q0.x; v[1] = q0.y; v[2] = q0.z; v[3] = q0.w;
+                    v[4] = q1.x; v[5] = q1.y; v[6] = q1.z; v[7] = q1.w;
                 } else {
 #pragma unroll
-                    for (int b = 0; b < kVx; b++) C[a][1 + b] = row[b];
+                    for (int b = 0; b < kVx; b++) v[b] = row[zm_col(int(x) + b)];
                 }
-                C[a][kVx + 1] = row[kVx];
+            };
+            // column x-1: the left lane's last value, or a load at a warp edge
+            auto left = [&](const float *row, float last) {
+                float l = __shfl_up_sync(0xffffffffu, last, 1);
+                if (lane == 0) l = row[zm_col(int(x) - 1)];
+                return first_t ? qnan : l;
+            };
+            // column x+8: the right lane's first value, or a load at a warp edge
+            auto right = [&](const float *row, float first) {
+                float v = __shfl_down_sync(0xffffffffu, first, 1);
+                if (lane == 31) v = row[zm_col(int(x) + kVx)];
+                return last_t ? qnan : v;
+            };
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                const float *row = Cb + (rl - 1 + a) * rs;
+                seg(row, &C[a][1]);
+                C[a][0] = left(row, C[a][kVx]);
+                C[a][kVx + 1] = right(row, C[a][1]);
             }
 #pragma unroll
             for (int a = 0; a < 2; a++) {
-                const float *drow = Db + (rr - 1 + a) * rs + x;
-                const float *urow = Ub + (rr + a) * rs + x;
-                D[a][0] = drow[-1];
-                if (vec) {
-                    const float4 q0 = *reinterpret_cast<const float4 *>(drow);
-                    const float4 q1 = *reinterpret_cast<const float4 *>(drow + 4);
-                    D[a][1] = q0.x; D[a][2] = q0.y; D[a][3] = q0.z; D[a][4] = q0.w;
-                    D[a][5] = q1.x; D[a][6] = q1.y; D[a][7] = q1.z; D[a][8] = q1.w;
-                    const float4 u0 = *reinterpret_cast<const float4 *>(urow);
-                    const float4 u1 = *reinterpret_cast<const float4 *>(urow + 4);
-                    U[a][0] = u0.x; U[a][1] = u0.y; U[a][2] = u0.z; U[a][3] = u0.w;
-                    U[a][4] = u1.x; U[a][5] = u1.y; U[a][6] = u1.z; U[a][7] = u1.w;
-                } else {
-#pragma unroll
-                    for (int b = 0; b < kVx; b++) {
-                        D[a][1 + b] = drow[b];
-                        U[a][b] = urow[b];
-                    }
-                }
-                U[a][kVx] = urow[kVx];
+                const float *drow = Db + (rl - 1 + a) * rs;
+                const float *urow = Ub + (rl + a) * rs;
+                seg(drow, &D[a][1]);
+                D[a][0] = left(drow, D[a][kVx]);
+                seg(urow, &U[a][0]);
+                U[a][kVx] = right(urow, U[a][0]);
             }
+        }
+        if (rowok) {
             uint32_t asc[kVx];
 #pragma unroll
             for (int i = 0; i < kVx; i++) {
@@ -445,6 +453,9 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
                 um[i] = upper | (slot << 14) | (cls << 18);
                 if (ok) crit |= cv ? (1u << i) : 0u;
             }
+            uint4 *um4 = reinterpret_cast<uint4 *>(s_um + tid * kVx);
+            um4[0] = make_uint4(um[0], um[1], um[2], um[3]);
+            um4[1] = make_uint4(um[4], um[5], um[6], um[7]);
             uint32_t *dst = F.lab + vrow;
             if (vec) {
                 // n0 is a multiple of 4, so x+3 < n0; the second half may be past the row
@@ -468,54 +479,60 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
         nm = __reduce_add_sync(0xffffffffu, nm);
         if (lane == 0 && nm) atomicAdd(&s_cnt[0], nm);
         __syncthreads();  // C: warp totals visible
-        uint32_t pos = inc - cnt;
-        for (int w = 0; w < warp; w++) pos += s_warp[w];
-        uint32_t np = 0;
-        if (crit) {
+        uint32_t pw = 0, tot = 0;  // this warp's first record, the brick's record count
 #pragma unroll
-            for (int i = 0; i < kVx; i++)
-                if ((crit >> i) & 1u) {
-                    const uint64_t q = slot0 + pos;
-                    F.rec_sid[q] = vrow + i;
-                    F.rec_val[q] = Cb[rr * rs + x + i];
-                    const uint32_t upper = um[i] & 0x3fffu, sl = um[i] >> 14;
-                    if (upper == 0) {
-                        F.rec_info[q] = 0;
-                    } else {
-                        const uint32_t at = atomicAdd(&s_cnt[3], 1u);
-                        if (at < kSaddleQueue) {
-                            s_queue[at] = make_uint2(pos | (sl << 16), (x + i) | (rr << 11) | (upper << 18));
-                        } else {
-                            // queue full: resolve this saddle in place
-                            float nb[14], c;
-                            gather_nb<MIN>(Db, Cb, Ub, rs, rr, x + i, nb, c);
-                            const uint64_t inf = saddle_info<MIN>(nb, upper, int(sl & 15u), sl >> 4, s_adj);
-                            F.rec_info[q] = inf;
-                            np += uint32_t(inf >> 56);
-                        }
-                    }
-                    pos++;
-                }
+        for (int w = 0; w < kZmThreads / 32; w++) {
+            const uint32_t t = s_warp[w];
+            pw += w < warp ? t : 0u;
+            tot += t;
         }
-        __syncthreads();  // D: queue complete
-        // ---- phase 2: saddle components, one queued saddle per thread
-        const uint32_t nq = min(s_cnt[3], uint32_t(kSaddleQueue));
-        for (uint32_t e = tid; e < nq; e += kZmThreads) {
-            const uint2 w = s_queue[e];
-            const uint32_t xx = w.y & 0x7ffu, qr = (w.y >> 11) & 0x7fu, upper = w.y >> 18;
-            float nb[14], c;
-            gather_nb<MIN>(Db, Cb, Ub, rs, qr, xx, nb, c);
-            const uint64_t inf = saddle_info<MIN>(nb, upper, int((w.x >> 16) & 15u), (w.x >> 20) & 3u, s_adj);
-            F.rec_info[slot0 + (w.x & 0xffffu)] = inf;
-            np += uint32_t(inf >> 56);
+        // ---- records, in index order, written by the warp cooperatively: lane
+        // j of a round writes the warp's record j (coalesced) and, for a
+        // saddle, finds its upper-link components and their highest vertices
+        const uint32_t excl = inc - cnt, cw = __shfl_sync(0xffffffffu, inc, 31);
+        uint32_t np = 0;
+        for (uint32_t base = 0; base < cw; base += 32) {
+            const uint32_t j = base + lane;
+            // owner: the last lane whose first record is at or before j
+            uint32_t own = 0, own_excl = 0;
+#pragma unroll
+            for (int st = 16; st >= 1; st >>= 1) {
+                const uint32_t e = __shfl_sync(0xffffffffu, excl, own + st);
+                if (e <= j) {
+                    own += st;
+                    own_excl = e;
+                }
+            }
+            const uint32_t ocrit = __shfl_sync(0xffffffffu, crit, own);
+            const uint32_t ovrow = __shfl_sync(0xffffffffu, vrow, own);
+            const uint32_t ox = __shfl_sync(0xffffffffu, x, own);
+            const uint32_t orr = __shfl_sync(0xffffffffu, rr, own);
+            if (j < cw) {
+                // vertex i of the owner: its (j - own_excl)-th critical vertex
+                uint32_t k = j - own_excl, m = ocrit, i = 0;
+                const uint32_t c4 = __popc(m & 15u);
+                if (k >= c4) { i = 4; k -= c4; m >>= 4; }
+                const uint32_t c2 = __popc(m & 3u);
+                if (k >= c2) { i += 2; k -= c2; m >>= 2; }
+                if (k >= (m & 1u)) i += 1;
+                const uint32_t w = s_um[(uint32_t(warp) * 32u + own) * kVx + i];
+                const uint32_t upper = w & 0x3fffu, sl = w >> 14;
+                const float *orow = Cb + orr * rs;
+                const uint64_t q = slot0 + pw + j;
+                F.rec_sid[q] = ovrow + i;
+                F.rec_val[q] = orow[zm_col(int(ox + i))];
+                uint64_t inf = 0;
+                if (upper) {
+                    inf = saddle_info<MIN>(orow, int(ox + i), s_roff, s_rdx, upper, int(sl & 15u), sl >> 4, s_adj,
+                                           comp2);
+                    np += uint32_t(inf >> 56);
+                }
+                F.rec_info[q] = inf;
+            }
         }
         np = __reduce_add_sync(0xffffffffu, np);
         if (lane == 0 && np) atomicAdd(&s_cnt[2], np);
-        if (tid == 0) {
-            uint32_t tot = 0;
-            for (int w = 0; w < kZmThreads / 32; w++) tot += s_warp[w];
-            atomicAdd(&s_cnt[1], tot);  // critical vertices; maxima subtracted below
-        }
+        if (tid == 0) s_cnt[1] = tot;  // critical vertices; maxima subtracted below
         prev_brick = brick;
     }
     __syncthreads();
