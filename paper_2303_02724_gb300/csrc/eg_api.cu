@@ -616,9 +616,9 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
         brick0 += ly.nbricks;
         rec0 += uint64_t(ly.nbricks) * ly.bcap;
         tile0 += scan_tiles(ly.nbricks);
-        char fs[96];
-        std::snprintf(fs, sizeof fs, "%d,%d,%u,%u,%u,%u,%u,%u,%u,%u;", key(i), ly.kd, F.N, ly.ty, ly.nyb, ly.nbricks,
-                      ly.zc, ly.nzc, F.vec, F.n[0]);
+        char fs[192];
+        std::snprintf(fs, sizeof fs, "%d,%d,%u,%u,%u,%u,%u,%u,%u,%u,%u,%u,%u;", key(i), ly.kd, F.N, ly.ty, ly.nyb,
+                      ly.nbricks, ly.zc, ly.nzc, F.vec, F.n[0], F.n[1], F.n[2], F.n[3]);
         P.signature += fs;
     }
 
