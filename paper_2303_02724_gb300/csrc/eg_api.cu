@@ -1094,12 +1094,18 @@ eg_status eg_get_graph(eg_handle h, eg_result_id id, eg_graph *out)
         {out->saddles, r.saddles, r.S * 4}, {out->sad_beta0, r.sad_b0, r.S},
         {out->sad_val, r.sad_val, r.S * 4}, {out->row_ptr, r.row_ptr, (r.S + 1) * 8},
         {out->col, r.col, r.A * 4}, {out->labels, r.lab, r.N * 4}};
+    // all copies in flight at once on the side stream (they overlap when the
+    // destinations are pinned), then one wait
     for (auto &c : cp)
         if (c.dst && c.b) {
-            cudaError_t e = cudaMemcpy(c.dst, c.src, c.b, cudaMemcpyDeviceToHost);
-            if (e != cudaSuccess) return from_cuda(e);
+            cudaError_t e = cudaMemcpyAsync(c.dst, c.src, c.b, cudaMemcpyDeviceToHost, h->side);
+            if (e != cudaSuccess) {
+                cudaStreamSynchronize(h->side);
+                return from_cuda(e);
+            }
         }
-    return EG_OK;
+    cudaError_t e = cudaStreamSynchronize(h->side);
+    return e == cudaSuccess ? EG_OK : from_cuda(e);
 }
 
 eg_status eg_get_graph_device(eg_handle h, eg_result_id id, eg_graph *out)

@@ -146,6 +146,42 @@ class Graph:
         return out
 
 
+class GraphBuffers:
+    """Host arrays a result is copied into, sized for up to M maxima, S
+    saddles, A arcs and N labels.  pinned=True allocates page-locked memory
+    (through torch), so the device-to-host copies run at link speed; the same
+    buffers can be reused for every result that fits (the Graph returned by
+    get_graph then views them, so it is only valid until the next reuse)."""
+
+    _FIELDS = (("maxima", np.uint32, "M"), ("max_val", np.float32, "M"), ("saddles", np.uint32, "S"),
+               ("sad_b0", np.uint8, "S"), ("sad_val", np.float32, "S"), ("row_ptr", np.uint64, "S1"),
+               ("col", np.uint32, "A"), ("labels", np.uint32, "N"))
+
+    def __init__(self, M: int, S: int, A: int, N: int = 0, pinned: bool = False):
+        self.cap = {"M": int(M), "S": int(S), "S1": int(S) + 1, "A": int(A), "N": int(N)}
+        self.arrays = {}
+        for name, dt, k in self._FIELDS:
+            n = self.cap[k]
+            if pinned and n:
+                import torch
+                buf = torch.empty(n * np.dtype(dt).itemsize, dtype=torch.uint8, pin_memory=True).numpy()
+                self.arrays[name] = buf.view(dt)
+            else:
+                self.arrays[name] = np.empty(n, dt)
+
+    def fits(self, M: int, S: int, A: int, N: int = 0) -> bool:
+        c = self.cap
+        return M <= c["M"] and S <= c["S"] and A <= c["A"] and N <= c["N"]
+
+    def views(self, M: int, S: int, A: int, N: int = 0) -> Graph:
+        if not self.fits(M, S, A, N):
+            raise ValueError("result larger than the buffers")
+        a = self.arrays
+        return Graph(d=0, extents=(), n_vertices=0, n_paths=0, maxima=a["maxima"][:M], max_val=a["max_val"][:M],
+                     saddles=a["saddles"][:S], sad_b0=a["sad_b0"][:S], sad_val=a["sad_val"][:S],
+                     row_ptr=a["row_ptr"][:S + 1], col=a["col"][:A], labels=a["labels"][:N] if N else None)
+
+
 def _stream_ptr(stream) -> int:
     if stream is None:
         import torch
@@ -247,15 +283,19 @@ class Handle:
         return dict(n_vertices=g.n_vertices, n_maxima=g.n_maxima, n_saddles=g.n_saddles,
                     n_paths=g.n_paths, n_arcs=g.n_arcs)
 
-    def get_graph(self, rid: int, labels: bool = True) -> Graph:
+    def get_graph(self, rid: int, labels: bool = True, buffers: "GraphBuffers" = None) -> Graph:
+        """Copy a result to host memory.  With `buffers` (see GraphBuffers, e.g.
+        pinned and reused across calls) the arrays of the returned Graph are
+        views into them; otherwise fresh numpy arrays."""
         g = EGGraphC()
         _check(self._lib.eg_get_graph(self._h, ctypes.c_uint64(rid), ctypes.byref(g)), "eg_get_graph")
         M, S, A, N = g.n_maxima, g.n_saddles, g.n_arcs, g.n_vertices
-        out = Graph(d=g.d, extents=tuple(g.extents[:g.d]), n_vertices=N, n_paths=g.n_paths,
-                    maxima=np.empty(M, np.uint32), max_val=np.empty(M, np.float32),
-                    saddles=np.empty(S, np.uint32), sad_b0=np.empty(S, np.uint8),
-                    sad_val=np.empty(S, np.float32), row_ptr=np.empty(S + 1, np.uint64),
-                    col=np.empty(A, np.uint32), labels=np.empty(N, np.uint32) if labels else None)
+        if buffers is None:
+            buffers = GraphBuffers(M, S, A, N if labels else 0)
+        out = buffers.views(M, S, A, N if labels else 0)
+        out.d, out.extents, out.n_vertices, out.n_paths = g.d, tuple(g.extents[:g.d]), N, g.n_paths
+        if not labels:
+            out.labels = None
         g.maxima = out.maxima.ctypes.data
         g.max_val = out.max_val.ctypes.data
         g.saddles = out.saddles.ctypes.data

@@ -5,6 +5,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 from paper_2303_02724_gb300 import _build, eg
@@ -54,3 +55,16 @@ def test_loads_and_host_only_calls(lib_path):
     assert lib.eg_launch_count(None) == 0
     assert lib.eg_release(None, 1) == eg.EG_ERR_ARG
     assert lib.eg_destroy(None) == eg.EG_OK
+
+
+def test_graph_buffers_views():
+    from paper_2303_02724_gb300 import eg
+    b = eg.GraphBuffers(5, 7, 11, 13)
+    assert b.fits(5, 7, 11, 13) and not b.fits(6, 7, 11, 13) and not b.fits(5, 7, 12)
+    g = b.views(2, 3, 4)
+    assert (g.maxima.size, g.saddles.size, g.row_ptr.size, g.col.size, g.labels) == (2, 3, 4, 4, None)
+    assert g.row_ptr.dtype == np.uint64 and g.sad_b0.dtype == np.uint8
+    assert np.shares_memory(g.col, b.arrays["col"])
+    assert b.views(0, 0, 0, 13).labels.size == 13
+    with pytest.raises(ValueError):
+        b.views(6, 0, 0)

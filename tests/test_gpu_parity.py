@@ -151,6 +151,21 @@ def test_host_entry_point(handle):
     assert_same(g, oracle.compute(f.values))
 
 
+def test_pinned_buffers_reused(handle):
+    from paper_2303_02724_gb300 import eg
+    buf = eg.GraphBuffers(4096, 8192, 16384, 24 * 24 * 24, pinned=True)
+    for seed in (1, 2):
+        f = F.grf((24, 24, 24), seed)
+        rid = handle.compute_host(torch.from_numpy(f.values).pin_memory().numpy())
+        g = handle.get_graph(rid, buffers=buf)
+        handle.release(rid)
+        assert_same(g, oracle.compute(f.values))
+    rid = handle.compute(torch.from_numpy(F.white_noise((64, 64, 64), 3).values).cuda())
+    with pytest.raises(ValueError):
+        handle.get_graph(rid, buffers=eg.GraphBuffers(1, 1, 1))
+    handle.release(rid)
+
+
 def test_batch_uneven(handle):
     specs = F.batch_specs(3, 24, scale=0.12)
     flds = [F.batch_field(e, s, gn) for (e, s, gn) in specs]
