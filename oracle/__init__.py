@@ -65,6 +65,10 @@ def _load():
         lib.eo_copy.restype = None
         lib.eo_free.argtypes = [P]
         lib.eo_free.restype = None
+        lib.eo_path_vertices.argtypes = [P]
+        lib.eo_path_vertices.restype = ctypes.c_uint64
+        lib.eo_paths.argtypes = [P, P, P]
+        lib.eo_paths.restype = None
         lib.eo_neighbour_offsets.argtypes = [ctypes.c_int, P]
         lib.eo_neighbour_offsets.restype = ctypes.c_int
         lib.eo_grid_adjacent.argtypes = [ctypes.c_int, P, P]
@@ -88,6 +92,12 @@ class OracleGraph:
     col: np.ndarray      # uint32[A]
     n_paths: int         # sum of beta0+ over saddles
     reps: np.ndarray = None  # uint32[P] UpperLinkRep per saddle (ascending ids, saddles in order)
+    path_ptr: np.ndarray = None  # uint64[P+1] offsets of the arc geometry (paths=True)
+    path_vtx: np.ndarray = None  # uint32[...] s, rep, gradient(rep), ..., maximum per path
+
+    def path(self, p):
+        """Vertices of path number p (saddle, representative, ..., maximum)."""
+        return self.path_vtx[self.path_ptr[p]:self.path_ptr[p + 1]]
 
     def saddle_reps(self, i):
         """Upper-link representatives of saddle number i."""
@@ -104,12 +114,13 @@ class OracleGraph:
 
 
 def compute(field: np.ndarray, extents=None, naive: bool = False,
-            minimum: bool = False) -> OracleGraph:
+            minimum: bool = False, paths: bool = False) -> OracleGraph:
     """Extremum graph of ``field`` (float32).
 
     ``extents`` lists the grid size per axis with axis 0 fastest; by default it
     is the numpy shape reversed, so a C-ordered array ``a[z, y, x]`` has
     ``x`` as axis 0.  ``minimum`` selects the minimum graph (reversed order).
+    ``paths`` adds the arc geometry (Algorithm 2's gradient paths).
     """
     lib = _load()
     f = np.ascontiguousarray(field, dtype=np.float32).reshape(-1)
@@ -138,6 +149,11 @@ def compute(field: np.ndarray, extents=None, naive: bool = False,
                     g.maxima.ctypes.data, g.max_val.ctypes.data, g.saddles.ctypes.data,
                     g.sad_b0.ctypes.data, g.sad_val.ctypes.data, g.row_ptr.ctypes.data,
                     g.col.ctypes.data, g.reps.ctypes.data)
+        if paths:
+            nv = int(lib.eo_path_vertices(h))
+            g.path_ptr = np.empty(npaths + 1, np.uint64)
+            g.path_vtx = np.empty(nv, np.uint32)
+            lib.eo_paths(h, g.path_ptr.ctypes.data, g.path_vtx.ctypes.data)
         return g
     finally:
         lib.eo_free(h)

@@ -36,6 +36,10 @@
  *   arcs        (s, label(rep)) for every saddle s and every component,
  *               duplicates removed, sorted by (s, m) (Sec. 2: arc (s,m) iff s
  *               bounds the descending manifold of m).
+ *   paths       the geometry of every arc (Algorithm 2): for every saddle s in
+ *               ascending order and every component in ascending order of its
+ *               representative, the vertices s, rep, gradient(rep), ...,
+ *               up to the maximum reached.
  *
  * The minimum graph (Sec. 2, Sec. 5) is the same computation with the order
  * reversed: "higher" becomes "lower" under the same perturbation.
@@ -355,6 +359,43 @@ void eo_copy(const eo_result *r, uint32_t *asc, uint32_t *label, uint8_t *beta0p
     if (row_ptr) memcpy(row_ptr, r->row_ptr, (size_t)(r->n_sad + 1) * sizeof(uint64_t));
     if (col) memcpy(col, r->col, (size_t)r->n_arcs * sizeof(uint32_t));
     if (reps) memcpy(reps, r->reps, (size_t)r->n_paths * sizeof(uint32_t));
+}
+
+/* Gradient paths (Algorithm 2): per saddle (ascending) and per component (in
+ * the order of r->reps), s then the gradient path from the representative to
+ * its maximum.  eo_path_vertices gives the total length; eo_paths fills
+ * path_ptr[n_paths + 1] (offsets) and path_vtx. */
+uint64_t eo_path_vertices(const eo_result *r)
+{
+    uint64_t total = 0;
+    for (int64_t p = 0; p < r->n_paths; p++) {
+        uint32_t u = r->reps[p];
+        total += 2;
+        while (r->asc[u] != u) {
+            u = r->asc[u];
+            total++;
+        }
+    }
+    return total;
+}
+
+void eo_paths(const eo_result *r, uint64_t *path_ptr, uint32_t *path_vtx)
+{
+    uint64_t at = 0;
+    int64_t p = 0;
+    for (int64_t i = 0; i < r->n_sad; i++) {
+        for (int c = 0; c < r->sad_b0[i]; c++, p++) {
+            path_ptr[p] = at;
+            uint32_t u = r->reps[p];
+            path_vtx[at++] = r->saddles[i];
+            path_vtx[at++] = u;
+            while (r->asc[u] != u) {
+                u = r->asc[u];
+                path_vtx[at++] = u;
+            }
+        }
+    }
+    path_ptr[p] = at;
 }
 
 /* Neighbour offsets kept by Algorithm 1 (for tests of the adjacency itself). */

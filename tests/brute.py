@@ -85,5 +85,14 @@ def brute_graph(field, extents, minimum=False):
     maxima = [v for v in range(n) if beta[v] == 0]
     saddles = [v for v in range(n) if beta[v] >= 2]
     arcs = {(s, int(label[r])) for s in saddles for r in reps[s]}
+    # arc geometry: per saddle and per representative in ascending id order,
+    # the saddle and the naive walk from the representative
+    paths = []
+    for s in saddles:
+        for r in sorted(int(x) for x in reps[s]):
+            walk = [s, r]
+            while asc[walk[-1]] != walk[-1]:
+                walk.append(int(asc[walk[-1]]))
+            paths.append(walk)
     return dict(asc=asc, label=label, beta=beta, maxima=maxima, saddles=saddles,
-                arcs=arcs, reps=reps)
+                arcs=arcs, reps=reps, paths=paths)

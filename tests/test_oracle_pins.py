@@ -59,7 +59,7 @@ def _golden_field(meta, sec):
 def test_golden(path):
     meta, sec = _read_golden(path)
     ext, vals = _golden_field(meta, sec)
-    g = oracle.compute(vals, extents=ext, minimum=bool(int(meta.get("minimum", "0"))))
+    g = oracle.compute(vals, extents=ext, minimum=bool(int(meta.get("minimum", "0"))), paths=True)
     ints = lambda s: [int(x) for x in s.split()] if s else []
     assert g.maxima.tolist() == ints(sec["maxima"])
     assert g.saddles.tolist() == ints(sec.get("saddles", ""))
@@ -73,6 +73,9 @@ def test_golden(path):
         assert np.array_equal(g.label, np.where(x <= 3, 29, 33).astype(np.uint32))
     assert np.array_equal(g.max_val, vals[g.maxima])
     assert np.array_equal(g.sad_val, vals[g.saddles])
+    if "paths" in sec:
+        want = [[int(y) for y in a.split(",")] for a in sec["paths"].split()]
+        assert [g.path(p).tolist() for p in range(g.n_paths)] == want
 
 
 # ----------------------------------------------------------- Algorithm 1 ----
@@ -117,7 +120,7 @@ def test_brute_force(shape, kind, minimum):
     n = int(np.prod(shape))
     seed = zlib.crc32(repr((shape, kind)).encode()) % 1000
     f = (F.white_noise(shape, seed) if kind == "normal" else F.integer_ties(shape, seed, 3)).values
-    g = oracle.compute(f, extents=shape, minimum=minimum)
+    g = oracle.compute(f, extents=shape, minimum=minimum, paths=True)
     b = brute_graph(f, shape, minimum=minimum)
     assert g.asc.tolist() == b["asc"].tolist()
     assert g.label.tolist() == b["label"].tolist()
@@ -128,6 +131,7 @@ def test_brute_force(shape, kind, minimum):
     assert g.n_paths == sum(len(b["reps"][s]) for s in b["saddles"])
     for i, s_ in enumerate(b["saddles"]):
         assert g.saddle_reps(i).tolist() == sorted(int(x) for x in b["reps"][s_])
+    assert [g.path(p).tolist() for p in range(g.n_paths)] == b["paths"]
     assert n == g.label.size
 
 
