@@ -147,7 +147,8 @@ def path_bytes(c):
     """Algorithmic bytes of one field: read f, write labels, the graph and its
     value copies (maxima, saddles, beta0+, row_ptr as uint64, col)."""
     N, M, S, A = c["n_vertices"], c["n_maxima"], c["n_saddles"], c["n_arcs"]
-    return 4 * N + 4 * N + 8 * M + 9 * S + 8 * (S + 1) + 4 * A
+    geometry = 4 * c["n_path_vertices"] + 8 * (c["n_paths"] + 1) if "n_path_vertices" in c else 0
+    return 4 * N + 4 * N + 8 * M + 9 * S + 8 * (S + 1) + 4 * A + geometry
 
 
 def kernel_bytes(c):
@@ -382,6 +383,8 @@ def main():
     ap.add_argument("--ref-sample-vertices", type=int, default=2 * 1024 * 1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--paths", action="store_true",
+                    help="also gather the arc geometry (EG_FLAG_PATHS) in every timed step")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--serve-requests", type=int, default=1024)
     ap.add_argument("--serve-fractions", type=float, nargs="+", default=[0.5, 0.8, 0.95])
@@ -410,7 +413,7 @@ def main():
     N = fld.n
     t_field = torch.from_numpy(fld.values).to(dev)
     stream = torch.cuda.current_stream(dev)
-    h = eg.Handle(local)
+    h = eg.Handle(local, paths=args.paths)
     h.set_timing(True)
 
     def step():
@@ -425,6 +428,8 @@ def main():
         rid, g = step()
         counts = dict(n_vertices=g.n_vertices, n_maxima=g.n_maxima, n_saddles=g.n_saddles,
                       n_paths=g.n_paths, n_arcs=g.n_arcs)
+        if args.paths:
+            counts["n_path_vertices"] = h.path_count(rid)
         h.release(rid)
 
     clocks = ClockSampler(local)
@@ -487,7 +492,7 @@ def main():
     # end to end through the C ABI with host buffers: H2D of the field and
     # D2H of the graph inside the timed region
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not args.paths:
         host = torch.from_numpy(fld.values).pin_memory().numpy()
         # two host threads, each with its own handle, stream and page-locked
         # output buffers (allocated once, reused), take alternate steps, so one
@@ -560,7 +565,9 @@ def main():
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload], "vertices": N, "l2": "inputs larger than L2"
+            "config": {"workload": WORKLOADS[args.workload] + ("; with the arc geometry (EG_FLAG_PATHS)"
+                                                               if args.paths else ""),
+                       "vertices": N, "l2": "inputs larger than L2"
                        if flush is None else "L2 flushed before every step (256 MB written)",
                        "parallelism": f"replicas x{ws}", **{k: v for k, v in counts.items() if k != "n_vertices"}},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",

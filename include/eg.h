@@ -71,6 +71,7 @@ typedef enum eg_status {
 #define EG_FLAG_NO_LABELS     0x2u  /* do not keep per-vertex labels in the result    */
 #define EG_FLAG_NO_GRAPH      0x4u  /* eg_batch_submit: launch the steps directly
                                        instead of replaying captured CUDA graphs    */
+#define EG_FLAG_PATHS         0x8u  /* also keep the arc geometry (eg_get_paths)    */
 
 /* Tuning knobs.  Zero in any field means "library default" (or the value a
  * previous eg_autotune chose for this handle).  The neighbourhood halo is one
@@ -165,6 +166,25 @@ EG_API eg_status eg_get_graph(eg_handle h, eg_result_id id, eg_graph *out);
 /* Same as eg_get_graph but fills the array pointers with the library-owned
  * DEVICE buffers instead of copying (valid until eg_release). */
 EG_API eg_status eg_get_graph_device(eg_handle h, eg_result_id id, eg_graph *out);
+
+/* Arc geometry (Algorithm 2, Sec. 3.4): for every saddle, in the order of
+ * eg_graph.saddles, and every component of its upper link, in ascending order
+ * of its highest vertex (UpperLinkRep), the path of vertex ids
+ *   s, rep, gradient(rep), gradient(gradient(rep)), ..., m
+ * where m is the maximum reached (the arc end) and gradient(v) is v's highest
+ * neighbour.  There are n_paths paths (eg_graph.n_paths); path p is
+ * path_vtx[path_ptr[p] .. path_ptr[p + 1]).  Only results computed with
+ * EG_FLAG_PATHS (handle configuration or eg_field_desc.flags) carry it; the
+ * geometry is gathered between classification and resolution and adds two
+ * host round trips to that computation (fields with paths never replay a
+ * captured graph).
+ * Call with path_ptr == path_vtx == NULL to get *n_path_vertices; then
+ * path_ptr must hold n_paths + 1 entries and path_vtx *n_path_vertices, both
+ * caller-owned host memory.
+ * Errors: EG_ERR_ARG (unknown id, no geometry kept, NULL n_path_vertices),
+ * plus any deferred device status as eg_get_graph. */
+EG_API eg_status eg_get_paths(eg_handle h, eg_result_id id, uint64_t *path_ptr, uint32_t *path_vtx,
+                              uint64_t *n_path_vertices);
 
 /* Autotuner: time candidate values of every eg_config knob on this batch of
  * fields (coordinate descent over the knobs, each candidate a full run of the

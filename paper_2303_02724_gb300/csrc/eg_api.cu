@@ -154,7 +154,8 @@ struct Result {
     void *small = nullptr;  // SmallBlock on device
     void *maxima = nullptr, *max_val = nullptr, *saddles = nullptr, *sad_b0 = nullptr, *sad_val = nullptr,
          *row_ptr = nullptr, *col = nullptr, *ends = nullptr, *ucnt = nullptr;
-    uint64_t M = 0, S = 0, P = 0, A = 0;
+    void *path_ptr = nullptr, *path_vtx = nullptr, *pbrick = nullptr;  // arc geometry (EG_FLAG_PATHS)
+    uint64_t M = 0, S = 0, P = 0, A = 0, V = 0;
     bool have_A = false;
     uint32_t err = 0;
     cudaEvent_t done = nullptr;
@@ -340,8 +341,8 @@ eg_status ensure_workspace(eg_ctx *h, uint64_t recs, uint64_t bricks, uint64_t t
 
 void free_result_buffers(eg_ctx *h, Result *r)
 {
-    void **bufs[] = {&r->lab, &r->small, &r->maxima, &r->max_val, &r->saddles, &r->sad_b0,
-                     &r->sad_val, &r->row_ptr, &r->col, &r->ends, &r->ucnt};
+    void **bufs[] = {&r->lab,     &r->small, &r->maxima, &r->max_val,  &r->saddles,  &r->sad_b0, &r->sad_val,
+                     &r->row_ptr, &r->col,   &r->ends,   &r->ucnt,     &r->path_ptr, &r->path_vtx, &r->pbrick};
     for (void **b : bufs) {
         h->pool.release(*b);
         *b = nullptr;
@@ -510,12 +511,72 @@ eg_status capture_graphs(eg_ctx *h, const Plan &P, const void *desc_host, GraphE
 
 // Run a set of fields (all of one call) through the pipeline.  use_graph:
 // replay (capturing on first use) the graphs of this call's layout.
+// Arc geometry of the fields that asked for it (EG_FLAG_PATHS), enqueued after
+// the counts are known and before resolution (lab[] still holds the gradient
+// pointers): path lengths, their scan, a read-back of each field's total, the
+// vertex buffers, then the paths.  The descriptor table is uploaded before
+// each kernel group (the host copy changes in between).
+eg_status enqueue_paths(eg_ctx *h, const Plan &P, Launch *L, FieldDev *Dh,
+                        std::vector<std::unique_ptr<Result>> &res, const std::vector<int> &order, cudaStream_t st)
+{
+    FieldDev *Dd = static_cast<FieldDev *>(L->desc_dev);
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(Dd, L->desc_host, P.desc_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return from_cuda(e);
+    for (const Group &G : P.groups)
+        if ((e = launch_path_len(G.kd, Dd + G.first, G.count, G.brick0, G.bricks, st)) != cudaSuccess)
+            return from_cuda(e);
+    if ((e = launch_path_scan(Dd, P.nf, st)) != cudaSuccess) return from_cuda(e);
+    h->launches += uint64_t(P.groups.size() + 1);
+    cudaEvent_t k2;
+    if ((e = cudaEventCreateWithFlags(&k2, cudaEventDisableTiming)) != cudaSuccess) return from_cuda(e);
+    cudaEventRecord(k2, st);
+    cudaStreamWaitEvent(h->side, k2, 0);
+    void *hv = nullptr;
+    if ((e = h->hpool.alloc(&hv, sizeof(uint64_t) * size_t(P.nf))) != cudaSuccess) {
+        cudaEventDestroy(k2);
+        return from_cuda(e);
+    }
+    uint64_t *V = static_cast<uint64_t *>(hv);
+    for (int oi = 0; oi < P.nf; oi++) {
+        V[oi] = 0;
+        if (Dh[oi].path_ptr)
+            cudaMemcpyAsync(V + oi, Dh[oi].pbrick + Dh[oi].nbricks, 8, cudaMemcpyDeviceToHost, h->side);
+    }
+    e = cudaStreamSynchronize(h->side);
+    cudaEventDestroy(k2);
+    eg_status s = EG_OK;
+    for (int oi = 0; oi < P.nf && e == cudaSuccess && s == EG_OK; oi++) {
+        if (!Dh[oi].path_ptr) continue;
+        Result &r = *res[order[oi]];
+        r.V = V[oi];
+        cudaError_t a = h->pool.alloc(&r.path_vtx, std::max<uint64_t>(r.V, 1) * 4);
+        if (a != cudaSuccess) s = from_cuda(a);
+        else Dh[oi].path_vtx = static_cast<uint32_t *>(r.path_vtx);
+    }
+    h->hpool.release(hv);
+    if (e != cudaSuccess) return from_cuda(e);
+    if (s != EG_OK) return s;
+    if ((e = cudaMemcpyAsync(Dd, L->desc_host, P.desc_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return from_cuda(e);
+    for (const Group &G : P.groups)
+        if ((e = launch_path_write(G.kd, Dd + G.first, G.count, G.brick0, G.bricks, st)) != cudaSuccess)
+            return from_cuda(e);
+    h->launches += uint64_t(P.groups.size());
+    return EG_OK;
+}
+
 eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std::vector<uint64_t> &ids,
                    const eg_config &cfg, bool use_graph = false)
 {
     const int nf = int(jobs.size());
     std::vector<Layout> lay(nf);
     for (int i = 0; i < nf; i++) lay[i] = make_layout(jobs[i].sh, h->sm_count, cfg);
+    // the arc geometry needs the gradient pointers after the counts are known
+    // and before resolution: such calls run step by step, without graphs
+    bool any_paths = false;
+    for (int i = 0; i < nf; i++) any_paths = any_paths || (jobs[i].flags & kFlagPaths);
+    if (any_paths) use_graph = false;
     // group fields by classifier kind so every launch covers a contiguous slice
     auto key = [&](int i) {
         return (lay[i].zm ? 0 : 2) * 16 + lay[i].kd * 2 + ((jobs[i].flags & kFlagMinimum) ? 1 : 0);
@@ -687,12 +748,15 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
     cudaEvent_t k1;
     if ((e = cudaEventCreateWithFlags(&k1, cudaEventDisableTiming)) != cudaSuccess) return fail(from_cuda(e));
     cudaEventRecord(k1, st);
-    // step (b) runs while the host reads the counts back
-    if ((es = run_part(1)) != EG_OK) {
-        cudaEventDestroy(k1);
-        return fail(es);
+    // step (b) runs while the host reads the counts back (after the geometry
+    // when that is wanted)
+    if (!any_paths) {
+        if ((es = run_part(1)) != EG_OK) {
+            cudaEventDestroy(k1);
+            return fail(es);
+        }
+        if (h->timing) cudaEventRecord(L->ev[2], st);
     }
-    if (h->timing) cudaEventRecord(L->ev[2], st);
     void *hcounts = nullptr;
     if ((e = h->hpool.alloc(&hcounts, sizeof(SmallBlock) * size_t(nf))) != cudaSuccess) {
         cudaEventDestroy(k1);
@@ -741,6 +805,18 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
         F.col = static_cast<uint32_t *>(r.col);
         F.ends = static_cast<uint32_t *>(r.ends);
         F.ucnt = static_cast<uint8_t *>(r.ucnt);
+        if (r.flags & kFlagPaths) {
+            if ((e = h->pool.alloc(&r.path_ptr, (r.P + 1) * 8)) != cudaSuccess) return fail(from_cuda(e));
+            if ((e = h->pool.alloc(&r.pbrick, (uint64_t(F.nbricks) + 1) * 8)) != cudaSuccess)
+                return fail(from_cuda(e));
+            F.path_ptr = static_cast<uint64_t *>(r.path_ptr);
+            F.pbrick = static_cast<uint64_t *>(r.pbrick);
+        }
+    }
+    if (any_paths && (es = enqueue_paths(h, P, L.get(), Dh, res, order, st)) != EG_OK) return fail(es);
+    if (any_paths) {
+        if ((es = run_part(1)) != EG_OK) return fail(es);
+        if (h->timing) cudaEventRecord(L->ev[2], st);
     }
     // phase 0 has finished (we waited for it), so the host table may change;
     // phase 2 uploads it again, ordered after resolution on the stream
@@ -775,7 +851,8 @@ eg_status collect(eg_ctx *h, Result &r)
         r.have_A = true;
         h->pool.release(r.ends);
         h->pool.release(r.ucnt);
-        r.ends = r.ucnt = nullptr;
+        h->pool.release(r.pbrick);
+        r.ends = r.ucnt = r.pbrick = nullptr;
         if (r.launch && r.launch.use_count() == 1) release_launch(h, r.launch.get());
     }
     if (r.err & kErrNaN) return EG_ERR_NAN;
@@ -904,7 +981,7 @@ eg_status eg_compute(eg_handle h, const float *field, int d, const int64_t *exte
     if (!make_shape(d, extents, sh)) return EG_ERR_ARG;
     std::lock_guard<std::mutex> g(h->mu);
     cudaSetDevice(h->device);
-    std::vector<Job> jobs{{field, sh, h->cfg.flags & (kFlagMinimum | kFlagNoLabels)}};
+    std::vector<Job> jobs{{field, sh, h->cfg.flags & (kFlagMinimum | kFlagNoLabels | kFlagPaths)}};
     std::vector<uint64_t> ids;
     eg_status s = run_jobs(h, jobs, static_cast<cudaStream_t>(stream), ids, h->cfg);
     if (s == EG_OK) *out = ids[0];
@@ -955,7 +1032,7 @@ eg_status eg_compute_host(eg_handle h, const float *field, int d, const int64_t 
     }
     cudaError_t e = cudaMemcpyAsync(h->stage, src, bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return from_cuda(e);
-    std::vector<Job> jobs{{static_cast<const float *>(h->stage), sh, h->cfg.flags & (kFlagMinimum | kFlagNoLabels)}};
+    std::vector<Job> jobs{{static_cast<const float *>(h->stage), sh, h->cfg.flags & (kFlagMinimum | kFlagNoLabels | kFlagPaths)}};
     std::vector<uint64_t> ids;
     eg_status s = run_jobs(h, jobs, st, ids, h->cfg);
     if (s == EG_OK) *out = ids[0];
@@ -970,7 +1047,7 @@ eg_status eg_batch_submit(eg_handle h, const eg_field_desc *fields, int n, void 
     for (int i = 0; i < n; i++) {
         if (!fields[i].field || !make_shape(fields[i].d, fields[i].extents, jobs[i].sh)) return EG_ERR_ARG;
         jobs[i].field = fields[i].field;
-        jobs[i].flags = (h->cfg.flags | uint32_t(fields[i].flags)) & (kFlagMinimum | kFlagNoLabels);
+        jobs[i].flags = (h->cfg.flags | uint32_t(fields[i].flags)) & (kFlagMinimum | kFlagNoLabels | kFlagPaths);
     }
     std::lock_guard<std::mutex> g(h->mu);
     cudaSetDevice(h->device);
@@ -1036,7 +1113,7 @@ eg_status eg_autotune(eg_handle h, const eg_field_desc *fields, int n, void *str
     for (int i = 0; i < n; i++) {
         if (!fields[i].field || !make_shape(fields[i].d, fields[i].extents, jobs[i].sh)) return EG_ERR_ARG;
         jobs[i].field = fields[i].field;
-        jobs[i].flags = (h->cfg.flags | uint32_t(fields[i].flags)) & (kFlagMinimum | kFlagNoLabels);
+        jobs[i].flags = (h->cfg.flags | uint32_t(fields[i].flags)) & (kFlagMinimum | kFlagNoLabels | kFlagPaths);
     }
     std::lock_guard<std::mutex> g(h->mu);
     cudaSetDevice(h->device);
@@ -1104,6 +1181,31 @@ eg_status eg_get_graph(eg_handle h, eg_result_id id, eg_graph *out)
                 return from_cuda(e);
             }
         }
+    cudaError_t e = cudaStreamSynchronize(h->side);
+    return e == cudaSuccess ? EG_OK : from_cuda(e);
+}
+
+eg_status eg_get_paths(eg_handle h, eg_result_id id, uint64_t *path_ptr, uint32_t *path_vtx,
+                       uint64_t *n_path_vertices)
+{
+    if (!h || !n_path_vertices) return EG_ERR_ARG;
+    std::lock_guard<std::mutex> g(h->mu);
+    cudaSetDevice(h->device);
+    auto it = h->results.find(id);
+    if (it == h->results.end()) return EG_ERR_ARG;
+    Result &r = *it->second;
+    if (!r.path_ptr) return EG_ERR_ARG;
+    eg_status s = collect(h, r);
+    *n_path_vertices = r.V;
+    if (s != EG_OK) return s;
+    if (path_ptr) {
+        cudaError_t e = cudaMemcpyAsync(path_ptr, r.path_ptr, (r.P + 1) * 8, cudaMemcpyDeviceToHost, h->side);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
+    if (path_vtx && r.V) {
+        cudaError_t e = cudaMemcpyAsync(path_vtx, r.path_vtx, r.V * 4, cudaMemcpyDeviceToHost, h->side);
+        if (e != cudaSuccess) return from_cuda(e);
+    }
     cudaError_t e = cudaStreamSynchronize(h->side);
     return e == cudaSuccess ? EG_OK : from_cuda(e);
 }

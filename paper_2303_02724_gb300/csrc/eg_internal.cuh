@@ -48,7 +48,7 @@ enum : uint32_t {
 };
 
 // flags carried per field
-enum : uint32_t { kFlagMinimum = 1u, kFlagNoLabels = 2u };
+enum : uint32_t { kFlagMinimum = 1u, kFlagNoLabels = 2u, kFlagPaths = 8u };
 
 // One field as the kernels see it.  Plain pointers; filled on the host.
 struct FieldDev {
@@ -73,6 +73,10 @@ struct FieldDev {
     uint64_t *row_ptr;       // [S+1]
     uint32_t *col;           // [A]
     unsigned long long *totals;  // [4] M, S, P, A
+    // arc geometry (only when requested, else null)
+    uint64_t *path_ptr;      // [P + 1] path lengths, then offsets into path_vtx
+    uint32_t *path_vtx;      // [V] saddle, representative, ..., maximum per path
+    uint64_t *pbrick;        // [nbricks + 1] path vertices per brick, then offsets and the total
     uint32_t *err;           // device status word
     uint32_t n[kMaxDim];     // extents (1 beyond the kernel dimension)
     uint32_t s[kMaxDim];     // strides

@@ -46,4 +46,12 @@ cudaError_t launch_resolve(const FieldDev *fields, int nf, uint64_t total_bricks
 cudaError_t launch_nodes_d(int kd, const FieldDev *fields, int nf, uint64_t base, uint64_t bricks, cudaStream_t st);
 cudaError_t launch_csr(const FieldDev *fields, int nf, uint64_t total_bricks, cudaStream_t st);
 
+// Arc geometry (fields with path_ptr set; between classification and
+// resolution): path lengths per brick, their scan (one CTA per field of the
+// table), then offsets and vertices.
+cudaError_t launch_path_len(int kd, const FieldDev *fields, int nf, uint64_t base, uint64_t bricks, cudaStream_t st);
+cudaError_t launch_path_scan(const FieldDev *fields, int nf, cudaStream_t st);
+cudaError_t launch_path_write(int kd, const FieldDev *fields, int nf, uint64_t base, uint64_t bricks,
+                              cudaStream_t st);
+
 }  // namespace eg

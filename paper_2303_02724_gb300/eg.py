@@ -23,6 +23,7 @@ EG_ERR_NOT_CONVERGED, EG_ERR_TIMEOUT, EG_ERR_BUSY, EG_ERR_INTERNAL = 5, 6, 7, 8
 EG_FLAG_MINIMUM_GRAPH = 0x1
 EG_FLAG_NO_LABELS = 0x2
 EG_FLAG_NO_GRAPH = 0x4
+EG_FLAG_PATHS = 0x8
 
 
 class EGError(RuntimeError):
@@ -71,6 +72,7 @@ SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_uint64)]),
     "eg_get_graph": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(EGGraphC)]),
     "eg_get_graph_device": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(EGGraphC)]),
+    "eg_get_paths": (ctypes.c_int, [_P, ctypes.c_uint64, _P, _P, ctypes.POINTER(ctypes.c_uint64)]),
     "eg_release": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "eg_workspace_bytes": (ctypes.c_uint64, [ctypes.c_int, _P]),
     "eg_mem_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
@@ -194,11 +196,14 @@ def _stream_ptr(stream) -> int:
 class Handle:
     """One library handle on one CUDA device."""
 
-    def __init__(self, device: int = 0, minimum: bool = False, config: Optional[EGConfig] = None):
+    def __init__(self, device: int = 0, minimum: bool = False, config: Optional[EGConfig] = None,
+                 paths: bool = False):
         lib = load()
         cfg = config if config is not None else EGConfig()
         if minimum:
             cfg.flags |= EG_FLAG_MINIMUM_GRAPH
+        if paths:
+            cfg.flags |= EG_FLAG_PATHS
         h = ctypes.c_void_p()
         _check(lib.eg_create(ctypes.byref(h), int(device), ctypes.byref(cfg)), "eg_create")
         self._h = h
@@ -306,6 +311,27 @@ class Handle:
         g.labels = out.labels.ctypes.data if labels else None
         _check(self._lib.eg_get_graph(self._h, ctypes.c_uint64(rid), ctypes.byref(g)), "eg_get_graph")
         return out
+
+    def path_count(self, rid: int) -> int:
+        """Number of path vertices of a result computed with EG_FLAG_PATHS."""
+        nv = ctypes.c_uint64()
+        _check(self._lib.eg_get_paths(self._h, ctypes.c_uint64(rid), None, None, ctypes.byref(nv)), "eg_get_paths")
+        return int(nv.value)
+
+    def get_paths(self, rid: int):
+        """Arc geometry of a result computed with EG_FLAG_PATHS: (path_ptr
+        uint64[n_paths + 1], path_vtx uint32[...]); path p is
+        path_vtx[path_ptr[p]:path_ptr[p + 1]] = saddle, representative, ...,
+        maximum."""
+        nv = ctypes.c_uint64()
+        _check(self._lib.eg_get_paths(self._h, ctypes.c_uint64(rid), None, None, ctypes.byref(nv)), "eg_get_paths")
+        g = EGGraphC()
+        _check(self._lib.eg_get_graph(self._h, ctypes.c_uint64(rid), ctypes.byref(g)), "eg_get_graph")
+        ptr = np.empty(g.n_paths + 1, np.uint64)
+        vtx = np.empty(max(1, nv.value), np.uint32)[:nv.value]
+        _check(self._lib.eg_get_paths(self._h, ctypes.c_uint64(rid), ctypes.c_void_p(ptr.ctypes.data),
+                                      ctypes.c_void_p(vtx.ctypes.data), ctypes.byref(nv)), "eg_get_paths")
+        return ptr, vtx
 
     def get_graph_device(self, rid: int) -> EGGraphC:
         g = EGGraphC()
