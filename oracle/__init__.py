@@ -159,6 +159,32 @@ def compute(field: np.ndarray, extents=None, naive: bool = False,
         lib.eo_free(h)
 
 
+def bundle(g: OracleGraph, minimum: bool = False) -> np.ndarray:
+    """Arc bundling (Sec. 3.5): when several saddles connect the same two
+    maxima, only the highest of them (value, then index; lowest for the
+    minimum graph) stands for that pair.  A saddle is kept when it stands for
+    at least one pair of its arc ends; a saddle whose arcs all end at one
+    maximum connects no pair and is kept.  Returns uint8[S], 1 = kept.
+    Plain loops: for small fields only."""
+    def higher(i):
+        v, s = float(g.sad_val[i]), int(g.saddles[i])
+        return (-v, -s) if minimum else (v, s)
+
+    best = {}
+    ends = [g.col[g.row_ptr[i]:g.row_ptr[i + 1]].tolist() for i in range(g.saddles.size)]
+    for i, e in enumerate(ends):
+        for a in range(len(e)):
+            for b in range(a + 1, len(e)):
+                pair = (e[a], e[b])
+                if pair not in best or higher(i) > higher(best[pair]):
+                    best[pair] = i
+    keep = np.zeros(g.saddles.size, np.uint8)
+    for i, e in enumerate(ends):
+        pairs = [(e[a], e[b]) for a in range(len(e)) for b in range(a + 1, len(e))]
+        keep[i] = 1 if not pairs or any(best[p] == i for p in pairs) else 0
+    return keep
+
+
 def neighbour_offsets(d: int) -> np.ndarray:
     """Offsets kept by Algorithm 1 against the origin, shape (2(2^d-1), d)."""
     lib = _load()

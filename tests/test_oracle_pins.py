@@ -20,7 +20,7 @@ import pytest
 
 import oracle
 from paper_2303_02724_gb300 import fields as F
-from tests.brute import brute_graph, alg1_adjacent
+from tests.brute import alg1_adjacent, brute_graph, sos_rank
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -299,3 +299,48 @@ def test_errors():
         oracle.compute(np.zeros(4, np.float32), extents=(0, 4))
     with pytest.raises(oracle.OracleError):
         oracle.compute(np.zeros(4, np.float32), extents=(1,) * 7)
+
+
+# ------------------------------------------------------------ arc bundling ---
+
+@pytest.mark.parametrize("shape", [(8, 8), (12, 10), (6, 5, 4), (4, 4, 3), (3, 3, 3, 3), (5, 4, 3, 3)],
+                         ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("kind", ["normal", "ties"])
+@pytest.mark.parametrize("minimum", [False, True])
+def test_bundling_brute_force(shape, kind, minimum):
+    """Sec. 3.5 restated on the brute-force graph: for every pair of maxima
+    joined by some saddle, the rank-highest saddle joining it is kept (so the
+    pair stays connected), and every kept saddle with two or more arc ends is
+    that highest saddle for at least one of its pairs."""
+    seed = zlib.crc32(repr((shape, kind, "bundle")).encode()) % 1000
+    f = (F.white_noise(shape, seed) if kind == "normal" else F.integer_ties(shape, seed, 3)).values
+    g = oracle.compute(f, extents=shape, minimum=minimum)
+    keep = oracle.bundle(g, minimum=minimum)
+    b = brute_graph(f, shape, minimum=minimum)
+    rank = sos_rank(np.asarray(f, np.float32).reshape(-1).astype(np.float64), minimum)
+    ends = {s: sorted({m for (t, m) in b["arcs"] if t == s}) for s in b["saddles"]}
+    kept = {int(s) for s, k in zip(g.saddles.tolist(), keep.tolist()) if k}
+    pairs = {}
+    for s, e in ends.items():
+        for x in range(len(e)):
+            for y in range(x + 1, len(e)):
+                pairs.setdefault((e[x], e[y]), []).append(s)
+    for pr, ss in pairs.items():
+        top = max(ss, key=lambda s: rank[s])
+        assert top in kept, (pr, ss)
+    for s in kept:
+        e = ends[s]
+        if len(e) >= 2:
+            assert any(max(pairs[(e[x], e[y])], key=lambda t: rank[t]) == s
+                       for x in range(len(e)) for y in range(x + 1, len(e)))
+    for s, e in ends.items():
+        if len(e) < 2:
+            assert s in kept
+    assert len(kept) <= len(ends)
+
+
+def test_bundling_keeps_single_pair_saddle_structure():
+    # 1D: every pair of adjacent maxima has exactly one saddle between them
+    f = np.array([0, 5, 1, 4, 2, 8, 3], np.float32)
+    g = oracle.compute(f)
+    assert oracle.bundle(g).tolist() == [1, 1]
