@@ -383,6 +383,8 @@ def main():
     ap.add_argument("--ref-sample-vertices", type=int, default=2 * 1024 * 1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--bundle", action="store_true",
+                    help="also time arc bundling (eg_get_bundled) on one result of the workload")
     ap.add_argument("--paths", action="store_true",
                     help="also gather the arc geometry (EG_FLAG_PATHS) in every timed step")
     ap.add_argument("--batch-count", type=int, default=256)
@@ -489,6 +491,20 @@ def main():
     pb = path_bytes(counts)
     path_achieved = pb / (mean_step_ms / 1e3) / 1e9
 
+    bundle = None
+    if args.bundle:
+        rid, g = step()
+        h.get_bundled(rid)  # warm-up
+        torch.cuda.synchronize(dev)
+        reps = 5
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            keep = h.get_bundled(rid)
+        bms = (time.perf_counter() - t0) / reps * 1e3
+        h.release(rid)
+        bundle = {"ms": bms, "timing": "host wall clock per eg_get_bundled call (device work, two waits, "
+                  "copy of the keep mask)", "saddles": int(keep.size), "kept": int(keep.sum())}
+
     # end to end through the C ABI with host buffers: H2D of the field and
     # D2H of the graph inside the timed region
     e2e = None
@@ -582,6 +598,8 @@ def main():
             "clocks": clk,
             "cpu_baseline": cpu,
         }
+        if bundle is not None:
+            line["bundle"] = bundle
         print(json.dumps(line), flush=True)
     h.close()
     if dist is not None:

@@ -186,6 +186,19 @@ EG_API eg_status eg_get_graph_device(eg_handle h, eg_result_id id, eg_graph *out
 EG_API eg_status eg_get_paths(eg_handle h, eg_result_id id, uint64_t *path_ptr, uint32_t *path_vtx,
                               uint64_t *n_path_vertices);
 
+/* Arc bundling (Sec. 3.5) on a finished result: when several saddles connect
+ * the same two maxima, only the highest of them (value, then index; the
+ * lowest for a minimum graph) stands for that pair.  keep[i] (caller-owned
+ * host memory, n_saddles bytes, in the order of eg_graph.saddles) is set to
+ * 1 when saddle i stands for at least one pair of its arc ends, or connects
+ * no pair (all its arcs end at one maximum), else 0; the bundled graph is the
+ * kept saddles with their arcs.  Runs on the device (a hash table over the
+ * pairs of maxima) on the handle's own stream and waits for it.
+ * Errors: EG_ERR_ARG (unknown id, NULL keep with saddles present),
+ * EG_ERR_OOM, EG_ERR_INTERNAL (table overflow; cannot happen), plus any
+ * deferred device status as eg_get_graph. */
+EG_API eg_status eg_get_bundled(eg_handle h, eg_result_id id, uint8_t *keep);
+
 /* Autotuner: time candidate values of every eg_config knob on this batch of
  * fields (coordinate descent over the knobs, each candidate a full run of the
  * pipeline timed with CUDA events on `stream`), keep the fastest in the

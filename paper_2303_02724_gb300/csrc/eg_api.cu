@@ -1210,6 +1210,57 @@ eg_status eg_get_paths(eg_handle h, eg_result_id id, uint64_t *path_ptr, uint32_
     return e == cudaSuccess ? EG_OK : from_cuda(e);
 }
 
+eg_status eg_get_bundled(eg_handle h, eg_result_id id, uint8_t *keep)
+{
+    if (!h) return EG_ERR_ARG;
+    std::lock_guard<std::mutex> g(h->mu);
+    cudaSetDevice(h->device);
+    auto it = h->results.find(id);
+    if (it == h->results.end()) return EG_ERR_ARG;
+    Result &r = *it->second;
+    eg_status s = collect(h, r);
+    if (s != EG_OK) return s;
+    if (r.S == 0) return EG_OK;
+    if (!keep) return EG_ERR_ARG;
+    cudaStream_t st = h->side;
+    void *small = nullptr, *keys = nullptr, *best = nullptr, *dkeep = nullptr;
+    auto done = [&](eg_status x) {
+        cudaStreamSynchronize(st);
+        for (void *p : {small, keys, best, dkeep}) h->pool.release(p);
+        return x;
+    };
+    cudaError_t e;
+    // [0] pair count, [1] status word
+    if ((e = h->pool.alloc(&small, 16)) != cudaSuccess) return done(from_cuda(e));
+    unsigned long long *cnt = static_cast<unsigned long long *>(small);
+    uint32_t *err = reinterpret_cast<uint32_t *>(cnt + 1);
+    if ((e = cudaMemsetAsync(small, 0, 16, st)) != cudaSuccess) return done(from_cuda(e));
+    const uint64_t *row_ptr = static_cast<const uint64_t *>(r.row_ptr);
+    if ((e = launch_bundle_pairs(row_ptr, r.S, cnt, st)) != cudaSuccess) return done(from_cuda(e));
+    unsigned long long pairs = 0;
+    if ((e = cudaMemcpyAsync(&pairs, cnt, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return done(from_cuda(e));
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return done(from_cuda(e));
+    uint32_t lg = 10;
+    while ((1ull << lg) < 2 * pairs) lg++;
+    const size_t tb = size_t(8) << lg;
+    if ((e = h->pool.alloc(&keys, tb)) != cudaSuccess) return done(from_cuda(e));
+    if ((e = h->pool.alloc(&best, tb)) != cudaSuccess) return done(from_cuda(e));
+    if ((e = h->pool.alloc(&dkeep, r.S)) != cudaSuccess) return done(from_cuda(e));
+    if ((e = cudaMemsetAsync(keys, 0xff, tb, st)) != cudaSuccess) return done(from_cuda(e));
+    if ((e = cudaMemsetAsync(best, 0, tb, st)) != cudaSuccess) return done(from_cuda(e));
+    if ((e = launch_bundle(row_ptr, static_cast<const uint32_t *>(r.col), static_cast<const uint32_t *>(r.saddles),
+                           static_cast<const float *>(r.sad_val), r.S, (r.flags & kFlagMinimum) != 0,
+                           static_cast<unsigned long long *>(keys), static_cast<unsigned long long *>(best), lg,
+                           static_cast<uint8_t *>(dkeep), err, st)) != cudaSuccess)
+        return done(from_cuda(e));
+    h->launches += 3;
+    uint32_t herr = 0;
+    if ((e = cudaMemcpyAsync(keep, dkeep, r.S, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return done(from_cuda(e));
+    if ((e = cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return done(from_cuda(e));
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return done(from_cuda(e));
+    return done(herr ? EG_ERR_INTERNAL : EG_OK);
+}
+
 eg_status eg_get_graph_device(eg_handle h, eg_result_id id, eg_graph *out)
 {
     if (!h || !out) return EG_ERR_ARG;

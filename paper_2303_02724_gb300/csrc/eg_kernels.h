@@ -54,4 +54,11 @@ cudaError_t launch_path_scan(const FieldDev *fields, int nf, cudaStream_t st);
 cudaError_t launch_path_write(int kd, const FieldDev *fields, int nf, uint64_t base, uint64_t bricks,
                               cudaStream_t st);
 
+// Arc bundling on a finished graph: pair count (added to *count), then the
+// hash-table passes (keys preset to all ones, best to zero, 2^lg slots).
+cudaError_t launch_bundle_pairs(const uint64_t *row_ptr, uint64_t S, unsigned long long *count, cudaStream_t st);
+cudaError_t launch_bundle(const uint64_t *row_ptr, const uint32_t *col, const uint32_t *saddles,
+                          const float *sad_val, uint64_t S, bool minimum, unsigned long long *keys,
+                          unsigned long long *best, uint32_t lg, uint8_t *keep, uint32_t *err, cudaStream_t st);
+
 }  // namespace eg

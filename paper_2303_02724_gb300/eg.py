@@ -73,6 +73,7 @@ SIGNATURES = {
     "eg_get_graph": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(EGGraphC)]),
     "eg_get_graph_device": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(EGGraphC)]),
     "eg_get_paths": (ctypes.c_int, [_P, ctypes.c_uint64, _P, _P, ctypes.POINTER(ctypes.c_uint64)]),
+    "eg_get_bundled": (ctypes.c_int, [_P, ctypes.c_uint64, _P]),
     "eg_release": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "eg_workspace_bytes": (ctypes.c_uint64, [ctypes.c_int, _P]),
     "eg_mem_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
@@ -311,6 +312,15 @@ class Handle:
         g.labels = out.labels.ctypes.data if labels else None
         _check(self._lib.eg_get_graph(self._h, ctypes.c_uint64(rid), ctypes.byref(g)), "eg_get_graph")
         return out
+
+    def get_bundled(self, rid: int) -> np.ndarray:
+        """Arc bundling of a finished result: uint8 per saddle, 1 = kept."""
+        g = EGGraphC()
+        _check(self._lib.eg_get_graph(self._h, ctypes.c_uint64(rid), ctypes.byref(g)), "eg_get_graph")
+        keep = np.empty(max(1, g.n_saddles), np.uint8)
+        _check(self._lib.eg_get_bundled(self._h, ctypes.c_uint64(rid), ctypes.c_void_p(keep.ctypes.data)),
+               "eg_get_bundled")
+        return keep[:g.n_saddles]
 
     def path_count(self, rid: int) -> int:
         """Number of path vertices of a result computed with EG_FLAG_PATHS."""
