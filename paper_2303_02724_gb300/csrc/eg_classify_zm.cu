@@ -191,24 +191,45 @@ __device__ __forceinline__ float min7x2(const float (&v)[14])
     return fminf(min3f(a, b, v[12]), min3f(c, d, v[13]));
 }
 
+// The 14 neighbour values of column xx of ring row `row` of plane buffer C (D
+// and U at float offsets dD, dU from C), in slot order.
+__device__ __forceinline__ void ring_nbrs(const float *row, int xx, int rs, int dD, int dU, float (&nb)[14])
+{
+    const int cm = zm_col(xx - 1), c0 = zm_col(xx), cp = zm_col(xx + 1);
+    const float *d0 = row + dD - rs, *d1 = row + dD;
+    const float *r0 = row - rs, *r2 = row + rs;
+    const float *u1 = row + dU, *u2 = row + dU + rs;
+    // (-1,-1,-1) (0,-1,-1) (-1,0,-1) (0,0,-1) (-1,-1,0) (0,-1,0) (-1,0,0)
+    // (1,0,0) (0,1,0) (1,1,0) (0,0,1) (1,0,1) (0,1,1) (1,1,1)
+    nb[0] = d0[cm];
+    nb[1] = d0[c0];
+    nb[2] = d1[cm];
+    nb[3] = d1[c0];
+    nb[4] = r0[cm];
+    nb[5] = r0[c0];
+    nb[6] = row[cm];
+    nb[7] = row[cp];
+    nb[8] = r2[c0];
+    nb[9] = r2[cp];
+    nb[10] = u1[c0];
+    nb[11] = u1[cp];
+    nb[12] = u2[c0];
+    nb[13] = u2[cp];
+}
+
 // Highest slot of `mask` (value, then rank; the minimum graph takes the
-// lowest value and the lowest rank), reading the values straight from the
-// ring: neighbour k of column xx of ring row `row` is at row + roff[k] (plane
-// and row step), column xx + rdx[k].
+// lowest value and the lowest rank).
 template <bool MIN>
-__device__ __forceinline__ int masked_top(const float *row, int xx, uint32_t mask, const int *roff, const int *rdx)
+__device__ __forceinline__ int masked_top(const float (&nb)[14], uint32_t mask)
 {
     float best = 0.f;
     int rk = -1;
-    while (mask) {
-        const int k = __ffs(mask) - 1;
-        mask &= mask - 1u;
-        const float v = row[roff[k] + zm_col(xx + rdx[k])];
-        if (rk < 0 || (MIN ? v < best : v >= best)) {
-            best = v;
+#pragma unroll
+    for (int k = 0; k < 14; k++)
+        if (((mask >> k) & 1u) && (rk < 0 || (MIN ? nb[k] < best : nb[k] >= best))) {
+            best = nb[k];
             rk = k;
         }
-    }
     return rk;
 }
 
@@ -216,27 +237,25 @@ __device__ __forceinline__ int masked_top(const float *row, int xx, uint32_t mas
 // (UpperLinkRep, Sec. 3.4), packed as 5-bit slots with beta0+ in bits 56..59.
 // first: the gradient slot (highest of all upper neighbours, hence the
 // representative of its component); cls: 1 when the table says exactly two
-// components.  comp2[m]: for a mask with exactly two components, the
-// component holding the lowest set bit (host-built table).
+// components.  low[m] (host-built table): the component of mask m holding
+// m's lowest set bit; a2 = low[upper].  Removing whole components leaves the
+// others intact, so low[] peels them off one by one.
 template <bool MIN>
-__device__ __forceinline__ uint64_t saddle_info(const float *row, int xx, const int *roff, const int *rdx,
-                                                uint32_t upper, int first, uint32_t cls, const uint32_t *s_adj,
-                                                const uint16_t *comp2)
+__device__ __forceinline__ uint64_t saddle_info(const float (&nb)[14], uint32_t upper, int first, uint32_t cls,
+                                                uint32_t a2, const uint16_t *low)
 {
     uint64_t codes = uint64_t(first);
     if (cls == 1) {
-        const uint32_t a = __ldg(comp2 + upper);
-        const uint32_t other = ((a >> first) & 1u) ? (upper ^ a) : a;
-        codes |= uint64_t(masked_top<MIN>(row, xx, other, roff, rdx)) << 5;
+        const uint32_t other = ((a2 >> first) & 1u) ? (upper ^ a2) : a2;
+        codes |= uint64_t(masked_top<MIN>(nb, other)) << 5;
         return (2ull << 56) | codes;
     }
-    const uint32_t comp = link_flood(1u << first, upper, s_adj);
     int b0 = 1;
-    uint32_t left = upper & ~comp;
-    while (left) {
-        const uint32_t c2 = link_flood(left & (~left + 1u), upper, s_adj);
-        left &= ~c2;
-        codes |= uint64_t(masked_top<MIN>(row, xx, c2, roff, rdx)) << (5 * b0);
+    for (uint32_t left = upper, c = a2; left; c = left ? uint32_t(__ldg(low + left)) : 0u) {
+        c = (c & left) ? (c & left) : left;  // (never empty; guarantees progress)
+        left &= ~c;
+        if ((c >> first) & 1u) continue;  // the gradient's component: coded first
+        codes |= uint64_t(masked_top<MIN>(nb, c)) << (5 * b0);
         b0++;
     }
     return (uint64_t(b0) << 56) | codes;
@@ -252,10 +271,7 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
     extern __shared__ float4 zm_smem4[];
     float *ring = reinterpret_cast<float *>(zm_smem4);
     __shared__ uint32_t s_lut[1024];
-    __shared__ uint32_t s_adj[14];
     __shared__ uint32_t s_off[14];
-    __shared__ int s_roff[14];  // ring offset (plane, row) of neighbour slot k from the centre row (this step)
-    __shared__ int s_rdx[14];   // column step of neighbour slot k
     __shared__ uint32_t s_warp[kZmThreads / 32];
     __shared__ unsigned s_cnt[4];
     // per-vertex classification of this step (upper mask | gradient slot << 14 |
@@ -266,7 +282,6 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint16_t *comp2 = reinterpret_cast<const uint16_t *>(lut + 1024);
     for (int i = tid; i < 1024; i += kZmThreads) s_lut[i] = __ldg(lut + i);
-    if (tid < 14) s_adj[tid] = Nbr<3>::adj_mask(tid);
     // persistent work queue: take items in ticket order until none are left
     while (true) {
     __syncthreads();
@@ -327,13 +342,6 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
             F.bcnt[prev_brick] = make_uint4(s_cnt[0], s_cnt[1] - s_cnt[0], s_cnt[2], 0u);
             s_cnt[0] = s_cnt[1] = s_cnt[2] = s_cnt[3] = 0;
         }
-        if (tid < 14) {
-            const uint32_t p = Nbr<3>::pat(tid);
-            const int plane = (p & 4u) ? int(((Nbr<3>::neg(tid) ? z - 1 : z + 1) & 3) - (z & 3)) * int(G.rb) : 0;
-            const int dy = (p & 2u) ? int(rs) : 0, dx = (p & 1u) ? 1 : 0;
-            s_roff[tid] = plane + (Nbr<3>::neg(tid) ? -dy : dy);
-            s_rdx[tid] = Nbr<3>::neg(tid) ? -dx : dx;
-        }
         zm_load_plane(F, G, P, ring + ((z + 2) & 3) * G.rb, z + 2, y0, ylo, yhi, vec);
         cp_async_wait1();
         __syncthreads();  // B: plane z+1 visible, counters reset
@@ -341,6 +349,7 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
         const float *Db = ring + ((z - 1) & 3) * G.rb + 8;
         const float *Cb = ring + (z & 3) * G.rb + 8;
         const float *Ub = ring + ((z + 1) & 3) * G.rb + 8;
+        const int dD = int(Db - Cb), dU = int(Ub - Cb);
         const uint32_t brick = uint32_t(z) * F.nyb + yb;
         const uint64_t slot0 = uint64_t(brick) * F.bcap;
         const bool rowok = active && r < brows;
@@ -523,8 +532,11 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
                 F.rec_val[q] = orow[zm_col(int(ox + i))];
                 uint64_t inf = 0;
                 if (upper) {
-                    inf = saddle_info<MIN>(orow, int(ox + i), s_roff, s_rdx, upper, int(sl & 15u), sl >> 4, s_adj,
-                                           comp2);
+                    const uint32_t cls = sl >> 4;
+                    const uint32_t a2 = __ldg(comp2 + upper);
+                    float nb[14];
+                    ring_nbrs(orow, int(ox + i), int(rs), dD, dU, nb);
+                    inf = saddle_info<MIN>(nb, upper, int(sl & 15u), cls, a2, comp2);
                     np += uint32_t(inf >> 56);
                 }
                 F.rec_info[q] = inf;
