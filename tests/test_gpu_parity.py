@@ -102,6 +102,17 @@ def test_layouts(handle, case):
     assert_same(run_gpu(handle, f.values), oracle.compute(f.values))
 
 
+@pytest.mark.parametrize("n0", [1, 3, 4, 8, 12, 20, 36, 100, 252, 512, 1020, 1021, 1024, 1025])
+def test_row_lengths(handle, n0):
+    """Every row-length regime of the plane-marching classifier: 16-byte rows
+    (n0 % 4 == 0, with a half-filled last 8-column group when n0 % 8 == 4),
+    4-byte rows, one vertex per row (126-row bricks), the 1024-vertex limit,
+    and the flat classifier just past it; 13 rows and 7 planes leave partial
+    row blocks and work items."""
+    f = F.white_noise((7, 13, n0), 1000 + n0)
+    assert_same(run_gpu(handle, f.values), oracle.compute(f.values))
+
+
 def test_unaligned_field_pointer(handle):
     f = F.config_3d_256(side=36)
     flat = torch.from_numpy(np.concatenate([[0.0], f.values.reshape(-1)]).astype(np.float32)).cuda()
