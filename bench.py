@@ -392,6 +392,8 @@ def main():
     ap.add_argument("--ref-sample-vertices", type=int, default=2 * 1024 * 1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-threads", type=int, default=4,
+                    help="host threads (one library handle each) taking turns in the end-to-end loop")
     ap.add_argument("--bundle", action="store_true",
                     help="also time arc bundling (eg_get_bundled) on one result of the workload")
     ap.add_argument("--paths", action="store_true",
@@ -523,15 +525,16 @@ def main():
         # output buffers (allocated once, reused), take alternate steps, so one
         # step's upload and kernels overlap the other's kernels and download
         import threading
-        hs = [h, eg.Handle(local)]
-        sts = [stream, torch.cuda.Stream(device=dev)]
+        nw = max(1, args.e2e_threads)
+        hs = [h] + [eg.Handle(local) for _ in range(nw - 1)]
+        sts = [stream] + [torch.cuda.Stream(device=dev) for _ in range(nw - 1)]
         outbs = [eg.GraphBuffers(counts["n_maxima"], counts["n_saddles"], counts["n_arcs"], pinned=True)
                  for _ in hs]
 
         def e2e_worker(w, k_steps, errs):
             try:
                 torch.cuda.set_device(dev)
-                for _ in range(w, k_steps, 2):
+                for _ in range(w, k_steps, nw):
                     rid = hs[w].compute_host(host, sts[w])
                     hs[w].get_graph(rid, labels=False, buffers=outbs[w])
                     hs[w].release(rid)
@@ -540,7 +543,7 @@ def main():
 
         def e2e_run(k_steps):
             errs = []
-            th = [threading.Thread(target=e2e_worker, args=(w, k_steps, errs)) for w in range(2)]
+            th = [threading.Thread(target=e2e_worker, args=(w, k_steps, errs)) for w in range(nw)]
             for t in th:
                 t.start()
             for t in th:
@@ -548,7 +551,7 @@ def main():
             if errs:
                 raise errs[0]
 
-        e2e_run(4)
+        e2e_run(2 * nw)
         torch.cuda.synchronize(dev)
         if dist is not None:
             dist.barrier()
@@ -556,7 +559,8 @@ def main():
         e2e_run(args.steps)
         torch.cuda.synchronize(dev)
         e2e_s = time.perf_counter() - t0
-        hs[1].close()
+        for hx in hs[1:]:
+            hx.close()
         if dist is not None:
             t = torch.tensor([e2e_s], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -565,8 +569,8 @@ def main():
 
         e2e = {"value": e2e_value, "unit": "Mvertices/s", "h2d_bytes_per_step": 4 * N,
                "d2h_bytes_per_step": graph_d2h_bytes(counts),
-               "mode": "eg_compute_host + eg_get_graph + eg_release per step, pinned host buffers; two host "
-                       "threads with a handle each take alternate steps, so uploads, kernels and downloads "
+               "mode": "eg_compute_host + eg_get_graph + eg_release per step, pinned host buffers; "
+                       f"{nw} host threads with a handle each take turns, so uploads, kernels and downloads "
                        "of consecutive steps overlap"}
 
     cpu = None
