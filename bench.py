@@ -40,7 +40,7 @@ WORKLOADS = {
                "L2, a few GB on the device)"),
     "serve": ("Served stream: requests with Poisson arrivals, each a float32 2D/3D/4D field (vertex count "
               "log-uniform 1e4..1e7, sums of U{4..64} Gaussians + 1e-3 uniform noise), seed 4; admission by "
-              "free HBM, continuous batching on two engines"),
+              "free HBM, continuous batching on two engines, results kept in device memory"),
     "batch": ("Batched: 256 float32 fields, 2D (side log-uniform 64..2048) or 3D (side log-uniform 32..256) "
               "50/50, sums of U{4..64} Gaussians + 1e-3 uniform noise, seed 3; one submission (persistent "
               "work-queue classifier, captured CUDA graphs, knobs autotuned on the batch) vs per-field plain "
@@ -350,14 +350,18 @@ def run_serve(args, ws, rank, local):
     vals = serve_fields(args.serve_requests)
     nv = sum(int(v.size) for v in vals)
     free, _total = torch.cuda.mem_get_info(local)
-    engines = [serve.GpuEngine(local), serve.GpuEngine(local)]
+    # results stay in device memory (the client releases them once consumed)
+    engines = [serve.GpuEngine(local, results="device"), serve.GpuEngine(local, results="device")]
     budget = int(free * 0.6)
 
     def run(offsets):
         srv = serve.Server(engines, budget_bytes=budget, max_batch=64, max_batch_vertices=1 << 27)
-        serve.replay(srv, vals, offsets)
+        reqs = serve.replay(srv, vals[:len(offsets)], offsets)
         srv.drain(3600)
         srv.close()
+        for r in reqs:
+            if r.result is not None:
+                r.result.release()
         return srv.stats()
 
     run(np.zeros(min(len(vals), 64)))  # warm-up (pools, kernels)
@@ -370,6 +374,26 @@ def run_serve(args, ws, rank, local):
         res[str(frac)] = run(offs)
     for e in engines:
         e.close()
+    # the same requests one at a time through the plain path (upload, compute,
+    # wait, release), for comparison with the served throughput
+    from paper_2303_02724_gb300 import eg
+    hp = eg.Handle(local)
+    dev = torch.device("cuda", local)
+    for v in vals[:16]:
+        rid = hp.compute(torch.from_numpy(v).to(dev))
+        hp.get_graph_device(rid)
+        hp.release(rid)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for v in vals:
+        rid = hp.compute(torch.from_numpy(v).to(dev))
+        hp.get_graph_device(rid)
+        hp.release(rid)
+    torch.cuda.synchronize(dev)
+    plain_s = time.perf_counter() - t0
+    hp.close()
+    plain = {"throughput_mvps": nv / plain_s / 1e6, "seconds": plain_s,
+             "mode": "each request alone: upload, eg_compute, wait, release"}
     if rank == 0:
         line = {"metric": "served throughput (Mvertices/s) and latency", "value": cap["throughput_mvps"],
                 "unit": "Mvertices/s", "n_gpus": ws, "steps": len(args.serve_fractions) + 1, "warmup": 1,
@@ -377,7 +401,8 @@ def run_serve(args, ws, rank, local):
                 "data": "synthetic",
                 "config": {"workload": WORKLOADS["serve"], "requests": len(vals), "vertices": nv,
                            "budget_bytes": budget, "engines": len(engines)},
-                "capacity": cap, "poisson": res}
+                "capacity": cap, "poisson": res, "plain_one_by_one": plain,
+                "speedup_vs_plain": cap["throughput_mvps"] / plain["throughput_mvps"]}
         print(json.dumps(line), flush=True)
 
 

@@ -29,6 +29,29 @@ import numpy as np
 EG_ERR_BUSY = 7
 
 
+class DeviceResult:
+    """A served result kept in device memory (the library's buffers) until
+    release(): counts and device pointers of the graph (eg_get_graph_device),
+    and to_host() for a host copy when the client wants one."""
+
+    def __init__(self, engine, rid, graph_c):
+        self.engine, self.rid, self.graph = engine, rid, graph_c
+        self._lock = threading.Lock()
+        self.released = False
+
+    def to_host(self, labels: bool = False):
+        with self._lock:
+            if self.released:
+                raise RuntimeError("result already released")
+            return self.engine.handle.get_graph(self.rid, labels=labels)
+
+    def release(self):
+        with self._lock:
+            if not self.released:
+                self.engine.handle.release(self.rid)
+                self.released = True
+
+
 @dataclass
 class Request:
     values: np.ndarray                 # float32 field, numpy shape = reversed(extents)
@@ -58,14 +81,21 @@ def request_bytes(n_vertices: int, d: int) -> int:
 
 
 class GpuEngine:
-    """Runs batches through the CUDA library on one stream with its own handle."""
+    """Runs batches through the CUDA library on one stream with its own handle.
 
-    def __init__(self, device: int = 0, minimum: bool = False):
+    results="host": every request's graph is copied to numpy arrays and its
+    device state freed.  results="device": the graph stays in device memory
+    (a DeviceResult) until the client releases it."""
+
+    def __init__(self, device: int = 0, minimum: bool = False, results: str = "host"):
         import torch
         from . import eg
+        if results not in ("host", "device"):
+            raise ValueError("results must be 'host' or 'device'")
         self.torch = torch
         self.eg = eg
         self.device = device
+        self.results = results
         self.handle = eg.Handle(device, minimum=minimum)
         self.stream = torch.cuda.Stream(device=device)
 
@@ -74,12 +104,18 @@ class GpuEngine:
         with torch.cuda.stream(self.stream):
             ts = [torch.from_numpy(r.values).to(self.device) for r in reqs]
             ids = self.handle.batch_submit(ts, self.stream)
+            keep = []
             try:
                 for r, rid in zip(reqs, ids):
-                    r.result = self.handle.get_graph(rid, labels=False)
+                    if self.results == "host":
+                        r.result = self.handle.get_graph(rid, labels=False)
+                    else:
+                        r.result = DeviceResult(self, rid, self.handle.get_graph_device(rid))
+                        keep.append(rid)
             finally:
                 for rid in ids:
-                    self.handle.release(rid)
+                    if rid not in keep:
+                        self.handle.release(rid)
         del ts
 
     def close(self):

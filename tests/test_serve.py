@@ -76,7 +76,8 @@ def test_poisson_arrivals_rate():
 
 
 @pytest.mark.gpu
-def test_served_results_equal_alone():
+@pytest.mark.parametrize("results", ["host", "device"])
+def test_served_results_equal_alone(results):
     torch = pytest.importorskip("torch")
     from paper_2303_02724_gb300 import _build, eg
     assert torch.cuda.is_available()
@@ -87,18 +88,22 @@ def test_served_results_equal_alone():
     with eg.Handle(0) as h:
         for v in vals:
             alone.append(h.graph_of(torch.from_numpy(v).cuda(), labels=False))
-    engines = [serve.GpuEngine(0), serve.GpuEngine(0)]
+    engines = [serve.GpuEngine(0, results=results), serve.GpuEngine(0, results=results)]
     srv = serve.Server(engines, budget_bytes=1 << 34, max_batch=8)
     out = serve.replay(srv, vals, serve.poisson_arrivals(2000.0, len(vals), 1))
     assert srv.drain(120)
     srv.close()
-    for e in engines:
-        e.close()
     st = srv.stats()
     assert st["requests"] == len(vals) and st["failed"] == 0
     for r, g in zip(out, alone):
         assert r.status == 0
+        got = r.result if results == "host" else r.result.to_host()
+        if results == "device":
+            assert r.result.graph.n_saddles == g.saddles.size
+            r.result.release()
         for k in ["maxima", "saddles", "sad_b0", "row_ptr", "col"]:
-            assert np.array_equal(getattr(r.result, k), getattr(g, k)), k
-        assert np.array_equal(r.result.max_val.view(np.uint32), g.max_val.view(np.uint32))
+            assert np.array_equal(getattr(got, k), getattr(g, k)), k
+        assert np.array_equal(got.max_val.view(np.uint32), g.max_val.view(np.uint32))
+    for e in engines:
+        e.close()
     assert st["batches"] < len(vals)  # requests shared batches
