@@ -96,7 +96,9 @@ class GpuEngine:
         self.eg = eg
         self.device = device
         self.results = results
-        self.handle = eg.Handle(device, minimum=minimum)
+        # every batch of a request stream has its own layout, so capturing a
+        # CUDA graph per batch would never be repaid by a replay: launch directly
+        self.handle = eg.Handle(device, minimum=minimum, config=eg.EGConfig(flags=eg.EG_FLAG_NO_GRAPH))
         self.stream = torch.cuda.Stream(device=device)
 
     def run(self, reqs: List[Request]) -> None:
