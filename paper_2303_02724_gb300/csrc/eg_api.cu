@@ -919,7 +919,7 @@ eg_status eg_create(eg_handle *out, int device, const eg_config *cfg)
         // two, 2 three or more; then, as 16-bit words, the component holding
         // the lowest set bit of every non-empty mask
         std::vector<uint32_t> lut(1024 + 8192, 0u);
-        uint16_t *comp2 = reinterpret_cast<uint16_t *>(lut.data() + 1024);
+        uint16_t *lowc = reinterpret_cast<uint16_t *>(lut.data() + 1024);
         for (uint32_t m = 0; m < (1u << 14); m++) {
             uint32_t left = m, comps = 0, first_comp = 0;
             while (left) {
@@ -937,7 +937,7 @@ eg_status eg_create(eg_handle *out, int device, const eg_config *cfg)
             }
             const uint32_t cls = comps < 2 ? 0u : (comps == 2 ? 1u : 2u);
             lut[m >> 4] |= cls << ((m & 15) * 2);
-            comp2[m] = uint16_t(first_comp);
+            lowc[m] = uint16_t(first_comp);
         }
         if ((e = h->pool.alloc(&h->lut3, lut.size() * 4)) != cudaSuccess) return from_cuda(e);
         if ((e = cudaMemcpy(h->lut3, lut.data(), lut.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)

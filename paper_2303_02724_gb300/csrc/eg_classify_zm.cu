@@ -280,7 +280,7 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
 
     __shared__ unsigned long long s_item;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint16_t *comp2 = reinterpret_cast<const uint16_t *>(lut + 1024);
+    const uint16_t *lowc = reinterpret_cast<const uint16_t *>(lut + 1024);
     for (int i = tid; i < 1024; i += kZmThreads) s_lut[i] = __ldg(lut + i);
     // persistent work queue: take items in ticket order until none are left
     while (true) {
@@ -533,10 +533,10 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
                 uint64_t inf = 0;
                 if (upper) {
                     const uint32_t cls = sl >> 4;
-                    const uint32_t a2 = __ldg(comp2 + upper);
+                    const uint32_t a2 = __ldg(lowc + upper);
                     float nb[14];
                     ring_nbrs(orow, int(ox + i), int(rs), dD, dU, nb);
-                    inf = saddle_info<MIN>(nb, upper, int(sl & 15u), cls, a2, comp2);
+                    inf = saddle_info<MIN>(nb, upper, int(sl & 15u), cls, a2, lowc);
                     np += uint32_t(inf >> 56);
                 }
                 F.rec_info[q] = inf;

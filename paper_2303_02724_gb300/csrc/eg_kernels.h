@@ -12,7 +12,8 @@ namespace eg {
 cudaError_t launch_classify_flat(int kd, const FieldDev *fields, int nf, uint64_t bricks, cudaStream_t st);
 
 // Steps (a)+(c), plane-marching kernel for 2D/3D fields with rows of at most
-// 1024 vertices.  lut: 2^14-bit saddle table (eg_saddle_lut3).
+// 1024 vertices.  lut: the 2-bit class of every 14-bit upper mask (1024 words),
+// then, as 16-bit words, the component holding each mask's lowest set bit.
 size_t zm_smem_bytes(uint32_t n0, uint32_t ty);
 // Persistent: grid = min(total_items, sm_count * ctas_per_sm) CTAs take work
 // items from *ticket (zeroed before the launch).
