@@ -377,6 +377,7 @@ struct Plan {
     int nf = 0;
     std::vector<Group> groups;
     uint64_t total_bricks = 0, total_tiles = 0;
+    uint64_t total_rtiles = 0;  // tiled resolution pass (3D kernels)
     size_t desc_bytes = 0;
     int walks = 4, ctas = 3;
     std::string signature;  // identical for calls that can share a captured graph
@@ -415,6 +416,10 @@ eg_status enqueue_part(eg_ctx *h, int part, const Plan &P, const FieldDev *Dd, c
         if ((e = launch_scan(false, Dd, P.nf, P.total_tiles, h->ws_scan, st)) != cudaSuccess) return from_cuda(e);
         nl++;
     } else if (part == 1) {
+        if (P.total_rtiles) {
+            if ((e = launch_resolve_tiles(Dd, P.nf, P.total_rtiles, st)) != cudaSuccess) return from_cuda(e);
+            nl++;
+        }
         if ((e = launch_resolve(Dd, P.nf, P.total_bricks, P.walks, st)) != cudaSuccess) return from_cuda(e);
         nl++;
     } else {
@@ -670,6 +675,12 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
         F.stile0 = tile0;
         F.kd = ly.kd;
         F.flags = j.flags;
+        F.rtile0 = P.total_rtiles;
+        if (ly.kd == 3) {
+            uint64_t nt = 0;
+            resolve_tile_shape(F.n[0], F.n[1], F.n[2], F.rt, &nt);
+            P.total_rtiles += nt;
+        }
         G.count++;
         G.bricks += ly.nbricks;
         G.items += ly.zm ? uint64_t(ly.nyb) * ly.nzc : ly.nbricks;

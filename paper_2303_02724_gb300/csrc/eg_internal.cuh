@@ -91,6 +91,8 @@ struct FieldDev {
     uint64_t brick0;         // first global brick id of this field in its launch
     uint64_t item0;          // first classification work item of this field in its launch
     uint64_t stile0;         // first scan tile of this field (all fields of a call)
+    uint64_t rtile0;         // first resolution tile of this field (all fields of a call)
+    uint32_t rt[3];          // log2 of the resolution tile extents (3D kernels; 0 tiles for 4D)
     int32_t kd;              // kernel dimension (2D fields run as 3D)
     uint32_t flags;
 };

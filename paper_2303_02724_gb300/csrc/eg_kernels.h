@@ -43,6 +43,13 @@ cudaError_t launch_resolve_one(const FieldDev &F, cudaStream_t st);
 // Step (b): labels = fixed points of the gradient pointers (all fields).
 cudaError_t launch_resolve(const FieldDev *fields, int nf, uint64_t total_bricks, int walks, cudaStream_t st);
 
+// Step (b), tiled pass for fields with few maxima (long gradient paths), run
+// before launch_resolve: tiles numbered by FieldDev::rtile0 over all fields.
+cudaError_t launch_resolve_tiles(const FieldDev *fields, int nf, uint64_t tiles, cudaStream_t st);
+// Resolution tile extents (log2) of a field of extents n0 x n1 x n2, and the
+// number of its tiles.
+void resolve_tile_shape(uint32_t n0, uint32_t n1, uint32_t n2, uint32_t rt[3], uint64_t *tiles);
+
 // Steps (d)+(e): nodes and arc ends per brick (one kernel dimension), then CSR.
 cudaError_t launch_nodes_d(int kd, const FieldDev *fields, int nf, uint64_t base, uint64_t bricks, cudaStream_t st);
 cudaError_t launch_csr(const FieldDev *fields, int nf, uint64_t total_bricks, cudaStream_t st);
