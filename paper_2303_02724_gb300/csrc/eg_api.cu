@@ -151,7 +151,8 @@ struct Result {
     uint64_t N = 0;
     uint32_t flags = 0;
     void *lab = nullptr;
-    void *small = nullptr;  // SmallBlock on device
+    void *small = nullptr;  // its SmallBlock on the device (in the launch's array)
+    int slot = 0;           // index of that SmallBlock in the launch's array
     void *maxima = nullptr, *max_val = nullptr, *saddles = nullptr, *sad_b0 = nullptr, *sad_val = nullptr,
          *row_ptr = nullptr, *col = nullptr, *ends = nullptr, *ucnt = nullptr;
     void *path_ptr = nullptr, *path_vtx = nullptr, *pbrick = nullptr;  // arc geometry (EG_FLAG_PATHS)
@@ -162,11 +163,15 @@ struct Result {
     std::shared_ptr<struct Launch> launch;  // keeps the descriptor table alive
 };
 
-// Descriptor tables of one launch (shared by the results of a batch).
+// Descriptor tables of one launch (shared by the results of a batch), and
+// the results' SmallBlocks, one array read back once for all of them.
 struct Launch {
     void *desc_dev = nullptr;
     void *desc_host = nullptr;
     size_t bytes = 0;
+    void *smalls = nullptr;           // SmallBlock[nsmall] on the device
+    int nsmall = 0;
+    std::vector<SmallBlock> hsmall;   // host copy once the launch finished
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // step timing (optional)
     ~Launch()
     {
@@ -341,8 +346,8 @@ eg_status ensure_workspace(eg_ctx *h, uint64_t recs, uint64_t bricks, uint64_t t
 
 void free_result_buffers(eg_ctx *h, Result *r)
 {
-    void **bufs[] = {&r->lab,     &r->small, &r->maxima, &r->max_val,  &r->saddles,  &r->sad_b0, &r->sad_val,
-                     &r->row_ptr, &r->col,   &r->ends,   &r->ucnt,     &r->path_ptr, &r->path_vtx, &r->pbrick};
+    void **bufs[] = {&r->lab,  &r->maxima, &r->max_val, &r->saddles,  &r->sad_b0,   &r->sad_val, &r->row_ptr,
+                     &r->col,  &r->ends,   &r->ucnt,    &r->path_ptr, &r->path_vtx, &r->pbrick};
     for (void **b : bufs) {
         h->pool.release(*b);
         *b = nullptr;
@@ -354,7 +359,8 @@ void release_launch(eg_ctx *h, Launch *L)
     if (!L) return;
     h->pool.release(L->desc_dev);
     h->hpool.release(L->desc_host);
-    L->desc_dev = L->desc_host = nullptr;
+    h->pool.release(L->smalls);
+    L->desc_dev = L->desc_host = L->smalls = nullptr;
 }
 
 struct Job {
@@ -620,6 +626,8 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
     };
     if (!use_graph && (e = h->pool.alloc(&L->desc_dev, L->bytes)) != cudaSuccess) return fail(from_cuda(e));
     if ((e = h->hpool.alloc(&L->desc_host, L->bytes)) != cudaSuccess) return fail(from_cuda(e));
+    if ((e = h->pool.alloc(&L->smalls, sizeof(SmallBlock) * size_t(nf))) != cudaSuccess) return fail(from_cuda(e));
+    L->nsmall = nf;
     FieldDev *Dh = reinterpret_cast<FieldDev *>(L->desc_host);
     std::memset(Dh, 0, L->bytes);
 
@@ -642,7 +650,8 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
         r->flags = j.flags;
         r->launch = L;
         e = h->pool.alloc(&r->lab, j.sh.N * sizeof(uint32_t));
-        if (e == cudaSuccess) e = h->pool.alloc(&r->small, sizeof(SmallBlock));
+        r->small = static_cast<SmallBlock *>(L->smalls) + i;
+        r->slot = i;
         res[i] = std::move(r);
         if (e != cudaSuccess) return fail(from_cuda(e));
         Result &R = *res[i];
@@ -774,9 +783,7 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
         return fail(from_cuda(e));
     }
     cudaStreamWaitEvent(h->side, k1, 0);
-    for (int i = 0; i < nf; i++)
-        cudaMemcpyAsync(static_cast<SmallBlock *>(hcounts) + i, res[i]->small, sizeof(SmallBlock),
-                        cudaMemcpyDeviceToHost, h->side);
+    cudaMemcpyAsync(hcounts, L->smalls, sizeof(SmallBlock) * size_t(nf), cudaMemcpyDeviceToHost, h->side);
     e = cudaStreamSynchronize(h->side);
     cudaEventDestroy(k1);
     if (e != cudaSuccess) {
@@ -854,9 +861,18 @@ eg_status collect(eg_ctx *h, Result &r)
     cudaError_t e = cudaEventSynchronize(r.done);
     if (e != cudaSuccess) return from_cuda(e);
     if (!r.have_A) {
-        SmallBlock sb;
-        e = cudaMemcpy(&sb, r.small, sizeof(SmallBlock), cudaMemcpyDeviceToHost);
-        if (e != cudaSuccess) return from_cuda(e);
+        // every result of the launch has finished with this one: read all
+        // their SmallBlocks at once, the first time any of them is collected
+        Launch &L = *r.launch;
+        if (L.hsmall.empty()) {
+            L.hsmall.resize(size_t(L.nsmall));
+            e = cudaMemcpy(L.hsmall.data(), L.smalls, sizeof(SmallBlock) * size_t(L.nsmall), cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) {
+                L.hsmall.clear();
+                return from_cuda(e);
+            }
+        }
+        const SmallBlock &sb = L.hsmall[size_t(r.slot)];
         r.A = sb.totals[3];
         r.err |= sb.err;
         r.have_A = true;
