@@ -159,7 +159,7 @@ struct Result {
     uint64_t M = 0, S = 0, P = 0, A = 0, V = 0;
     bool have_A = false;
     uint32_t err = 0;
-    cudaEvent_t done = nullptr;
+    cudaEvent_t done = nullptr;  // the launch's completion event (owned by the launch)
     std::shared_ptr<struct Launch> launch;  // keeps the descriptor table alive
 };
 
@@ -172,11 +172,13 @@ struct Launch {
     void *smalls = nullptr;           // SmallBlock[nsmall] on the device
     int nsmall = 0;
     std::vector<SmallBlock> hsmall;   // host copy once the launch finished
+    cudaEvent_t done = nullptr;       // recorded after the launch's last step
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // step timing (optional)
     ~Launch()
     {
         for (auto &e : ev)
             if (e) cudaEventDestroy(e);
+        if (done) cudaEventDestroy(done);
     }
 };
 
@@ -619,7 +621,6 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
         for (auto &r : res)
             if (r) {
                 free_result_buffers(h, r.get());
-                if (r->done) cudaEventDestroy(r->done);
             }
         release_launch(h, L.get());
         return s;
@@ -843,11 +844,9 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
     if (h->timing) cudaEventRecord(L->ev[4], st);
     cudaEventRecord(h->ws_free, st);
     ids.resize(nf);
-    for (int i = 0; i < nf; i++) {
-        Result &r = *res[i];
-        if ((e = cudaEventCreateWithFlags(&r.done, cudaEventDisableTiming)) != cudaSuccess) return fail(from_cuda(e));
-        cudaEventRecord(r.done, st);
-    }
+    if ((e = cudaEventCreateWithFlags(&L->done, cudaEventDisableTiming)) != cudaSuccess) return fail(from_cuda(e));
+    cudaEventRecord(L->done, st);
+    for (int i = 0; i < nf; i++) res[i]->done = L->done;
     for (int i = 0; i < nf; i++) {
         uint64_t id = h->next_id++;
         ids[i] = id;
@@ -1118,7 +1117,6 @@ eg_status timed_trial(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, 
         for (uint64_t id : ids) {
             Result &R = *h->results[id];
             eg_status cs = collect(h, R);
-            if (R.done) cudaEventDestroy(R.done);
             free_result_buffers(h, &R);
             if (R.launch && R.launch.use_count() == 1) release_launch(h, R.launch.get());
             h->results.erase(id);
@@ -1318,10 +1316,7 @@ eg_status eg_release(eg_handle h, eg_result_id id)
     auto it = h->results.find(id);
     if (it == h->results.end()) return EG_ERR_ARG;
     Result &r = *it->second;
-    if (r.done) {
-        cudaEventSynchronize(r.done);
-        cudaEventDestroy(r.done);
-    }
+    if (r.done) cudaEventSynchronize(r.done);
     free_result_buffers(h, &r);
     if (r.launch && r.launch.use_count() == 1) release_launch(h, r.launch.get());
     h->results.erase(it);
