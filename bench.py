@@ -272,10 +272,14 @@ def run_batch(args, ws, rank, local):
     tuned = h.autotune(ts, stream)
     hp = eg.Handle(local)
 
+    h.set_timing(True)
+    bsteps = []
+
     def batched():
         ids = h.batch_submit(ts, stream)
         for rid in ids:
             h.get_graph_device(rid)
+        bsteps.append(h.step_times(ids[0]))  # the batch's step times
         for rid in ids:
             h.release(rid)
 
@@ -314,6 +318,8 @@ def run_batch(args, ws, rank, local):
                            "parallelism": f"fields sharded over {ws} ranks"},
                 "plain": out["plain"], "speedup_vs_plain": out["batched"]["value"] / out["plain"]["value"],
                 "autotuned": tuned,
+                "step_ms": {nm: statistics.mean(x[i] for x in bsteps[-args.steps:])
+                            for i, nm in enumerate(["classify", "resolve", "emit"])},
                 "gpu_launches": out["batched"]["gpu_launches"]}
         print(json.dumps(line), flush=True)
     h.close()
