@@ -29,6 +29,12 @@ _lib = None
 
 EO_OK, EO_ERR_ARG, EO_ERR_NAN, EO_ERR_OOM = 0, 1, 2, 3
 
+# element types of the C oracle (Sec. 5: 8- to 64-bit integers, 32/64-bit floats)
+DTYPES = {np.dtype(np.float32): 0, np.dtype(np.float64): 1, np.dtype(np.int8): 2,
+          np.dtype(np.uint8): 3, np.dtype(np.int16): 4, np.dtype(np.uint16): 5,
+          np.dtype(np.int32): 6, np.dtype(np.uint32): 7, np.dtype(np.int64): 8,
+          np.dtype(np.uint64): 9}
+
 
 class OracleError(RuntimeError):
     pass
@@ -59,6 +65,9 @@ def _load():
         lib.eo_compute.argtypes = [P, ctypes.c_int, P, ctypes.c_int, ctypes.c_int,
                                    ctypes.POINTER(ctypes.c_void_p)]
         lib.eo_compute.restype = ctypes.c_int
+        lib.eo_compute_typed.argtypes = [P, ctypes.c_int, ctypes.c_int, P, ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_void_p)]
+        lib.eo_compute_typed.restype = ctypes.c_int
         lib.eo_counts.argtypes = [P, P]
         lib.eo_counts.restype = None
         lib.eo_copy.argtypes = [P] * 12
@@ -84,10 +93,10 @@ class OracleGraph:
     label: np.ndarray    # uint32[N]   maximum reached
     beta0p: np.ndarray   # uint8[N]    upper-link components
     maxima: np.ndarray   # uint32[M]   ascending
-    max_val: np.ndarray  # float32[M]
+    max_val: np.ndarray  # [M] values at the maxima, in the field's element type
     saddles: np.ndarray  # uint32[S]   ascending
     sad_b0: np.ndarray   # uint8[S]
-    sad_val: np.ndarray  # float32[S]
+    sad_val: np.ndarray  # [S] values at the saddles, in the field's element type
     row_ptr: np.ndarray  # uint64[S+1]
     col: np.ndarray      # uint32[A]
     n_paths: int         # sum of beta0+ over saddles
@@ -114,23 +123,28 @@ class OracleGraph:
 
 
 def compute(field: np.ndarray, extents=None, naive: bool = False,
-            minimum: bool = False, paths: bool = False) -> OracleGraph:
-    """Extremum graph of ``field`` (float32).
+            minimum: bool = False, paths: bool = False, dtype=None) -> OracleGraph:
+    """Extremum graph of ``field``.
 
     ``extents`` lists the grid size per axis with axis 0 fastest; by default it
     is the numpy shape reversed, so a C-ordered array ``a[z, y, x]`` has
     ``x`` as axis 0.  ``minimum`` selects the minimum graph (reversed order).
     ``paths`` adds the arc geometry (Algorithm 2's gradient paths).
+    ``dtype``: the element type the values are compared in (one of DTYPES);
+    None means float32 (the field is converted to it).
     """
     lib = _load()
-    f = np.ascontiguousarray(field, dtype=np.float32).reshape(-1)
+    dt = np.dtype(np.float32 if dtype is None else dtype)
+    if dt not in DTYPES:
+        raise OracleError(f"unsupported element type {dt}")
+    f = np.ascontiguousarray(field, dtype=dt).reshape(-1)
     if extents is None:
         extents = tuple(reversed(np.asarray(field).shape))
     ext = np.ascontiguousarray(extents, dtype=np.int64)
     d = int(ext.size)
     h = ctypes.c_void_p()
-    st = lib.eo_compute(f.ctypes.data, d, ext.ctypes.data, int(naive), int(minimum),
-                        ctypes.byref(h))
+    st = lib.eo_compute_typed(f.ctypes.data, DTYPES[dt], d, ext.ctypes.data, int(naive),
+                              int(minimum), ctypes.byref(h))
     if st != EO_OK:
         raise OracleError({EO_ERR_ARG: "bad argument", EO_ERR_NAN: "NaN in field",
                            EO_ERR_OOM: "out of memory"}.get(st, str(st)))
@@ -141,8 +155,8 @@ def compute(field: np.ndarray, extents=None, naive: bool = False,
         g = OracleGraph(
             asc=np.empty(n, np.uint32), label=np.empty(n, np.uint32),
             beta0p=np.empty(n, np.uint8), maxima=np.empty(nm, np.uint32),
-            max_val=np.empty(nm, np.float32), saddles=np.empty(ns, np.uint32),
-            sad_b0=np.empty(ns, np.uint8), sad_val=np.empty(ns, np.float32),
+            max_val=np.empty(nm, dt), saddles=np.empty(ns, np.uint32),
+            sad_b0=np.empty(ns, np.uint8), sad_val=np.empty(ns, dt),
             row_ptr=np.empty(ns + 1, np.uint64), col=np.empty(na, np.uint32),
             n_paths=npaths, reps=np.empty(npaths, np.uint32))
         lib.eo_copy(h, g.asc.ctypes.data, g.label.ctypes.data, g.beta0p.ctypes.data,
@@ -166,8 +180,10 @@ def bundle(g: OracleGraph, minimum: bool = False) -> np.ndarray:
     at least one pair of its arc ends; a saddle whose arcs all end at one
     maximum connects no pair and is kept.  Returns uint8[S], 1 = kept.
     Plain loops: for small fields only."""
+    vals = g.sad_val.tolist()  # Python int / float: exact for every element type
+
     def higher(i):
-        v, s = float(g.sad_val[i]), int(g.saddles[i])
+        v, s = vals[i], int(g.saddles[i])
         return (-v, -s) if minimum else (v, s)
 
     best = {}

@@ -44,6 +44,11 @@
  * The minimum graph (Sec. 2, Sec. 5) is the same computation with the order
  * reversed: "higher" becomes "lower" under the same perturbation.
  *
+ * Element types (Sec. 5: 8- to 64-bit signed and unsigned integers, 32- and
+ * 64-bit floats): two values are compared in their own type, with C's
+ * comparison operators on that type; nothing is converted.  The value copies
+ * of maxima and saddles are the input's bytes.
+ *
  * Vertex index: v = x0 + n0*(x1 + n1*(x2 + ...)), axis 0 fastest.
  */
 #include <stdint.h>
@@ -56,6 +61,21 @@
 
 enum { EO_OK = 0, EO_ERR_ARG = 1, EO_ERR_NAN = 2, EO_ERR_OOM = 3 };
 
+/* element types of a field */
+enum { EO_F32 = 0, EO_F64 = 1, EO_I8 = 2, EO_U8 = 3, EO_I16 = 4, EO_U16 = 5,
+       EO_I32 = 6, EO_U32 = 7, EO_I64 = 8, EO_U64 = 9, EO_NTYPES = 10 };
+
+static size_t eo_dtype_size(int t)
+{
+    switch (t) {
+    case EO_I8: case EO_U8: return 1;
+    case EO_I16: case EO_U16: return 2;
+    case EO_F32: case EO_I32: case EO_U32: return 4;
+    case EO_F64: case EO_I64: case EO_U64: return 8;
+    default: return 0;
+    }
+}
+
 typedef struct eo_result {
     int64_t n;
     int64_t n_max, n_sad, n_paths, n_arcs;
@@ -63,10 +83,11 @@ typedef struct eo_result {
     uint32_t *label;   /* [n] maximum reached */
     uint8_t *beta0p;   /* [n] number of upper-link components */
     uint32_t *maxima;  /* [n_max] ascending */
-    float *max_val;    /* [n_max] */
+    int dtype;         /* element type of the field and of the value copies */
+    void *max_val;     /* [n_max] value copies, in the field's type */
     uint32_t *saddles; /* [n_sad] ascending */
     uint8_t *sad_b0;   /* [n_sad] */
-    float *sad_val;    /* [n_sad] */
+    void *sad_val;     /* [n_sad] value copies, in the field's type */
     uint64_t *row_ptr; /* [n_sad+1] */
     uint32_t *col;     /* [n_arcs] */
     uint32_t *reps;    /* [n_paths] UpperLinkRep of every saddle, saddles in order,
@@ -75,14 +96,44 @@ typedef struct eo_result {
 
 /* ---- order (simulated perturbation, Sec. 3.3) ----------------------------- */
 
+/* The field: its values and their element type. */
+typedef struct eo_field {
+    const void *f;
+    int t;
+} eo_field;
+
+#define EO_CMP(T) { T x = ((const T *)F->f)[a], y = ((const T *)F->f)[b]; return (x > y) - (x < y); }
+
+/* Sign of f[a] - f[b], comparing the two values in their own type. */
+static int eo_cmp_values(const eo_field *F, uint32_t a, uint32_t b)
+{
+    switch (F->t) {
+    case EO_F32: EO_CMP(float)
+    case EO_F64: EO_CMP(double)
+    case EO_I8: EO_CMP(int8_t)
+    case EO_U8: EO_CMP(uint8_t)
+    case EO_I16: EO_CMP(int16_t)
+    case EO_U16: EO_CMP(uint16_t)
+    case EO_I32: EO_CMP(int32_t)
+    case EO_U32: EO_CMP(uint32_t)
+    case EO_I64: EO_CMP(int64_t)
+    default: EO_CMP(uint64_t)
+    }
+}
+
+static int eo_isnan(const eo_field *F, uint64_t v)
+{
+    if (F->t == EO_F32) return isnan(((const float *)F->f)[v]);
+    if (F->t == EO_F64) return isnan(((const double *)F->f)[v]);
+    return 0;
+}
+
 /* 1 iff w is higher than v.  With reverse set, "higher" means lower: the
  * minimum graph is the maximum graph of the reversed order. */
-static int eo_higher(const float *f, uint32_t v, uint32_t w, int reverse)
+static int eo_higher(const eo_field *F, uint32_t v, uint32_t w, int reverse)
 {
-    int up;
-    if (f[w] > f[v]) up = 1;
-    else if (f[w] < f[v]) up = 0;
-    else up = (w > v);
+    int c = eo_cmp_values(F, w, v);
+    int up = c > 0 ? 1 : (c < 0 ? 0 : (w > v));
     return reverse ? !up : up;
 }
 
@@ -157,7 +208,7 @@ static void eo_union(int *parent, int a, int b)
  * components and the highest vertex of each.  Returns beta0+; writes the
  * representatives (one per component, in no particular order) to reps and the
  * gradient (highest upper-link vertex, or v) to *grad. */
-static int eo_classify_vertex(const float *f, int d, const int64_t *ext,
+static int eo_classify_vertex(const eo_field *f, int d, const int64_t *ext,
                               int nnb, int64_t off[][EO_MAXD], uint32_t v,
                               int reverse, uint32_t *reps, uint32_t *grad)
 {
@@ -230,11 +281,14 @@ void eo_free(eo_result *r)
 /* naive != 0: follow the gradient from every vertex to its maximum with no
  * reuse (Algorithm 2's loop, started everywhere).  naive == 0: the same walk,
  * back-filling the labels of every vertex on a walk once its end is known. */
-int eo_compute(const float *f, int d, const int64_t *ext, int naive, int reverse,
-               eo_result **out)
+int eo_compute_typed(const void *values, int dtype, int d, const int64_t *ext, int naive,
+                     int reverse, eo_result **out)
 {
     *out = NULL;
-    if (!f || !ext || d < 1 || d > EO_MAXD) return EO_ERR_ARG;
+    const size_t es = eo_dtype_size(dtype);
+    if (!values || !ext || d < 1 || d > EO_MAXD || es == 0) return EO_ERR_ARG;
+    const eo_field field = {values, dtype};
+    const eo_field *f = &field;
     uint64_t n = 1;
     for (int i = 0; i < d; i++) {
         if (ext[i] < 1) return EO_ERR_ARG;
@@ -242,7 +296,7 @@ int eo_compute(const float *f, int d, const int64_t *ext, int naive, int reverse
         if (n > 0xFFFFFFFFull) return EO_ERR_ARG;
     }
     for (uint64_t v = 0; v < n; v++)
-        if (isnan(f[v])) return EO_ERR_NAN;
+        if (eo_isnan(f, v)) return EO_ERR_NAN;
 
     int64_t off[EO_MAXNB][EO_MAXD];
     int nnb = eo_offsets(d, off);
@@ -250,6 +304,7 @@ int eo_compute(const float *f, int d, const int64_t *ext, int naive, int reverse
     eo_result *r = (eo_result *)calloc(1, sizeof(eo_result));
     if (!r) return EO_ERR_OOM;
     r->n = (int64_t)n;
+    r->dtype = dtype;
     r->asc = (uint32_t *)malloc(n * sizeof(uint32_t));
     r->label = (uint32_t *)malloc(n * sizeof(uint32_t));
     r->beta0p = (uint8_t *)malloc(n);
@@ -298,10 +353,10 @@ int eo_compute(const float *f, int d, const int64_t *ext, int naive, int reverse
     r->n_sad = n_sad;
     r->n_paths = n_paths;
     r->maxima = (uint32_t *)malloc((n_max ? n_max : 1) * sizeof(uint32_t));
-    r->max_val = (float *)malloc((n_max ? n_max : 1) * sizeof(float));
+    r->max_val = malloc((n_max ? n_max : 1) * es);
     r->saddles = (uint32_t *)malloc((n_sad ? n_sad : 1) * sizeof(uint32_t));
     r->sad_b0 = (uint8_t *)malloc(n_sad ? n_sad : 1);
-    r->sad_val = (float *)malloc((n_sad ? n_sad : 1) * sizeof(float));
+    r->sad_val = malloc((n_sad ? n_sad : 1) * es);
     r->row_ptr = (uint64_t *)malloc((n_sad + 1) * sizeof(uint64_t));
     r->col = (uint32_t *)malloc((n_paths ? n_paths : 1) * sizeof(uint32_t));
     r->reps = (uint32_t *)malloc((n_paths ? n_paths : 1) * sizeof(uint32_t));
@@ -313,7 +368,7 @@ int eo_compute(const float *f, int d, const int64_t *ext, int naive, int reverse
     for (uint64_t v = 0; v < n; v++) {
         if (r->beta0p[v] == 0) {
             r->maxima[im] = (uint32_t)v;
-            r->max_val[im] = f[v];
+            memcpy((char *)r->max_val + im * es, (const char *)values + v * es, es);
             im++;
         } else if (r->beta0p[v] >= 2) {
             uint32_t g;
@@ -327,7 +382,7 @@ int eo_compute(const float *f, int d, const int64_t *ext, int naive, int reverse
                 if (c == 0 || ends[c] != ends[c - 1]) r->col[ia++] = ends[c];
             r->saddles[is] = (uint32_t)v;
             r->sad_b0[is] = (uint8_t)b;
-            r->sad_val[is] = f[v];
+            memcpy((char *)r->sad_val + is * es, (const char *)values + v * es, es);
             is++;
             r->row_ptr[is] = (uint64_t)ia;
         }
@@ -337,6 +392,13 @@ int eo_compute(const float *f, int d, const int64_t *ext, int naive, int reverse
     return EO_OK;
 }
 
+/* float32 field (the library's default element type). */
+int eo_compute(const float *f, int d, const int64_t *ext, int naive, int reverse,
+               eo_result **out)
+{
+    return eo_compute_typed(f, EO_F32, d, ext, naive, reverse, out);
+}
+
 /* Flat accessors for foreign-function callers. */
 void eo_counts(const eo_result *r, int64_t *c5)
 {
@@ -344,18 +406,18 @@ void eo_counts(const eo_result *r, int64_t *c5)
 }
 
 void eo_copy(const eo_result *r, uint32_t *asc, uint32_t *label, uint8_t *beta0p,
-             uint32_t *maxima, float *max_val, uint32_t *saddles, uint8_t *sad_b0,
-             float *sad_val, uint64_t *row_ptr, uint32_t *col, uint32_t *reps)
+             uint32_t *maxima, void *max_val, uint32_t *saddles, uint8_t *sad_b0,
+             void *sad_val, uint64_t *row_ptr, uint32_t *col, uint32_t *reps)
 {
-    size_t n = (size_t)r->n;
+    size_t n = (size_t)r->n, es = eo_dtype_size(r->dtype);
     if (asc) memcpy(asc, r->asc, n * sizeof(uint32_t));
     if (label) memcpy(label, r->label, n * sizeof(uint32_t));
     if (beta0p) memcpy(beta0p, r->beta0p, n);
     if (maxima) memcpy(maxima, r->maxima, (size_t)r->n_max * sizeof(uint32_t));
-    if (max_val) memcpy(max_val, r->max_val, (size_t)r->n_max * sizeof(float));
+    if (max_val) memcpy(max_val, r->max_val, (size_t)r->n_max * es);
     if (saddles) memcpy(saddles, r->saddles, (size_t)r->n_sad * sizeof(uint32_t));
     if (sad_b0) memcpy(sad_b0, r->sad_b0, (size_t)r->n_sad);
-    if (sad_val) memcpy(sad_val, r->sad_val, (size_t)r->n_sad * sizeof(float));
+    if (sad_val) memcpy(sad_val, r->sad_val, (size_t)r->n_sad * es);
     if (row_ptr) memcpy(row_ptr, r->row_ptr, (size_t)(r->n_sad + 1) * sizeof(uint64_t));
     if (col) memcpy(col, r->col, (size_t)r->n_arcs * sizeof(uint32_t));
     if (reps) memcpy(reps, r->reps, (size_t)r->n_paths * sizeof(uint32_t));

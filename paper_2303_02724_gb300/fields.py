@@ -5,7 +5,8 @@ samples (Sec. 6, Table 2, Table 3), which are not available here.  Both the
 CUDA path and the CPU oracle are fed from this module; it imports nothing from
 either of them.
 
-All arrays are float32, C-ordered with the LAST numpy axis fastest, which is
+All arrays are float32 (except those of ``typed_ties`` and ``quantise``, which
+hold the requested element type), C-ordered with the LAST numpy axis fastest, which is
 axis 0 of the grid (vertex index v = x0 + n0*(x1 + n1*(x2 + ...))).  So a 3D
 field has numpy shape (n2, n1, n0) and ``extents`` = (n0, n1, n2).
 
@@ -258,3 +259,58 @@ def schwefel(extents, seed=5, lo=-500.0, hi=500.0):
         sh[d - 1 - k] = extents[k]
         acc = acc + axes[k].reshape(sh)
     return Field(np.ascontiguousarray(acc, dtype=np.float32), extents, f"schwefel{d}d")
+
+
+# Element types a field may have (Sec. 5 lists 8- to 64-bit integers and
+# floats).  Per type, values on both sides of every boundary a wrong
+# comparison would trip over: the extremes, both sides of the sign bit, and
+# neighbours that float32 (or float64) cannot tell apart.
+ELEMENT_TYPES = ("float32", "float64", "int8", "uint8", "int16", "uint16", "int32", "uint32",
+                 "int64", "uint64")
+EDGE_VALUES = {
+    "float32": [-math.inf, -3.0e38, -1.0, -0.0, 0.0, 1.0e-45, 1.0, 1.0 + 2.0 ** -23, 3.0e38, math.inf],
+    "float64": [-math.inf, -1.0e300, -1.0, -0.0, 0.0, 5.0e-324, 1.0, 1.0 + 2.0 ** -52, 1.0 + 2.0 ** -30,
+                1.0e300, math.inf],
+    "int8": [-128, -127, -1, 0, 1, 126, 127],
+    "uint8": [0, 1, 127, 128, 129, 254, 255],
+    "int16": [-32768, -32767, -1, 0, 1, 32766, 32767],
+    "uint16": [0, 1, 32767, 32768, 65534, 65535],
+    "int32": [-2 ** 31, -2 ** 31 + 1, -1, 0, 1, 2 ** 24, 2 ** 24 + 1, 2 ** 31 - 1],
+    "uint32": [0, 1, 2 ** 24, 2 ** 24 + 1, 2 ** 31 - 1, 2 ** 31, 2 ** 32 - 2, 2 ** 32 - 1],
+    "int64": [-2 ** 63, -2 ** 63 + 1, -1, 0, 1, 2 ** 53, 2 ** 53 + 1, 2 ** 63 - 1],
+    "uint64": [0, 1, 2 ** 53, 2 ** 53 + 1, 2 ** 63 - 1, 2 ** 63, 2 ** 64 - 2, 2 ** 64 - 1],
+}
+
+
+def typed_ties(extents, seed, dtype):
+    """Field of element type ``dtype`` drawn uniformly from that type's
+    EDGE_VALUES: heavy ties plus values that only an exact comparison in the
+    type itself orders correctly."""
+    dt = np.dtype(dtype)
+    rng = np.random.default_rng(seed)
+    shape = tuple(reversed(tuple(extents)))
+    table = np.array(EDGE_VALUES[dt.name], dtype=dt)
+    v = table[rng.integers(0, table.size, size=shape)]
+    return Field(np.ascontiguousarray(v), tuple(extents), f"edges_{dt.name}")
+
+
+def quantise(field: Field, dtype, levels=None) -> Field:
+    """The same field in element type ``dtype``: integers get the values
+    rescaled affinely onto [lo, lo + levels - 1] (default: the type's whole
+    range, capped at 2^52 levels so that the float64 arithmetic stays exact)
+    and rounded, so narrow types form plateaus; float64 gets the float32
+    values widened (every float32 is a float64)."""
+    dt = np.dtype(dtype)
+    v = np.asarray(field.values, np.float64)
+    if dt.kind == "f":
+        out = v.astype(dt)
+    else:
+        info = np.iinfo(dt)
+        n = min(int(info.max) - int(info.min) + 1, 2 ** 52) if levels is None else int(levels)
+        lo, hi = float(v.min()), float(v.max())
+        q = np.rint((v - lo) / (hi - lo if hi > lo else 1.0) * (n - 1))
+        if info.min < 0:
+            out = (q.astype(np.int64) + (-(n // 2))).astype(dt)  # centred on zero
+        else:
+            out = q.astype(np.uint64).astype(dt)
+    return Field(np.ascontiguousarray(out), field.extents, f"{field.name}_{dt.name}", dict(field.meta))

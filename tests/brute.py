@@ -44,8 +44,9 @@ def sos_rank(values, minimum=False):
     return rank
 
 
-def brute_graph(field, extents, minimum=False):
-    vals = np.asarray(field, dtype=np.float32).reshape(-1).astype(np.float64)
+def brute_graph(field, extents, minimum=False, dtype=np.float32):
+    # values stay in their own element type: numpy's sort compares them exactly
+    vals = np.asarray(field, dtype=dtype).reshape(-1)
     n = vals.size
     X = coords(extents)
     assert len(X) == n

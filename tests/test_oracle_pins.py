@@ -344,3 +344,97 @@ def test_bundling_keeps_single_pair_saddle_structure():
     f = np.array([0, 5, 1, 4, 2, 8, 3], np.float32)
     g = oracle.compute(f)
     assert oracle.bundle(g).tolist() == [1, 1]
+
+
+# ---------------------------------------------------------- element types ---
+# Sec. 5: the library takes 8- to 64-bit integers and 32/64-bit floats.  The
+# order is still (value, then index); values are compared in their own type.
+
+TYPED_SHAPES = [(8, 8), (4, 4, 4), (3, 3, 3, 3), (9,), (5, 3, 2)]
+
+
+@pytest.mark.parametrize("dtype", F.ELEMENT_TYPES)
+@pytest.mark.parametrize("shape", TYPED_SHAPES, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("minimum", [False, True])
+def test_typed_brute_force(dtype, shape, minimum):
+    """Boundary values of each type (extremes, both sides of the sign bit,
+    neighbours float32 cannot separate) against the brute force, whose
+    sort-based order compares the values in their own type."""
+    seed = zlib.crc32(repr((shape, dtype)).encode()) % 1000
+    f = F.typed_ties(shape, seed, dtype).values
+    g = oracle.compute(f, extents=shape, minimum=minimum, dtype=f.dtype)
+    b = brute_graph(f, shape, minimum=minimum, dtype=f.dtype)
+    assert g.asc.tolist() == b["asc"].tolist()
+    assert g.label.tolist() == b["label"].tolist()
+    assert g.beta0p.tolist() == b["beta"].tolist()
+    assert g.maxima.tolist() == b["maxima"]
+    assert g.saddles.tolist() == b["saddles"]
+    assert g.arcs() == b["arcs"]
+    for i, s_ in enumerate(b["saddles"]):
+        assert g.saddle_reps(i).tolist() == sorted(int(x) for x in b["reps"][s_])
+    flat = f.reshape(-1)
+    assert g.max_val.dtype == f.dtype and g.sad_val.dtype == f.dtype
+    assert g.max_val.tobytes() == flat[g.maxima].tobytes()
+    assert g.sad_val.tobytes() == flat[g.saddles].tobytes()
+
+
+@pytest.mark.parametrize("dtype", ["uint64", "int64", "uint32", "int32", "float64"])
+def test_typed_differs_from_float32(dtype):
+    """Values that float32 merges (2^24 and 2^24+1, 2^53 and 2^53+1, 1 and
+    1+2^-30) must stay ordered: a 1D field whose float32 image is constant
+    still has its maximum at the largest value, not at the last index."""
+    hi = {"uint64": 2 ** 53 + 1, "int64": 2 ** 53 + 1, "uint32": 2 ** 24 + 1,
+          "int32": 2 ** 24 + 1, "float64": 1.0 + 2.0 ** -30}[dtype]
+    lo = {"float64": 1.0}.get(dtype, hi - 1)
+    f = np.array([lo, hi, lo], dtype=dtype)
+    assert np.unique(f.astype(np.float32)).size == 1
+    g = oracle.compute(f, dtype=f.dtype)
+    assert g.maxima.tolist() == [1]
+    assert g.label.tolist() == [1] * 3
+    g32 = oracle.compute(f.astype(np.float32))
+    assert g32.maxima.tolist() == [2]
+
+
+@pytest.mark.parametrize("dtype", ["int8", "uint8", "int16", "uint16"])
+def test_typed_narrow_equals_float32(dtype):
+    """Integers of at most 16 bits are exact in float32 with their order and
+    ties kept, so the graph of the typed field equals that of its float32
+    image (the float32 path is pinned independently above)."""
+    for shape, seed in [((12, 10), 1), ((6, 5, 4), 2), ((4, 3, 3, 3), 3)]:
+        f = F.quantise(F.white_noise(shape, seed), dtype, levels=6).values
+        g = oracle.compute(f, extents=shape, dtype=f.dtype)
+        g32 = oracle.compute(f.astype(np.float32), extents=shape)
+        assert np.array_equal(g.label, g32.label)
+        assert np.array_equal(g.maxima, g32.maxima) and np.array_equal(g.saddles, g32.saddles)
+        assert np.array_equal(g.row_ptr, g32.row_ptr) and np.array_equal(g.col, g32.col)
+        assert np.array_equal(g.max_val.astype(np.float32), g32.max_val)
+
+
+def test_typed_nan_and_bad_type():
+    with pytest.raises(oracle.OracleError):
+        oracle.compute(np.array([0.0, np.nan], np.float64), dtype=np.float64)
+    with pytest.raises(oracle.OracleError):
+        oracle.compute(np.zeros(4, np.float16), dtype=np.float16)
+    g = oracle.compute(np.array([-np.inf, 0.0, -0.0, np.inf, 1.0]), dtype=np.float64)
+    assert g.maxima.tolist() == [3]
+
+
+def test_typed_bundling_uses_exact_values():
+    """Arc bundling ranks saddles by their values in the field's own type."""
+    for dtype in ["uint64", "int64", "float64", "int8"]:
+        for seed in range(3):
+            shape = (7, 6, 5)
+            f = F.typed_ties(shape, seed, dtype).values
+            g = oracle.compute(f, extents=shape, dtype=f.dtype)
+            keep = oracle.bundle(g)
+            b = brute_graph(f, shape, dtype=f.dtype)
+            rank = sos_rank(f.reshape(-1))
+            pairs = {}
+            for s in b["saddles"]:
+                e = sorted({m for (t, m) in b["arcs"] if t == s})
+                for x in range(len(e)):
+                    for y in range(x + 1, len(e)):
+                        pairs.setdefault((e[x], e[y]), []).append(s)
+            kept = {int(s) for s, k in zip(g.saddles.tolist(), keep.tolist()) if k}
+            for ss in pairs.values():
+                assert max(ss, key=lambda s: rank[s]) in kept
