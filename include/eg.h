@@ -2,7 +2,8 @@
  * eg.h -- C ABI of the GB300 extremum-graph library.
  *
  * The library computes the extremum graph (maximum graph by default) of a
- * float32 scalar field sampled on a d-dimensional regular grid, 1 <= d <= 4,
+ * scalar field (float32 by default; 8- to 64-bit integers and float64 through
+ * eg_compute_typed, Sec. 5) sampled on a d-dimensional regular grid, 1 <= d <= 4,
  * under the Freudenthal triangulation of the grid (Sec. 3.2, Algorithm 1), as
  * defined in Sec. 2 of Ande, Subhash & Natarajan, "Tachyon: efficient shared
  * memory parallel computation of extremum graphs":
@@ -17,8 +18,9 @@
  *           descending manifold of that maximum, i.e. the Morse decomposition).
  *
  * Ties are broken by simulation of simplicity (Sec. 3.3): vertex w is higher
- * than v iff f[w] > f[v], or f[w] == f[v] and w > v (linear index).  -0.0
- * equals +0.0; infinities are ordinary values; NaN is rejected.
+ * than v iff f[w] > f[v], or f[w] == f[v] and w > v (linear index).  Values are
+ * compared exactly in the field's own element type.  -0.0 equals +0.0;
+ * infinities are ordinary values; NaN is rejected.
  *
  * Grid layout: axis 0 is fastest; vertex index v = x0 + n0*(x1 + n1*(x2 + ..)).
  * Every vertex id in and out of the library is this linear index (uint32), so a
@@ -66,6 +68,27 @@ typedef enum eg_status {
     EG_ERR_INTERNAL = 8        /* a device-side consistency check failed          */
 } eg_status;
 
+/* Element types of a field (Sec. 5: 8-, 16-, 32- and 64-bit signed and
+ * unsigned integers, 32- and 64-bit floats). */
+typedef enum eg_dtype {
+    EG_DTYPE_F32 = 0,
+    EG_DTYPE_F64 = 1,
+    EG_DTYPE_I8 = 2,
+    EG_DTYPE_U8 = 3,
+    EG_DTYPE_I16 = 4,
+    EG_DTYPE_U16 = 5,
+    EG_DTYPE_I32 = 6,
+    EG_DTYPE_U32 = 7,
+    EG_DTYPE_I64 = 8,
+    EG_DTYPE_U64 = 9
+} eg_dtype;
+#define EG_DTYPE_COUNT 10
+
+/* eg_field_desc.flags bits 16..19: the field's element type (an eg_dtype;
+ * 0 = float32), e.g. flags = EG_FLAG_DTYPE(EG_DTYPE_U8). */
+#define EG_FLAG_DTYPE(t) ((uint32_t)(t) << 16)
+#define EG_FLAG_DTYPE_MASK 0xf0000u
+
 /* eg_config.flags */
 #define EG_FLAG_MINIMUM_GRAPH 0x1u  /* minimum graph: the same order reversed (Sec. 2) */
 #define EG_FLAG_NO_LABELS     0x2u  /* do not keep per-vertex labels in the result    */
@@ -90,10 +113,11 @@ typedef struct eg_config {
 typedef struct eg_ctx *eg_handle;
 typedef uint64_t eg_result_id;
 
-/* One field of a batch.  field: device float32, caller-owned, valid until the
- * batch's results are read; extents[k] >= 1 for k < d. */
+/* One field of a batch.  field: device array of the element type named in
+ * flags (float32 unless EG_FLAG_DTYPE says otherwise), caller-owned, valid
+ * until the batch's results are read; extents[k] >= 1 for k < d. */
 typedef struct eg_field_desc {
-    const float *field;
+    const void *field;
     int32_t d;
     int32_t flags;           /* per-field EG_FLAG_* (ORed with the handle's)        */
     int64_t extents[EG_MAX_DIM];
@@ -104,6 +128,7 @@ typedef struct eg_field_desc {
  * at least the counted size).  Call once with NULL arrays to learn the sizes. */
 typedef struct eg_graph {
     int32_t d;
+    int32_t dtype;           /* element type of the field and of max_val, sad_val */
     int64_t extents[EG_MAX_DIM];
     int64_t n_vertices;
     int64_t n_maxima;        /* M                                                   */
@@ -111,10 +136,11 @@ typedef struct eg_graph {
     int64_t n_paths;         /* P = sum of beta0+ over saddles (gradient paths)     */
     int64_t n_arcs;          /* A = number of unique (saddle, maximum) pairs        */
     uint32_t *maxima;        /* [M]   ascending vertex ids                          */
-    float *max_val;          /* [M]   f at each maximum (exact copy)                */
+    void *max_val;           /* [M]   f at each maximum (exact copy, element type
+                                      dtype: eg_dtype_size(dtype) bytes each)        */
     uint32_t *saddles;       /* [S]   ascending vertex ids                          */
     uint8_t *sad_beta0;      /* [S]   upper-link components of each saddle          */
-    float *sad_val;          /* [S]   f at each saddle (exact copy)                 */
+    void *sad_val;           /* [S]   f at each saddle (exact copy, element type dtype) */
     uint64_t *row_ptr;       /* [S+1] CSR row offsets into col                      */
     uint32_t *col;           /* [A]   maxima of each saddle, ascending, unique      */
     uint32_t *labels;        /* [N]   maximum reached from every vertex             */
@@ -137,6 +163,22 @@ EG_API eg_status eg_destroy(eg_handle h);
  * Errors: EG_ERR_ARG, EG_ERR_NAN (field holds NaN), EG_ERR_OOM, EG_ERR_CUDA. */
 EG_API eg_status eg_compute(eg_handle h, const float *field, int d, const int64_t *extents,
                             void *stream, eg_result_id *out);
+
+/* As eg_compute, for a field of element type `dtype` (an eg_dtype): device
+ * array of N elements of eg_dtype_size(dtype) bytes, naturally aligned.
+ * Values are compared exactly in that type (Sec. 3.3's order; Sec. 5's list
+ * of types); the value copies of the result (eg_graph.max_val, sad_val) have
+ * that type too.  Integers of at most 16 bits are exact in float32 with their
+ * order and ties kept: they are widened to float32 on the device and take the
+ * float32 kernels.  32- and 64-bit integers and float64 take a classifier
+ * that compares them in their own type.
+ * Errors: as eg_compute, plus EG_ERR_ARG for an unknown dtype or a misaligned
+ * field; EG_ERR_NAN for a float64 NaN. */
+EG_API eg_status eg_compute_typed(eg_handle h, const void *field, int dtype, int d, const int64_t *extents,
+                                  void *stream, eg_result_id *out);
+
+/* Size in bytes of one element of type `dtype`, 0 if dtype is unknown. */
+EG_API size_t eg_dtype_size(int dtype);
 
 /* As eg_compute, for a field in HOST memory: the host-to-device copy of the
  * field is enqueued on `stream` first (through the handle's pinned staging
@@ -187,8 +229,9 @@ EG_API eg_status eg_get_paths(eg_handle h, eg_result_id id, uint64_t *path_ptr, 
                               uint64_t *n_path_vertices);
 
 /* Arc bundling (Sec. 3.5) on a finished result: when several saddles connect
- * the same two maxima, only the highest of them (value, then index; the
- * lowest for a minimum graph) stands for that pair.  keep[i] (caller-owned
+ * the same two maxima, only the highest of them (value in the field's own
+ * element type, then index; the lowest for a minimum graph) stands for that
+ * pair.  keep[i] (caller-owned
  * host memory, n_saddles bytes, in the order of eg_graph.saddles) is set to
  * 1 when saddle i stands for at least one pair of its arc ends, or connects
  * no pair (all its arcs end at one maximum), else 0; the bundled graph is the

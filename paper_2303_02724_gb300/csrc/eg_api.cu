@@ -23,6 +23,11 @@
 
 using namespace eg;
 
+static_assert(kF32 == EG_DTYPE_F32 && kF64 == EG_DTYPE_F64 && kI8 == EG_DTYPE_I8 && kU8 == EG_DTYPE_U8 &&
+                  kI16 == EG_DTYPE_I16 && kU16 == EG_DTYPE_U16 && kI32 == EG_DTYPE_I32 && kU32 == EG_DTYPE_U32 &&
+                  kI64 == EG_DTYPE_I64 && kU64 == EG_DTYPE_U64 && kNumTypes == EG_DTYPE_COUNT,
+              "internal element-type codes follow eg_dtype");
+
 namespace {
 
 eg_status from_cuda(cudaError_t e)
@@ -147,6 +152,8 @@ struct alignas(16) SmallBlock {
 
 struct Result {
     int d = 0;
+    uint32_t dtype = 0;     // element type of the field and of the value copies
+    void *wide = nullptr;   // float32 image of a narrow integer field (while classifying)
     int64_t ext[kMaxDim] = {0, 0, 0, 0};
     uint64_t N = 0;
     uint32_t flags = 0;
@@ -254,12 +261,15 @@ struct Layout {
     size_t smem;
 };
 
-Layout make_layout(const Shape &sh, int sm_count, const eg_config &cfg)
+Layout make_layout(const Shape &sh, int sm_count, const eg_config &cfg, uint32_t dtype = kF32)
 {
     Layout L{};
     L.kd = sh.d == 4 ? 4 : 3;
     const uint32_t n0 = sh.n[0], n1 = sh.n[1], n2 = sh.n[2];
-    if (L.kd == 3 && n0 <= 1024) {
+    // the plane-marching classifier reads float32 (the field, or the float32
+    // image of a narrow integer field); other types take the flat classifier
+    const bool f32_values = dtype == kF32 || dtype_narrow(dtype);
+    if (L.kd == 3 && n0 <= 1024 && f32_values) {
         // one thread per 8 consecutive vertices of a row, 256 threads per CTA
         const uint32_t txn = (n0 + 7) / 8;
         uint32_t ty = 256 / txn;
@@ -348,8 +358,8 @@ eg_status ensure_workspace(eg_ctx *h, uint64_t recs, uint64_t bricks, uint64_t t
 
 void free_result_buffers(eg_ctx *h, Result *r)
 {
-    void **bufs[] = {&r->lab,  &r->maxima, &r->max_val, &r->saddles,  &r->sad_b0,   &r->sad_val, &r->row_ptr,
-                     &r->col,  &r->ends,   &r->ucnt,    &r->path_ptr, &r->path_vtx, &r->pbrick};
+    void **bufs[] = {&r->lab, &r->maxima,   &r->max_val,  &r->saddles, &r->sad_b0, &r->sad_val, &r->row_ptr,
+                     &r->col, &r->ends,     &r->ucnt,     &r->path_ptr, &r->path_vtx, &r->pbrick, &r->wide};
     for (void **b : bufs) {
         h->pool.release(*b);
         *b = nullptr;
@@ -366,9 +376,10 @@ void release_launch(eg_ctx *h, Launch *L)
 }
 
 struct Job {
-    const float *field;
+    const void *field;
     Shape sh;
     uint32_t flags;
+    uint32_t dtype = kF32;
 };
 
 // One launch slice: fields of one classifier kind, contiguous in the table.
@@ -378,6 +389,14 @@ struct Group {
     size_t smem;
     bool zm, minimum;
     int kd;
+    uint32_t cdt;  // type the classifier compares in (float32 for narrow integers)
+};
+
+// A field (table position) whose element type needs extra work.
+struct TypedField {
+    int pos;
+    uint32_t dtype;
+    uint64_t n;
 };
 
 // Everything the enqueue phases of one call need besides the table contents.
@@ -388,6 +407,9 @@ struct Plan {
     uint64_t total_rtiles = 0;  // tiled resolution pass (3D kernels)
     size_t desc_bytes = 0;
     int walks = 4, ctas = 3;
+    int sm_count = 0;
+    std::vector<TypedField> widen;   // narrow integer fields: float32 image before classification
+    std::vector<TypedField> values;  // non-float32 fields: value copies after assembly
     std::string signature;  // identical for calls that can share a captured graph
 };
 
@@ -409,6 +431,10 @@ eg_status enqueue_part(eg_ctx *h, int part, const Plan &P, const FieldDev *Dd, c
             return from_cuda(e);
         if ((e = launch_init_fields(Dd, P.nf, st)) != cudaSuccess) return from_cuda(e);
         nl++;
+        for (const TypedField &t : P.widen) {
+            if ((e = launch_widen(t.dtype, Dd + t.pos, t.n, P.sm_count, st)) != cudaSuccess) return from_cuda(e);
+            nl++;
+        }
         for (size_t gi = 0; gi < P.groups.size(); gi++) {
             const Group &G = P.groups[gi];
             if (G.zm)
@@ -417,7 +443,7 @@ eg_status enqueue_part(eg_ctx *h, int part, const Plan &P, const FieldDev *Dd, c
                                        reinterpret_cast<unsigned long long *>(h->ws_scan) + 2 + gi, h->sm_count,
                                        P.ctas, st);
             else
-                e = launch_classify_flat(G.kd, Dd + G.first, G.count, G.bricks, st);
+                e = launch_classify_flat(G.kd, G.cdt, Dd + G.first, G.count, G.bricks, st);
             if (e != cudaSuccess) return from_cuda(e);
             nl++;
         }
@@ -442,6 +468,10 @@ eg_status enqueue_part(eg_ctx *h, int part, const Plan &P, const FieldDev *Dd, c
         if ((e = launch_scan(true, Dd, P.nf, P.total_tiles, h->ws_scan, st)) != cudaSuccess) return from_cuda(e);
         if ((e = launch_csr(Dd, P.nf, P.total_bricks, st)) != cudaSuccess) return from_cuda(e);
         nl += 2;
+        for (const TypedField &t : P.values) {
+            if ((e = launch_values(t.dtype, Dd + t.pos, P.sm_count, st)) != cudaSuccess) return from_cuda(e);
+            nl++;
+        }
     }
     if (launches) *launches = nl;
     return EG_OK;
@@ -584,15 +614,16 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
 {
     const int nf = int(jobs.size());
     std::vector<Layout> lay(nf);
-    for (int i = 0; i < nf; i++) lay[i] = make_layout(jobs[i].sh, h->sm_count, cfg);
+    for (int i = 0; i < nf; i++) lay[i] = make_layout(jobs[i].sh, h->sm_count, cfg, jobs[i].dtype);
     // the arc geometry needs the gradient pointers after the counts are known
     // and before resolution: such calls run step by step, without graphs
     bool any_paths = false;
     for (int i = 0; i < nf; i++) any_paths = any_paths || (jobs[i].flags & kFlagPaths);
     if (any_paths) use_graph = false;
     // group fields by classifier kind so every launch covers a contiguous slice
+    auto cdt = [&](int i) { return dtype_narrow(jobs[i].dtype) ? uint32_t(kF32) : jobs[i].dtype; };
     auto key = [&](int i) {
-        return (lay[i].zm ? 0 : 2) * 16 + lay[i].kd * 2 + ((jobs[i].flags & kFlagMinimum) ? 1 : 0);
+        return int(cdt(i)) * 64 + (lay[i].zm ? 0 : 2) * 16 + lay[i].kd * 2 + ((jobs[i].flags & kFlagMinimum) ? 1 : 0);
     };
     std::vector<int> order(nf);
     for (int i = 0; i < nf; i++) order[i] = i;
@@ -602,6 +633,7 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
     P.nf = nf;
     P.walks = cfg.resolve_walks > 0 ? cfg.resolve_walks : 4;
     P.ctas = cfg.persistent_ctas > 0 ? cfg.persistent_ctas : 3;
+    P.sm_count = h->sm_count;
     uint64_t total_recs = 0;
     for (int i = 0; i < nf; i++) {
         P.total_bricks += lay[i].nbricks;
@@ -642,22 +674,31 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
         const Job &j = jobs[i];
         const Layout &ly = lay[i];
         if (P.groups.empty() || P.groups.back().key != key(i))
-            P.groups.push_back({key(i), oi, 0, brick0, 0, 0, 0, ly.zm, (j.flags & kFlagMinimum) != 0, ly.kd});
+            P.groups.push_back({key(i), oi, 0, brick0, 0, 0, 0, ly.zm, (j.flags & kFlagMinimum) != 0, ly.kd, cdt(i)});
         Group &G = P.groups.back();
         auto r = std::make_unique<Result>();
         r->d = j.sh.d;
         for (int q = 0; q < kMaxDim; q++) r->ext[q] = q < j.sh.d ? j.sh.n[q] : 0;
         r->N = j.sh.N;
         r->flags = j.flags;
+        r->dtype = j.dtype;
         r->launch = L;
         e = h->pool.alloc(&r->lab, j.sh.N * sizeof(uint32_t));
+        if (e == cudaSuccess && dtype_narrow(j.dtype)) e = h->pool.alloc(&r->wide, j.sh.N * sizeof(float));
         r->small = static_cast<SmallBlock *>(L->smalls) + i;
         r->slot = i;
         res[i] = std::move(r);
         if (e != cudaSuccess) return fail(from_cuda(e));
         Result &R = *res[i];
         FieldDev &F = Dh[oi];
-        F.f = j.field;
+        // the float32 kernels read the field itself, or the float32 image of
+        // a narrow integer field; the 32/64-bit types are read through fraw
+        F.f = j.dtype == kF32 ? static_cast<const float *>(j.field)
+                              : (dtype_narrow(j.dtype) ? static_cast<const float *>(R.wide) : nullptr);
+        F.fraw = j.field;
+        F.dtype = j.dtype;
+        if (dtype_narrow(j.dtype)) P.widen.push_back({oi, j.dtype, j.sh.N});
+        if (j.dtype != kF32) P.values.push_back({oi, j.dtype, j.sh.N});
         F.lab = static_cast<uint32_t *>(R.lab);
         F.rec_sid = static_cast<uint32_t *>(h->ws_rec_sid) + rec0;
         F.rec_info = static_cast<uint64_t *>(h->ws_rec_info) + rec0;
@@ -679,7 +720,7 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
         F.nyb = ly.nyb;
         F.zc = ly.zc;
         F.nzc = ly.nzc;
-        F.vec = (j.sh.n[0] % 4 == 0 && (reinterpret_cast<uintptr_t>(j.field) & 15) == 0) ? 1u : 0u;
+        F.vec = (j.sh.n[0] % 4 == 0 && (reinterpret_cast<uintptr_t>(F.f) & 15) == 0) ? 1u : 0u;
         F.brick0 = brick0;
         F.item0 = G.items;
         F.stile0 = tile0;
@@ -699,8 +740,8 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
         rec0 += uint64_t(ly.nbricks) * ly.bcap;
         tile0 += scan_tiles(ly.nbricks);
         char fs[192];
-        std::snprintf(fs, sizeof fs, "%d,%d,%u,%u,%u,%u,%u,%u,%u,%u,%u,%u,%u;", key(i), ly.kd, F.N, ly.ty, ly.nyb,
-                      ly.nbricks, ly.zc, ly.nzc, F.vec, F.n[0], F.n[1], F.n[2], F.n[3]);
+        std::snprintf(fs, sizeof fs, "%d,%d,%u,%u,%u,%u,%u,%u,%u,%u,%u,%u,%u,%u;", key(i), ly.kd, F.N, ly.ty, ly.nyb,
+                      ly.nbricks, ly.zc, ly.nzc, F.vec, F.n[0], F.n[1], F.n[2], F.n[3], j.dtype);
         P.signature += fs;
     }
 
@@ -809,17 +850,23 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
     for (int oi = 0; oi < nf; oi++) {
         Result &r = *res[order[oi]];
         FieldDev &F = Dh[oi];
+        const size_t es = dtype_size(r.dtype);
         struct { void **p; size_t b; } want[] = {
-            {&r.maxima, r.M * 4}, {&r.max_val, r.M * 4}, {&r.saddles, r.S * 4}, {&r.sad_b0, r.S},
-            {&r.sad_val, r.S * 4}, {&r.row_ptr, (r.S + 1) * 8}, {&r.col, r.P * 4},
+            {&r.maxima, r.M * 4}, {&r.max_val, r.M * es}, {&r.saddles, r.S * 4}, {&r.sad_b0, r.S},
+            {&r.sad_val, r.S * es}, {&r.row_ptr, (r.S + 1) * 8}, {&r.col, r.P * 4},
             {&r.ends, r.P * 4}, {&r.ucnt, r.S}};
         for (auto &w : want)
-            if ((e = h->pool.alloc(w.p, std::max<size_t>(w.b, 4))) != cudaSuccess) return fail(from_cuda(e));
+            if ((e = h->pool.alloc(w.p, std::max<size_t>(w.b, 8))) != cudaSuccess) return fail(from_cuda(e));
         F.maxima = static_cast<uint32_t *>(r.maxima);
-        F.max_val = static_cast<float *>(r.max_val);
         F.saddles = static_cast<uint32_t *>(r.saddles);
         F.sad_b0 = static_cast<uint8_t *>(r.sad_b0);
-        F.sad_val = static_cast<float *>(r.sad_val);
+        // float32 value copies come with the records; other types are copied
+        // from the field after assembly
+        const bool f32 = r.dtype == kF32;
+        F.max_val = f32 ? static_cast<float *>(r.max_val) : nullptr;
+        F.sad_val = f32 ? static_cast<float *>(r.sad_val) : nullptr;
+        F.max_raw = f32 ? nullptr : r.max_val;
+        F.sad_raw = f32 ? nullptr : r.sad_val;
         F.row_ptr = static_cast<uint64_t *>(r.row_ptr);
         F.col = static_cast<uint32_t *>(r.col);
         F.ends = static_cast<uint32_t *>(r.ends);
@@ -878,7 +925,8 @@ eg_status collect(eg_ctx *h, Result &r)
         h->pool.release(r.ends);
         h->pool.release(r.ucnt);
         h->pool.release(r.pbrick);
-        r.ends = r.ucnt = r.pbrick = nullptr;
+        h->pool.release(r.wide);
+        r.ends = r.ucnt = r.pbrick = r.wide = nullptr;
         if (r.launch && r.launch.use_count() == 1) release_launch(h, r.launch.get());
     }
     if (r.err & kErrNaN) return EG_ERR_NAN;
@@ -891,6 +939,7 @@ eg_status collect(eg_ctx *h, Result &r)
 void fill_counts(const Result &r, eg_graph *out)
 {
     out->d = r.d;
+    out->dtype = int32_t(r.dtype);
     for (int i = 0; i < kMaxDim; i++) out->extents[i] = r.ext[i];
     out->n_vertices = int64_t(r.N);
     out->n_maxima = int64_t(r.M);
@@ -1014,6 +1063,27 @@ eg_status eg_compute(eg_handle h, const float *field, int d, const int64_t *exte
     return s;
 }
 
+size_t eg_dtype_size(int dtype)
+{
+    return dtype >= 0 && dtype < int(kNumTypes) ? dtype_size(uint32_t(dtype)) : 0;
+}
+
+eg_status eg_compute_typed(eg_handle h, const void *field, int dtype, int d, const int64_t *extents,
+                           void *stream, eg_result_id *out)
+{
+    if (!h || !field || !out || dtype < 0 || dtype >= int(kNumTypes)) return EG_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(field) % dtype_size(uint32_t(dtype)) != 0) return EG_ERR_ARG;
+    Shape sh;
+    if (!make_shape(d, extents, sh)) return EG_ERR_ARG;
+    std::lock_guard<std::mutex> g(h->mu);
+    cudaSetDevice(h->device);
+    std::vector<Job> jobs{{field, sh, h->cfg.flags & (kFlagMinimum | kFlagNoLabels | kFlagPaths), uint32_t(dtype)}};
+    std::vector<uint64_t> ids;
+    eg_status s = run_jobs(h, jobs, static_cast<cudaStream_t>(stream), ids, h->cfg);
+    if (s == EG_OK) *out = ids[0];
+    return s;
+}
+
 eg_status eg_compute_host(eg_handle h, const float *field, int d, const int64_t *extents, void *stream,
                           eg_result_id *out)
 {
@@ -1065,16 +1135,33 @@ eg_status eg_compute_host(eg_handle h, const float *field, int d, const int64_t 
     return s;
 }
 
+}  // extern "C"
+
+namespace {
+
+// A batch descriptor as a job; false on a bad field.
+bool job_of(eg_ctx *h, const eg_field_desc &fd, Job &j)
+{
+    if (!fd.field || !make_shape(fd.d, fd.extents, j.sh)) return false;
+    const uint32_t dt = (uint32_t(fd.flags) & EG_FLAG_DTYPE_MASK) >> 16;
+    if (dt >= kNumTypes || reinterpret_cast<uintptr_t>(fd.field) % dtype_size(dt) != 0) return false;
+    j.field = fd.field;
+    j.dtype = dt;
+    j.flags = (h->cfg.flags | uint32_t(fd.flags)) & (kFlagMinimum | kFlagNoLabels | kFlagPaths);
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
 eg_status eg_batch_submit(eg_handle h, const eg_field_desc *fields, int n, void *stream, eg_result_id *out_ids)
 {
     if (!h || (n > 0 && (!fields || !out_ids)) || n < 0) return EG_ERR_ARG;
     if (n == 0) return EG_OK;
     std::vector<Job> jobs(n);
-    for (int i = 0; i < n; i++) {
-        if (!fields[i].field || !make_shape(fields[i].d, fields[i].extents, jobs[i].sh)) return EG_ERR_ARG;
-        jobs[i].field = fields[i].field;
-        jobs[i].flags = (h->cfg.flags | uint32_t(fields[i].flags)) & (kFlagMinimum | kFlagNoLabels | kFlagPaths);
-    }
+    for (int i = 0; i < n; i++)
+        if (!job_of(h, fields[i], jobs[i])) return EG_ERR_ARG;
     std::lock_guard<std::mutex> g(h->mu);
     cudaSetDevice(h->device);
     std::vector<uint64_t> ids;
@@ -1135,11 +1222,8 @@ eg_status eg_autotune(eg_handle h, const eg_field_desc *fields, int n, void *str
 {
     if (!h || n <= 0 || !fields) return EG_ERR_ARG;
     std::vector<Job> jobs(n);
-    for (int i = 0; i < n; i++) {
-        if (!fields[i].field || !make_shape(fields[i].d, fields[i].extents, jobs[i].sh)) return EG_ERR_ARG;
-        jobs[i].field = fields[i].field;
-        jobs[i].flags = (h->cfg.flags | uint32_t(fields[i].flags)) & (kFlagMinimum | kFlagNoLabels | kFlagPaths);
-    }
+    for (int i = 0; i < n; i++)
+        if (!job_of(h, fields[i], jobs[i])) return EG_ERR_ARG;
     std::lock_guard<std::mutex> g(h->mu);
     cudaSetDevice(h->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1191,10 +1275,11 @@ eg_status eg_get_graph(eg_handle h, eg_result_id id, eg_graph *out)
     eg_status s = collect(h, r);
     fill_counts(r, out);
     if (s != EG_OK) return s;
+    const size_t es = dtype_size(r.dtype);
     struct { void *dst; const void *src; size_t b; } cp[] = {
-        {out->maxima, r.maxima, r.M * 4}, {out->max_val, r.max_val, r.M * 4},
+        {out->maxima, r.maxima, r.M * 4}, {out->max_val, r.max_val, r.M * es},
         {out->saddles, r.saddles, r.S * 4}, {out->sad_beta0, r.sad_b0, r.S},
-        {out->sad_val, r.sad_val, r.S * 4}, {out->row_ptr, r.row_ptr, (r.S + 1) * 8},
+        {out->sad_val, r.sad_val, r.S * es}, {out->row_ptr, r.row_ptr, (r.S + 1) * 8},
         {out->col, r.col, r.A * 4}, {out->labels, r.lab, r.N * 4}};
     // all copies in flight at once on the side stream (they overlap when the
     // destinations are pinned), then one wait
@@ -1248,10 +1333,10 @@ eg_status eg_get_bundled(eg_handle h, eg_result_id id, uint8_t *keep)
     if (r.S == 0) return EG_OK;
     if (!keep) return EG_ERR_ARG;
     cudaStream_t st = h->side;
-    void *small = nullptr, *keys = nullptr, *best = nullptr, *dkeep = nullptr;
+    void *small = nullptr, *keys = nullptr, *best = nullptr, *dkeep = nullptr, *best_id = nullptr;
     auto done = [&](eg_status x) {
         cudaStreamSynchronize(st);
-        for (void *p : {small, keys, best, dkeep}) h->pool.release(p);
+        for (void *p : {small, keys, best, dkeep, best_id}) h->pool.release(p);
         return x;
     };
     cudaError_t e;
@@ -1273,12 +1358,25 @@ eg_status eg_get_bundled(eg_handle h, eg_result_id id, uint8_t *keep)
     if ((e = h->pool.alloc(&dkeep, r.S)) != cudaSuccess) return done(from_cuda(e));
     if ((e = cudaMemsetAsync(keys, 0xff, tb, st)) != cudaSuccess) return done(from_cuda(e));
     if ((e = cudaMemsetAsync(best, 0, tb, st)) != cudaSuccess) return done(from_cuda(e));
-    if ((e = launch_bundle(row_ptr, static_cast<const uint32_t *>(r.col), static_cast<const uint32_t *>(r.saddles),
-                           static_cast<const float *>(r.sad_val), r.S, (r.flags & kFlagMinimum) != 0,
-                           static_cast<unsigned long long *>(keys), static_cast<unsigned long long *>(best), lg,
-                           static_cast<uint8_t *>(dkeep), err, st)) != cudaSuccess)
-        return done(from_cuda(e));
-    h->launches += 3;
+    if (r.dtype == kF32) {
+        if ((e = launch_bundle(row_ptr, static_cast<const uint32_t *>(r.col),
+                               static_cast<const uint32_t *>(r.saddles), static_cast<const float *>(r.sad_val), r.S,
+                               (r.flags & kFlagMinimum) != 0, static_cast<unsigned long long *>(keys),
+                               static_cast<unsigned long long *>(best), lg, static_cast<uint8_t *>(dkeep), err,
+                               st)) != cudaSuccess)
+            return done(from_cuda(e));
+        h->launches += 3;
+    } else {
+        if ((e = h->pool.alloc(&best_id, size_t(4) << lg)) != cudaSuccess) return done(from_cuda(e));
+        if ((e = cudaMemsetAsync(best_id, 0, size_t(4) << lg, st)) != cudaSuccess) return done(from_cuda(e));
+        if ((e = launch_bundle_typed(r.dtype, row_ptr, static_cast<const uint32_t *>(r.col),
+                                     static_cast<const uint32_t *>(r.saddles), r.sad_val, r.S,
+                                     (r.flags & kFlagMinimum) != 0, static_cast<unsigned long long *>(keys),
+                                     static_cast<unsigned long long *>(best), static_cast<unsigned int *>(best_id),
+                                     lg, static_cast<uint8_t *>(dkeep), err, st)) != cudaSuccess)
+            return done(from_cuda(e));
+        h->launches += 4;
+    }
     uint32_t herr = 0;
     if ((e = cudaMemcpyAsync(keep, dkeep, r.S, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return done(from_cuda(e));
     if ((e = cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return done(from_cuda(e));
@@ -1298,10 +1396,10 @@ eg_status eg_get_graph_device(eg_handle h, eg_result_id id, eg_graph *out)
     fill_counts(r, out);
     if (s != EG_OK) return s;
     out->maxima = static_cast<uint32_t *>(r.maxima);
-    out->max_val = static_cast<float *>(r.max_val);
+    out->max_val = r.max_val;
     out->saddles = static_cast<uint32_t *>(r.saddles);
     out->sad_beta0 = static_cast<uint8_t *>(r.sad_b0);
-    out->sad_val = static_cast<float *>(r.sad_val);
+    out->sad_val = r.sad_val;
     out->row_ptr = static_cast<uint64_t *>(r.row_ptr);
     out->col = static_cast<uint32_t *>(r.col);
     out->labels = static_cast<uint32_t *>(r.lab);

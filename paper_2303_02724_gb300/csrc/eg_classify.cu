@@ -9,8 +9,13 @@
 //
 // This is the general kernel (any d in 1..4, any extents): one CTA per flat
 // brick of kFlatBrick consecutive vertex ids, neighbour values read through
-// the read-only cache.  2D/3D fields with rows of at most 1024 vertices use the
-// plane-marching kernel of eg_classify_zm.cu instead.
+// the read-only cache.  2D/3D float32 fields with rows of at most 1024
+// vertices use the plane-marching kernel of eg_classify_zm.cu instead.
+//
+// It is also the classifier of the 32- and 64-bit element types (Sec. 5):
+// values are loaded as raw bits and mapped to order keys of the same width
+// (key(a) < key(b) iff a < b in the type itself), so the comparison is exact
+// in the type; the simulated-perturbation rank sits below the key.
 //
 // Every maximum and saddle of a brick is written, in index order, into that
 // brick's record slot, so a scan over per-brick counts gives global positions.
@@ -22,22 +27,44 @@ namespace eg {
 constexpr int kClassifyThreads = 256;
 constexpr int kVpt = kFlatBrick / kClassifyThreads;
 
-// Monotone key of a float: a < b (IEEE, non-NaN) <=> key(a) < key(b); -0 == +0.
-__device__ __forceinline__ uint32_t order_key(float x)
+// Comparison word: the order key above an 8-bit neighbourhood rank (the
+// simulated perturbation inside one neighbourhood: rank order is index order).
+template <typename B>
+struct CmpWord;
+template <>
+struct CmpWord<uint32_t> {
+    using W = uint64_t;
+    static __device__ __forceinline__ W make(uint32_t k, uint32_t r) { return (W(k) << 8) | r; }
+};
+template <>
+struct CmpWord<uint64_t> {
+    using W = unsigned __int128;
+    static __device__ __forceinline__ W make(uint64_t k, uint32_t r) { return (W(k) << 8) | r; }
+};
+
+// Raw bits of element v: float32 reads F.f (the field, or the float32 image of
+// a narrow integer field), every other type reads the field itself.
+template <uint32_t DT>
+__device__ __forceinline__ typename TypeKey<DT>::B load_bits(const FieldDev &F, uint32_t v)
 {
-    uint32_t u = __float_as_uint(x);
-    u = (u == 0x80000000u) ? 0u : u;
-    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    using B = typename TypeKey<DT>::B;
+    if constexpr (DT == kF32) return __float_as_uint(__ldg(F.f + v));
+    else if constexpr (sizeof(B) == 8) return B(__ldg(static_cast<const unsigned long long *>(F.fraw) + v));
+    else return B(__ldg(static_cast<const unsigned int *>(F.fraw) + v));
 }
 
 // Classify vertex v of field F.  Returns asc(v); sets b0 and the packed rep
 // slots (5 bits per component, component order arbitrary).
-template <int D>
+template <int D, uint32_t DT>
 __device__ __forceinline__ uint32_t classify_vertex(const FieldDev &F, const uint32_t (&s)[kMaxDim],
                                                     uint32_t v, const uint32_t *s_adj, bool minimum,
                                                     int &b0, uint64_t &codes, bool &nan)
 {
     using NB = Nbr<D>;
+    using TK = TypeKey<DT>;
+    using B = typename TK::B;
+    using CW = CmpWord<B>;
+    using W = typename CW::W;
     constexpr int K = NB::K;
     // coordinates -> in-bounds masks per axis
     uint32_t pok = 0, mok = 0, rem = v;
@@ -53,19 +80,19 @@ __device__ __forceinline__ uint32_t classify_vertex(const FieldDev &F, const uin
         if (c + 1 < F.n[i]) pok |= 1u << i;
         if (c > 0) mok |= 1u << i;
     }
-    const uint32_t flip = minimum ? 0xffffffffu : 0u;
-    float fv = __ldg(F.f + v);
-    nan = fv != fv;
-    const uint64_t cc = (uint64_t(order_key(fv) ^ flip) << 8) | uint64_t(NB::H);
-    uint64_t cmp[K];
+    const B flip = minimum ? ~B(0) : B(0);
+    const B bv = load_bits<DT>(F, v);
+    nan = TK::nan(bv);
+    const W cc = CW::make(TK::key(bv) ^ flip, uint32_t(NB::H));
+    W cmp[K];
     uint32_t upper = 0, asc = v;
-    uint64_t best = 0;
+    W best = 0;
     int bestk = -1;
 #pragma unroll
     for (int k = 0; k < K; k++) {
         const uint32_t p = NB::pat(k);
         const bool inb = NB::neg(k) ? ((p & ~mok) == 0) : ((p & ~pok) == 0);
-        uint64_t ck = 0;
+        W ck = 0;
         uint32_t w = 0;
         if (inb) {
             uint32_t o = 0;
@@ -74,7 +101,7 @@ __device__ __forceinline__ uint32_t classify_vertex(const FieldDev &F, const uin
                 if (p & (1u << i)) o += s[i];
             w = NB::neg(k) ? v - o : v + o;
             const uint32_t r = minimum ? uint32_t(2 * NB::H) - NB::rank(k) : NB::rank(k);
-            ck = (uint64_t(order_key(__ldg(F.f + w)) ^ flip) << 8) | r;
+            ck = CW::make(TK::key(load_bits<DT>(F, w)) ^ flip, r);
         }
         cmp[k] = ck;
         if (ck > cc) {
@@ -99,7 +126,7 @@ __device__ __forceinline__ uint32_t classify_vertex(const FieldDev &F, const uin
     while (left) {
         uint32_t c2 = link_flood(left & (~left + 1u), upper, s_adj);
         left &= ~c2;
-        uint64_t rb = 0;
+        W rb = 0;
         int rk = 0;
 #pragma unroll
         for (int k = 0; k < K; k++)
@@ -114,7 +141,7 @@ __device__ __forceinline__ uint32_t classify_vertex(const FieldDev &F, const uin
 }
 
 // Classification of brick b of field F (one CTA, kClassifyThreads threads).
-template <int D>
+template <int D, uint32_t DT>
 __device__ __forceinline__ void classify_brick(const FieldDev &F, uint32_t b)
 {
     using NB = Nbr<D>;
@@ -144,10 +171,12 @@ __device__ __forceinline__ void classify_brick(const FieldDev &F, uint32_t b)
         if (valid) {
             bool nan;
             const uint32_t v = uint32_t(v64);
-            const uint32_t asc = classify_vertex<D>(F, s, v, s_adj, minimum, b0, codes, nan);
+            const uint32_t asc = classify_vertex<D, DT>(F, s, v, s_adj, minimum, b0, codes, nan);
             anynan |= nan;
             F.lab[v] = asc;
-            fv = F.f[v];
+            // (other element types get their value copies from the field
+            // itself once the graph is assembled)
+            if constexpr (DT == kF32) fv = F.f[v];
         }
         const bool crit = valid && b0 != 1;
         uint32_t tot;
@@ -177,14 +206,14 @@ __device__ __forceinline__ void classify_brick(const FieldDev &F, uint32_t b)
     if (tid == 0) F.bcnt[b] = make_uint4(s_cnt[0], s_cnt[1], s_cnt[2], 0u);
 }
 
-template <int D>
+template <int D, uint32_t DT>
 __global__ void __launch_bounds__(kClassifyThreads)
 k_classify(const FieldDev *__restrict__ fields, int nf)
 {
     const uint64_t g = fields[0].brick0 + blockIdx.x;
     const int fi = find_field<false>(fields, nf, g);
     const FieldDev &F = fields[fi];
-    classify_brick<D>(F, uint32_t(g - F.brick0));
+    classify_brick<D, DT>(F, uint32_t(g - F.brick0));
 }
 
 // Single-field variant with the descriptor passed by value (no descriptor
@@ -193,15 +222,29 @@ template <int D>
 __global__ void __launch_bounds__(kClassifyThreads)
 k_classify_one(const FieldDev F)
 {
-    classify_brick<D>(F, blockIdx.x);
+    classify_brick<D, kF32>(F, blockIdx.x);
 }
 
-template <int D>
+template <int D, uint32_t DT>
 cudaError_t launch_classify(const FieldDev *fields, int nf, uint64_t bricks, cudaStream_t st)
 {
     if (bricks == 0) return cudaSuccess;
-    k_classify<D><<<dim3(unsigned(bricks)), kClassifyThreads, 0, st>>>(fields, nf);
+    k_classify<D, DT><<<dim3(unsigned(bricks)), kClassifyThreads, 0, st>>>(fields, nf);
     return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t launch_classify_typed(uint32_t dtype, const FieldDev *fields, int nf, uint64_t bricks, cudaStream_t st)
+{
+    switch (dtype) {
+    case kF32: return launch_classify<D, kF32>(fields, nf, bricks, st);
+    case kF64: return launch_classify<D, kF64>(fields, nf, bricks, st);
+    case kI32: return launch_classify<D, kI32>(fields, nf, bricks, st);
+    case kU32: return launch_classify<D, kU32>(fields, nf, bricks, st);
+    case kI64: return launch_classify<D, kI64>(fields, nf, bricks, st);
+    case kU64: return launch_classify<D, kU64>(fields, nf, bricks, st);
+    default: return cudaErrorInvalidValue;  // narrow integers are classified as their float32 image
+    }
 }
 
 cudaError_t launch_classify_one(int kd, const FieldDev &F, cudaStream_t st)
@@ -213,11 +256,12 @@ cudaError_t launch_classify_one(int kd, const FieldDev &F, cudaStream_t st)
     return cudaGetLastError();
 }
 
-cudaError_t launch_classify_flat(int kd, const FieldDev *fields, int nf, uint64_t bricks, cudaStream_t st)
+cudaError_t launch_classify_flat(int kd, uint32_t dtype, const FieldDev *fields, int nf, uint64_t bricks,
+                                 cudaStream_t st)
 {
     switch (kd) {
-    case 3: return launch_classify<3>(fields, nf, bricks, st);
-    case 4: return launch_classify<4>(fields, nf, bricks, st);
+    case 3: return launch_classify_typed<3>(dtype, fields, nf, bricks, st);
+    case 4: return launch_classify_typed<4>(dtype, fields, nf, bricks, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -109,7 +109,7 @@ k_nodes(const FieldDev *__restrict__ fields, int nf, uint64_t base, uint64_t bri
             const uint64_t q = m_off + lm;
             if (q < capM) {
                 F.maxima[q] = sid;
-                F.max_val[q] = val;
+                if (F.max_val) F.max_val[q] = val;  // (other element types: copied after assembly)
             } else {
                 atomicOr(F.err, kErrInternal);
             }
@@ -119,7 +119,7 @@ k_nodes(const FieldDev *__restrict__ fields, int nf, uint64_t base, uint64_t bri
             if (q < capS && p + b0 <= capP) {
                 F.saddles[q] = sid;
                 F.sad_b0[q] = uint8_t(b0);
-                F.sad_val[q] = val;
+                if (F.sad_val) F.sad_val[q] = val;
                 F.ucnt[q] = uint8_t(u);
                 for (int e = 0; e < u; e++) F.ends[p + e] = tmp[e];
             } else {

@@ -50,9 +50,100 @@ enum : uint32_t {
 // flags carried per field
 enum : uint32_t { kFlagMinimum = 1u, kFlagNoLabels = 2u, kFlagPaths = 8u };
 
+// element types of a field (the values of eg_dtype)
+enum : uint32_t {
+    kF32 = 0, kF64 = 1, kI8 = 2, kU8 = 3, kI16 = 4, kU16 = 5, kI32 = 6, kU32 = 7, kI64 = 8, kU64 = 9,
+    kNumTypes = 10
+};
+
+__host__ __device__ __forceinline__ uint32_t dtype_size(uint32_t t)
+{
+    return t == kI8 || t == kU8 ? 1u : (t == kI16 || t == kU16 ? 2u : (t == kF64 || t == kI64 || t == kU64 ? 8u : 4u));
+}
+
+// Integers of at most 16 bits: exact in float32 with order and ties kept, so
+// they are widened to float32 and take the float32 kernels.
+__host__ __device__ __forceinline__ bool dtype_narrow(uint32_t t) { return t >= kI8 && t <= kU16; }
+
+// Raw bits of an element type and their order key: a < b (in the type; IEEE
+// and non-NaN for floats) <=> key(a) < key(b); -0 and +0 share a key.
+template <uint32_t DT>
+struct TypeKey;
+template <>
+struct TypeKey<kF32> {
+    using B = uint32_t;
+    static __device__ __forceinline__ B key(B u)
+    {
+        u = (u == 0x80000000u) ? 0u : u;
+        return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    }
+    static __device__ __forceinline__ bool nan(B u) { return (u & 0x7fffffffu) > 0x7f800000u; }
+};
+template <>
+struct TypeKey<kF64> {
+    using B = uint64_t;
+    static __device__ __forceinline__ B key(B u)
+    {
+        constexpr B sign = 1ull << 63;
+        u = (u == sign) ? 0ull : u;
+        return (u & sign) ? ~u : (u | sign);
+    }
+    static __device__ __forceinline__ bool nan(B u) { return (u & ~(1ull << 63)) > 0x7ff0000000000000ull; }
+};
+template <>
+struct TypeKey<kI32> {
+    using B = uint32_t;
+    static __device__ __forceinline__ B key(B u) { return u ^ 0x80000000u; }
+    static __device__ __forceinline__ bool nan(B) { return false; }
+};
+template <>
+struct TypeKey<kU32> {
+    using B = uint32_t;
+    static __device__ __forceinline__ B key(B u) { return u; }
+    static __device__ __forceinline__ bool nan(B) { return false; }
+};
+template <>
+struct TypeKey<kI64> {
+    using B = uint64_t;
+    static __device__ __forceinline__ B key(B u) { return u ^ (1ull << 63); }
+    static __device__ __forceinline__ bool nan(B) { return false; }
+};
+template <>
+struct TypeKey<kI8> {
+    using B = uint32_t;  // the 8 bits, zero-extended
+    static __device__ __forceinline__ B key(B u) { return u ^ 0x80u; }
+    static __device__ __forceinline__ bool nan(B) { return false; }
+};
+template <>
+struct TypeKey<kU8> {
+    using B = uint32_t;
+    static __device__ __forceinline__ B key(B u) { return u; }
+    static __device__ __forceinline__ bool nan(B) { return false; }
+};
+template <>
+struct TypeKey<kI16> {
+    using B = uint32_t;  // the 16 bits, zero-extended
+    static __device__ __forceinline__ B key(B u) { return u ^ 0x8000u; }
+    static __device__ __forceinline__ bool nan(B) { return false; }
+};
+template <>
+struct TypeKey<kU16> {
+    using B = uint32_t;
+    static __device__ __forceinline__ B key(B u) { return u; }
+    static __device__ __forceinline__ bool nan(B) { return false; }
+};
+template <>
+struct TypeKey<kU64> {
+    using B = uint64_t;
+    static __device__ __forceinline__ B key(B u) { return u; }
+    static __device__ __forceinline__ bool nan(B) { return false; }
+};
+
 // One field as the kernels see it.  Plain pointers; filled on the host.
 struct FieldDev {
-    const float *f;          // [N] input values
+    const float *f;          // [N] float32 values the float32 kernels read: the field itself,
+                             //     or its float32 image (8/16-bit integer fields)
+    const void *fraw;        // [N] the field in its own element type (== f for float32)
     uint32_t *lab;           // [N] gradient pointer, then the label (maximum reached)
     // classification records: one slot of bcap entries per brick, index order
     uint32_t *rec_sid;       // vertex id
@@ -66,10 +157,12 @@ struct FieldDev {
     uint8_t *ucnt;           // [S] unique arc count per saddle
     // outputs
     uint32_t *maxima;        // [M]
-    float *max_val;          // [M]
+    float *max_val;          // [M] float32 fields (null for other element types)
     uint32_t *saddles;       // [S]
     uint8_t *sad_b0;         // [S]
-    float *sad_val;          // [S]
+    float *sad_val;          // [S] float32 fields (null for other element types)
+    void *max_raw;           // [M] value copies in the field's element type (non-float32 fields)
+    void *sad_raw;           // [S]
     uint64_t *row_ptr;       // [S+1]
     uint32_t *col;           // [A]
     unsigned long long *totals;  // [4] M, S, P, A
@@ -95,6 +188,7 @@ struct FieldDev {
     uint32_t rt[3];          // log2 of the resolution tile extents (3D kernels; 0 tiles for 4D)
     int32_t kd;              // kernel dimension (2D fields run as 3D)
     uint32_t flags;
+    uint32_t dtype;          // element type of fraw
 };
 
 __host__ __device__ __forceinline__ void brick_range(const FieldDev &F, uint32_t b, uint64_t &v0, uint32_t &len)

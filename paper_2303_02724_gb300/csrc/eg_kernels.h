@@ -7,9 +7,20 @@
 namespace eg {
 
 // Steps (a)+(c), general kernel: one CTA per flat brick (any d, any extents).
-// fields: the slice of descriptors using this kernel dimension; the grid
-// covers their bricks, global ids from fields[0].brick0.
-cudaError_t launch_classify_flat(int kd, const FieldDev *fields, int nf, uint64_t bricks, cudaStream_t st);
+// fields: the slice of descriptors using this kernel dimension and
+// classification type (float32 for narrow integer fields, whose float32
+// image it reads; else the element type); the grid covers their bricks,
+// global ids from fields[0].brick0.
+cudaError_t launch_classify_flat(int kd, uint32_t dtype, const FieldDev *fields, int nf, uint64_t bricks,
+                                 cudaStream_t st);
+
+// Element types (Sec. 5).  Widening of a narrow integer field (fields[i].fraw,
+// 8/16-bit) to its float32 image fields[i].f; value copies of a non-float32
+// field's maxima and saddles (after the graph is assembled; M and S read
+// from the device counters).  Both read the descriptor at `field` (so they
+// can be captured in graphs).
+cudaError_t launch_widen(uint32_t dtype, const FieldDev *field, uint64_t n, int sm_count, cudaStream_t st);
+cudaError_t launch_values(uint32_t dtype, const FieldDev *field, int sm_count, cudaStream_t st);
 
 // Steps (a)+(c), plane-marching kernel for 2D/3D fields with rows of at most
 // 1024 vertices.  lut: the 2-bit class of every 14-bit upper mask (1024 words),
@@ -68,5 +79,13 @@ cudaError_t launch_bundle_pairs(const uint64_t *row_ptr, uint64_t S, unsigned lo
 cudaError_t launch_bundle(const uint64_t *row_ptr, const uint32_t *col, const uint32_t *saddles,
                           const float *sad_val, uint64_t S, bool minimum, unsigned long long *keys,
                           unsigned long long *best, uint32_t lg, uint8_t *keep, uint32_t *err, cudaStream_t st);
+// The same for a field of another element type: saddle values sad_raw in
+// that type; the highest saddle of a pair is found in two rounds (its value
+// key in best, then its vertex id among the saddles with that value in
+// best_id; both tables zeroed).
+cudaError_t launch_bundle_typed(uint32_t dtype, const uint64_t *row_ptr, const uint32_t *col,
+                                const uint32_t *saddles, const void *sad_raw, uint64_t S, bool minimum,
+                                unsigned long long *keys, unsigned long long *best, unsigned int *best_id,
+                                uint32_t lg, uint8_t *keep, uint32_t *err, cudaStream_t st);
 
 }  // namespace eg

@@ -25,6 +25,17 @@ EG_FLAG_NO_LABELS = 0x2
 EG_FLAG_NO_GRAPH = 0x4
 EG_FLAG_PATHS = 0x8
 
+# element types (eg_dtype): numpy dtype <-> code; EG_FLAG_DTYPE(t) = t << 16
+DTYPES = {np.dtype(np.float32): 0, np.dtype(np.float64): 1, np.dtype(np.int8): 2, np.dtype(np.uint8): 3,
+          np.dtype(np.int16): 4, np.dtype(np.uint16): 5, np.dtype(np.int32): 6, np.dtype(np.uint32): 7,
+          np.dtype(np.int64): 8, np.dtype(np.uint64): 9}
+DTYPE_OF_CODE = {v: k for k, v in DTYPES.items()}
+
+
+def dtype_flag(dtype) -> int:
+    """eg_field_desc.flags bits naming a field's element type."""
+    return DTYPES[np.dtype(dtype)] << 16
+
 
 class EGError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
@@ -48,7 +59,7 @@ class EGFieldDesc(ctypes.Structure):
 
 
 class EGGraphC(ctypes.Structure):
-    _fields_ = [("d", ctypes.c_int32), ("extents", ctypes.c_int64 * MAX_DIM),
+    _fields_ = [("d", ctypes.c_int32), ("dtype", ctypes.c_int32), ("extents", ctypes.c_int64 * MAX_DIM),
                 ("n_vertices", ctypes.c_int64), ("n_maxima", ctypes.c_int64),
                 ("n_saddles", ctypes.c_int64), ("n_paths", ctypes.c_int64),
                 ("n_arcs", ctypes.c_int64),
@@ -68,6 +79,9 @@ SIGNATURES = {
     "eg_destroy": (ctypes.c_int, [_P]),
     "eg_compute": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, ctypes.POINTER(ctypes.c_uint64)]),
     "eg_compute_host": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, ctypes.POINTER(ctypes.c_uint64)]),
+    "eg_compute_typed": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int, _P, _P,
+                                        ctypes.POINTER(ctypes.c_uint64)]),
+    "eg_dtype_size": (ctypes.c_size_t, [ctypes.c_int]),
     "eg_batch_submit": (ctypes.c_int, [_P, ctypes.POINTER(EGFieldDesc), ctypes.c_int, _P,
                                         ctypes.POINTER(ctypes.c_uint64)]),
     "eg_get_graph": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(EGGraphC)]),
@@ -156,14 +170,16 @@ class GraphBuffers:
     buffers can be reused for every result that fits (the Graph returned by
     get_graph then views them, so it is only valid until the next reuse)."""
 
-    _FIELDS = (("maxima", np.uint32, "M"), ("max_val", np.float32, "M"), ("saddles", np.uint32, "S"),
-               ("sad_b0", np.uint8, "S"), ("sad_val", np.float32, "S"), ("row_ptr", np.uint64, "S1"),
+    _FIELDS = (("maxima", np.uint32, "M"), ("max_val", None, "M"), ("saddles", np.uint32, "S"),
+               ("sad_b0", np.uint8, "S"), ("sad_val", None, "S"), ("row_ptr", np.uint64, "S1"),
                ("col", np.uint32, "A"), ("labels", np.uint32, "N"))
 
-    def __init__(self, M: int, S: int, A: int, N: int = 0, pinned: bool = False):
+    def __init__(self, M: int, S: int, A: int, N: int = 0, pinned: bool = False, dtype=np.float32):
         self.cap = {"M": int(M), "S": int(S), "S1": int(S) + 1, "A": int(A), "N": int(N)}
+        self.dtype = np.dtype(dtype)  # element type of the value copies
         self.arrays = {}
         for name, dt, k in self._FIELDS:
+            dt = self.dtype if dt is None else dt
             n = self.cap[k]
             if pinned and n:
                 import torch
@@ -172,12 +188,13 @@ class GraphBuffers:
             else:
                 self.arrays[name] = np.empty(n, dt)
 
-    def fits(self, M: int, S: int, A: int, N: int = 0) -> bool:
+    def fits(self, M: int, S: int, A: int, N: int = 0, dtype=np.float32) -> bool:
         c = self.cap
-        return M <= c["M"] and S <= c["S"] and A <= c["A"] and N <= c["N"]
+        return (M <= c["M"] and S <= c["S"] and A <= c["A"] and N <= c["N"]
+                and np.dtype(dtype) == self.dtype)
 
-    def views(self, M: int, S: int, A: int, N: int = 0) -> Graph:
-        if not self.fits(M, S, A, N):
+    def views(self, M: int, S: int, A: int, N: int = 0, dtype=np.float32) -> Graph:
+        if not self.fits(M, S, A, N, dtype):
             raise ValueError("result larger than the buffers")
         a = self.arrays
         return Graph(d=0, extents=(), n_vertices=0, n_paths=0, maxima=a["maxima"][:M], max_val=a["max_val"][:M],
@@ -229,16 +246,30 @@ class Handle:
         self.close()
 
     # ---------------------------------------------------------------- submit
-    def compute(self, field, stream=None) -> int:
-        """field: contiguous float32 CUDA tensor; axis 0 of the grid is its LAST dim."""
-        if not field.is_cuda or field.dtype.itemsize != 4 or not field.is_contiguous():
-            raise ValueError("field must be a contiguous float32 CUDA tensor")
+    def compute(self, field, stream=None, dtype=None) -> int:
+        """field: contiguous CUDA tensor; axis 0 of the grid is its LAST dim.
+        dtype None: float32 (eg_compute).  Otherwise a numpy element type (see
+        DTYPES): the tensor holds the elements as raw bytes of that size (any
+        torch dtype of the same item size, e.g. from device_array) and the call
+        is eg_compute_typed."""
+        if not field.is_cuda or not field.is_contiguous():
+            raise ValueError("field must be a contiguous CUDA tensor")
         ext = _extents_of(field.shape)
         e = (ctypes.c_int64 * max(1, len(ext)))(*ext)
         rid = ctypes.c_uint64()
-        _check(self._lib.eg_compute(self._h, ctypes.c_void_p(field.data_ptr()), len(ext), e,
-                                    ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(rid)),
-               "eg_compute")
+        if dtype is None:
+            if field.dtype.itemsize != 4:
+                raise ValueError("field must be a float32 CUDA tensor (or pass dtype)")
+            _check(self._lib.eg_compute(self._h, ctypes.c_void_p(field.data_ptr()), len(ext), e,
+                                        ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(rid)),
+                   "eg_compute")
+        else:
+            dt = np.dtype(dtype)
+            if dt not in DTYPES or field.element_size() != dt.itemsize:
+                raise ValueError(f"element type {dt} does not match the tensor")
+            _check(self._lib.eg_compute_typed(self._h, ctypes.c_void_p(field.data_ptr()), DTYPES[dt], len(ext),
+                                              e, ctypes.c_void_p(_stream_ptr(stream)), ctypes.byref(rid)),
+                   "eg_compute_typed")
         return rid.value
 
     def compute_host(self, field: np.ndarray, stream=None) -> int:
@@ -252,9 +283,12 @@ class Handle:
                "eg_compute_host")
         return rid.value
 
-    def batch_submit(self, fields: Sequence, stream=None, flags: Sequence[int] = ()) -> list:
+    def batch_submit(self, fields: Sequence, stream=None, flags: Sequence[int] = (),
+                     dtypes: Sequence = ()) -> list:
+        """dtypes[i] (numpy element type, default float32) names the element
+        type of fields[i] (a CUDA tensor of that item size)."""
         n = len(fields)
-        descs = self._descs(fields, flags)
+        descs = self._descs(fields, flags, dtypes)
         ids = (ctypes.c_uint64 * max(1, n))()
         _check(self._lib.eg_batch_submit(self._h, descs, n, ctypes.c_void_p(_stream_ptr(stream)), ids),
                "eg_batch_submit")
@@ -268,16 +302,17 @@ class Handle:
                                      ctypes.byref(best)), "eg_autotune")
         return best.as_dict()
 
-    def _descs(self, fields, flags=()):
+    def _descs(self, fields, flags=(), dtypes=()):
         n = len(fields)
         descs = (EGFieldDesc * max(1, n))()
         for i, f in enumerate(fields):
-            if not f.is_cuda or f.dtype.itemsize != 4 or not f.is_contiguous():
-                raise ValueError("fields must be contiguous float32 CUDA tensors")
+            dt = np.dtype(dtypes[i]) if i < len(dtypes) and dtypes[i] is not None else np.dtype(np.float32)
+            if not f.is_cuda or dt not in DTYPES or f.element_size() != dt.itemsize or not f.is_contiguous():
+                raise ValueError("fields must be contiguous CUDA tensors of their element types")
             ext = _extents_of(f.shape)
             descs[i].field = f.data_ptr()
             descs[i].d = len(ext)
-            descs[i].flags = int(flags[i]) if i < len(flags) else 0
+            descs[i].flags = (int(flags[i]) if i < len(flags) else 0) | (DTYPES[dt] << 16)
             for k, x in enumerate(ext):
                 descs[i].extents[k] = x
         return descs
@@ -296,9 +331,10 @@ class Handle:
         g = EGGraphC()
         _check(self._lib.eg_get_graph(self._h, ctypes.c_uint64(rid), ctypes.byref(g)), "eg_get_graph")
         M, S, A, N = g.n_maxima, g.n_saddles, g.n_arcs, g.n_vertices
+        vdt = DTYPE_OF_CODE[g.dtype]
         if buffers is None:
-            buffers = GraphBuffers(M, S, A, N if labels else 0)
-        out = buffers.views(M, S, A, N if labels else 0)
+            buffers = GraphBuffers(M, S, A, N if labels else 0, dtype=vdt)
+        out = buffers.views(M, S, A, N if labels else 0, dtype=vdt)
         out.d, out.extents, out.n_vertices, out.n_paths = g.d, tuple(g.extents[:g.d]), N, g.n_paths
         if not labels:
             out.labels = None
@@ -403,3 +439,15 @@ def labels_static(field, labels, minimum: bool = False, stream=None):
 def workspace_bytes(extents) -> int:
     e = (ctypes.c_int64 * max(1, len(extents)))(*extents)
     return int(load().eg_workspace_bytes(len(extents), e))
+
+
+def device_array(a: np.ndarray, device: int = 0):
+    """Copy a numpy array of any element type in DTYPES to a CUDA tensor with
+    the same bytes and shape (unsigned types travel as the signed torch type
+    of the same size); pass its numpy dtype to Handle.compute / batch_submit."""
+    import torch
+    a = np.ascontiguousarray(a)
+    view = {1: np.int8, 2: np.int16, 4: np.int32, 8: np.int64}
+    if a.dtype.kind == "u" and a.dtype != np.uint8:
+        a = a.view(view[a.dtype.itemsize])
+    return torch.from_numpy(a).to(f"cuda:{device}")
