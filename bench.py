@@ -144,23 +144,28 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def path_bytes(c):
+def path_bytes(c, es=4):
     """Algorithmic bytes of one field: read f, write labels, the graph and its
-    value copies (maxima, saddles, beta0+, row_ptr as uint64, col)."""
+    value copies (maxima, saddles, beta0+, row_ptr as uint64, col).  es: bytes
+    per value of the field's element type."""
     N, M, S, A = c["n_vertices"], c["n_maxima"], c["n_saddles"], c["n_arcs"]
     geometry = 4 * c["n_path_vertices"] + 8 * (c["n_paths"] + 1) if "n_path_vertices" in c else 0
-    return 4 * N + 4 * N + 8 * M + 9 * S + 8 * (S + 1) + 4 * A + geometry
+    return es * N + 4 * N + (4 + es) * M + (5 + es) * S + 8 * (S + 1) + 4 * A + geometry
 
 
-def kernel_bytes(c):
+def kernel_bytes(c, es=4):
     """Compulsory bytes of each step's own contract (inputs read once, outputs
     written once).  classify: f, gradient pointers, critical records (12 B),
     counts; resolve: pointers in, labels out; emit: records in, graph out."""
     N, M, S, P, A = c["n_vertices"], c["n_maxima"], c["n_saddles"], c["n_paths"], c["n_arcs"]
     rec = 12 * (M + S)
-    return {"classify": 4 * N + 4 * N + rec,
+    return {"classify": es * N + 4 * N + rec,
             "resolve": 4 * N + 4 * N,
-            "emit": rec + 4 * P + 8 * M + 9 * S + 8 * (S + 1) + 4 * A}
+            "emit": rec + 4 * P + (4 + es) * M + (5 + es) * S + 8 * (S + 1) + 4 * A}
+
+
+SHORT_DTYPE = {"float32": "f32", "float64": "f64", "int8": "i8", "uint8": "u8", "int16": "i16",
+               "uint16": "u16", "int32": "i32", "uint32": "u32", "int64": "i64", "uint64": "u64"}
 
 
 def graph_d2h_bytes(c):
@@ -429,6 +434,9 @@ def main():
                     help="also time arc bundling (eg_get_bundled) on one result of the workload")
     ap.add_argument("--paths", action="store_true",
                     help="also gather the arc geometry (EG_FLAG_PATHS) in every timed step")
+    ap.add_argument("--dtype", default="float32", choices=list(SHORT_DTYPE),
+                    help="element type of the single-field workload: the field quantised onto the "
+                         "integer type's range (plateaus for narrow types) or widened to float64")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--serve-requests", type=int, default=4096)
     ap.add_argument("--serve-fractions", type=float, nargs="+", default=[0.5, 0.8, 0.95])
@@ -454,19 +462,24 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     fld = make_field(args.workload)
+    typed = args.dtype != "float32"
+    if typed:
+        from paper_2303_02724_gb300 import fields as F
+        fld = F.quantise(fld, args.dtype)
+    es = fld.values.dtype.itemsize
     N = fld.n
-    t_field = torch.from_numpy(fld.values).to(dev)
+    t_field = eg.device_array(fld.values, local)
     stream = torch.cuda.current_stream(dev)
     h = eg.Handle(local, paths=args.paths)
     h.set_timing(True)
 
     def step():
-        rid = h.compute(t_field, stream)
+        rid = h.compute(t_field, stream, dtype=fld.values.dtype if typed else None)
         g = h.get_graph_device(rid)  # waits for the result (counts only)
         return rid, g
 
     L2_BYTES = 129 * 1024 * 1024
-    flush = None if 4 * N > 2 * L2_BYTES else torch.empty(64 << 20, dtype=torch.int32, device=dev)
+    flush = None if es * N > 2 * L2_BYTES else torch.empty(64 << 20, dtype=torch.int32, device=dev)
     counts = None
     for _ in range(args.warmup):
         rid, g = step()
@@ -526,11 +539,11 @@ def main():
     names = ["classify", "resolve", "emit"]
     mean_ms = {nm: statistics.mean(s[i] for s in step_ms) for i, nm in enumerate(names)}
     dom = max(mean_ms, key=mean_ms.get)
-    kb = kernel_bytes(counts)
+    kb = kernel_bytes(counts, es)
     peak, peak_kind = peaks()
     achieved = kb[dom] / (mean_ms[dom] / 1e3) / 1e9
     mean_step_ms = statistics.mean(s[3] for s in step_ms)
-    pb = path_bytes(counts)
+    pb = path_bytes(counts, es)
     path_achieved = pb / (mean_step_ms / 1e3) / 1e9
 
     bundle = None
@@ -550,7 +563,7 @@ def main():
     # end to end through the C ABI with host buffers: H2D of the field and
     # D2H of the graph inside the timed region
     e2e = None
-    if not args.no_e2e and not args.paths:
+    if not args.no_e2e and not args.paths and not typed:
         host = torch.from_numpy(fld.values).pin_memory().numpy()
         # two host threads, each with its own handle, stream and page-locked
         # output buffers (allocated once, reused), take alternate steps, so one
@@ -612,7 +625,7 @@ def main():
         runs = []
         for _ in range(7):
             t0 = time.perf_counter()
-            oracle.compute(sample)
+            oracle.compute(sample, dtype=sample.dtype)
             runs.append(time.perf_counter() - t0)
         dt = statistics.mean(sorted(runs)[1:-1])
         cpu = {"value": sample.size / dt / 1e6, "unit": "Mvertices/s", "cores": 1, "kind": "oracle",
@@ -623,16 +636,18 @@ def main():
         line = {
             "metric": "Mvertices/s full extremum graph (bit-exact)", "value": value, "unit": "Mvertices/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": SHORT_DTYPE[args.dtype],
             "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload] + ("; with the arc geometry (EG_FLAG_PATHS)"
-                                                               if args.paths else ""),
+                                                               if args.paths else "")
+                       + (f"; quantised to {args.dtype}" if typed and fld.values.dtype.kind in "iu" else "")
+                       + ("; widened to float64" if args.dtype == "float64" else ""),
                        "vertices": N, "l2": "inputs larger than L2"
                        if flush is None else "L2 flushed before every step (256 MB written)",
                        "parallelism": f"replicas x{ws}", **{k: v for k, v in counts.items() if k != "n_vertices"}},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
-                         "traffic": traffic_from_profiles(dom, args.workload),
+                         "traffic": None if typed else traffic_from_profiles(dom, args.workload),
                          "algorithmic_bytes": kb[dom], "ms": mean_ms[dom]},
             "path_roofline": {"achieved": path_achieved, "frac": path_achieved / peak,
                               "algorithmic_bytes": pb, "ms": mean_step_ms},

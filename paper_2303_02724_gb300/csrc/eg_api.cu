@@ -409,7 +409,6 @@ struct Plan {
     int walks = 4, ctas = 3;
     int sm_count = 0;
     std::vector<TypedField> widen;   // narrow integer fields: float32 image before classification
-    std::vector<TypedField> values;  // non-float32 fields: value copies after assembly
     std::string signature;  // identical for calls that can share a captured graph
 };
 
@@ -468,10 +467,6 @@ eg_status enqueue_part(eg_ctx *h, int part, const Plan &P, const FieldDev *Dd, c
         if ((e = launch_scan(true, Dd, P.nf, P.total_tiles, h->ws_scan, st)) != cudaSuccess) return from_cuda(e);
         if ((e = launch_csr(Dd, P.nf, P.total_bricks, st)) != cudaSuccess) return from_cuda(e);
         nl += 2;
-        for (const TypedField &t : P.values) {
-            if ((e = launch_values(t.dtype, Dd + t.pos, P.sm_count, st)) != cudaSuccess) return from_cuda(e);
-            nl++;
-        }
     }
     if (launches) *launches = nl;
     return EG_OK;
@@ -698,7 +693,6 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
         F.fraw = j.field;
         F.dtype = j.dtype;
         if (dtype_narrow(j.dtype)) P.widen.push_back({oi, j.dtype, j.sh.N});
-        if (j.dtype != kF32) P.values.push_back({oi, j.dtype, j.sh.N});
         F.lab = static_cast<uint32_t *>(R.lab);
         F.rec_sid = static_cast<uint32_t *>(h->ws_rec_sid) + rec0;
         F.rec_info = static_cast<uint64_t *>(h->ws_rec_info) + rec0;
@@ -861,7 +855,7 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
         F.saddles = static_cast<uint32_t *>(r.saddles);
         F.sad_b0 = static_cast<uint8_t *>(r.sad_b0);
         // float32 value copies come with the records; other types are copied
-        // from the field after assembly
+        // from the field by the node kernel
         const bool f32 = r.dtype == kF32;
         F.max_val = f32 ? static_cast<float *>(r.max_val) : nullptr;
         F.sad_val = f32 ? static_cast<float *>(r.sad_val) : nullptr;

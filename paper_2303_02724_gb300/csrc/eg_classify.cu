@@ -27,21 +27,6 @@ namespace eg {
 constexpr int kClassifyThreads = 256;
 constexpr int kVpt = kFlatBrick / kClassifyThreads;
 
-// Comparison word: the order key above an 8-bit neighbourhood rank (the
-// simulated perturbation inside one neighbourhood: rank order is index order).
-template <typename B>
-struct CmpWord;
-template <>
-struct CmpWord<uint32_t> {
-    using W = uint64_t;
-    static __device__ __forceinline__ W make(uint32_t k, uint32_t r) { return (W(k) << 8) | r; }
-};
-template <>
-struct CmpWord<uint64_t> {
-    using W = unsigned __int128;
-    static __device__ __forceinline__ W make(uint64_t k, uint32_t r) { return (W(k) << 8) | r; }
-};
-
 // Raw bits of element v: float32 reads F.f (the field, or the float32 image of
 // a narrow integer field), every other type reads the field itself.
 template <uint32_t DT>
@@ -55,6 +40,12 @@ __device__ __forceinline__ typename TypeKey<DT>::B load_bits(const FieldDev &F, 
 
 // Classify vertex v of field F.  Returns asc(v); sets b0 and the packed rep
 // slots (5 bits per component, component order arbitrary).
+//
+// Inside one neighbourhood the simulated perturbation needs no index
+// arithmetic: slot order is index order, so among equal values a positive
+// slot (larger index) is higher than the centre and a negative one lower;
+// among neighbours, the later slot is higher.  The minimum graph complements
+// the keys and mirrors both rules.
 template <int D, uint32_t DT>
 __device__ __forceinline__ uint32_t classify_vertex(const FieldDev &F, const uint32_t (&s)[kMaxDim],
                                                     uint32_t v, const uint32_t *s_adj, bool minimum,
@@ -63,8 +54,6 @@ __device__ __forceinline__ uint32_t classify_vertex(const FieldDev &F, const uin
     using NB = Nbr<D>;
     using TK = TypeKey<DT>;
     using B = typename TK::B;
-    using CW = CmpWord<B>;
-    using W = typename CW::W;
     constexpr int K = NB::K;
     // coordinates -> in-bounds masks per axis
     uint32_t pok = 0, mok = 0, rem = v;
@@ -83,16 +72,17 @@ __device__ __forceinline__ uint32_t classify_vertex(const FieldDev &F, const uin
     const B flip = minimum ? ~B(0) : B(0);
     const B bv = load_bits<DT>(F, v);
     nan = TK::nan(bv);
-    const W cc = CW::make(TK::key(bv) ^ flip, uint32_t(NB::H));
-    W cmp[K];
+    const B kv = TK::key(bv) ^ flip;
+    B key[K];
     uint32_t upper = 0, asc = v;
-    W best = 0;
+    B best = 0;
     int bestk = -1;
 #pragma unroll
     for (int k = 0; k < K; k++) {
         const uint32_t p = NB::pat(k);
         const bool inb = NB::neg(k) ? ((p & ~mok) == 0) : ((p & ~pok) == 0);
-        W ck = 0;
+        B kw = 0;
+        bool up = false;
         uint32_t w = 0;
         if (inb) {
             uint32_t o = 0;
@@ -100,14 +90,17 @@ __device__ __forceinline__ uint32_t classify_vertex(const FieldDev &F, const uin
             for (int i = 0; i < D; i++)
                 if (p & (1u << i)) o += s[i];
             w = NB::neg(k) ? v - o : v + o;
-            const uint32_t r = minimum ? uint32_t(2 * NB::H) - NB::rank(k) : NB::rank(k);
-            ck = CW::make(TK::key(load_bits<DT>(F, w)) ^ flip, r);
+            kw = TK::key(load_bits<DT>(F, w)) ^ flip;
+            // ties: higher iff the slot lies above the centre in the order
+            up = (NB::neg(k) == minimum) ? kw >= kv : kw > kv;
         }
-        cmp[k] = ck;
-        if (ck > cc) {
+        key[k] = kw;
+        if (up) {
             upper |= 1u << k;
-            if (ck > best) {
-                best = ck;
+            // the highest upper neighbour; among equal keys the later slot
+            // (maximum graph) or the earlier one (minimum graph)
+            if (bestk < 0 || (minimum ? kw > best : kw >= best)) {
+                best = kw;
                 bestk = k;
                 asc = w;
             }
@@ -126,12 +119,12 @@ __device__ __forceinline__ uint32_t classify_vertex(const FieldDev &F, const uin
     while (left) {
         uint32_t c2 = link_flood(left & (~left + 1u), upper, s_adj);
         left &= ~c2;
-        W rb = 0;
-        int rk = 0;
+        B rb = 0;
+        int rk = -1;
 #pragma unroll
         for (int k = 0; k < K; k++)
-            if (((c2 >> k) & 1u) && cmp[k] > rb) {
-                rb = cmp[k];
+            if (((c2 >> k) & 1u) && (rk < 0 || (minimum ? key[k] > rb : key[k] >= rb))) {
+                rb = key[k];
                 rk = k;
             }
         codes |= uint64_t(rk) << (5 * b0);

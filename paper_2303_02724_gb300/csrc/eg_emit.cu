@@ -45,6 +45,19 @@ __device__ __forceinline__ int saddle_ends(const uint32_t *lab, const uint32_t (
     return n;
 }
 
+// Value copy of a vertex of a non-float32 field: the element's bits.
+__device__ __forceinline__ void copy_value(const FieldDev &F, uint32_t v, void *dst, uint64_t q)
+{
+    switch (dtype_size(F.dtype)) {
+    case 1: static_cast<uint8_t *>(dst)[q] = static_cast<const uint8_t *>(F.fraw)[v]; break;
+    case 2: static_cast<uint16_t *>(dst)[q] = static_cast<const uint16_t *>(F.fraw)[v]; break;
+    case 4: static_cast<uint32_t *>(dst)[q] = static_cast<const uint32_t *>(F.fraw)[v]; break;
+    default:
+        static_cast<unsigned long long *>(dst)[q] = static_cast<const unsigned long long *>(F.fraw)[v];
+        break;
+    }
+}
+
 // Inclusive warp scan of a packed 64-bit counter; returns the exclusive value,
 // *total receives the warp sum.
 __device__ __forceinline__ uint64_t warp_excl_scan_u64(uint64_t x, uint64_t *total)
@@ -109,7 +122,8 @@ k_nodes(const FieldDev *__restrict__ fields, int nf, uint64_t base, uint64_t bri
             const uint64_t q = m_off + lm;
             if (q < capM) {
                 F.maxima[q] = sid;
-                if (F.max_val) F.max_val[q] = val;  // (other element types: copied after assembly)
+                if (F.max_val) F.max_val[q] = val;
+                else copy_value(F, sid, F.max_raw, q);  // other element types: from the field
             } else {
                 atomicOr(F.err, kErrInternal);
             }
@@ -120,6 +134,7 @@ k_nodes(const FieldDev *__restrict__ fields, int nf, uint64_t base, uint64_t bri
                 F.saddles[q] = sid;
                 F.sad_b0[q] = uint8_t(b0);
                 if (F.sad_val) F.sad_val[q] = val;
+                else copy_value(F, sid, F.sad_raw, q);
                 F.ucnt[q] = uint8_t(u);
                 for (int e = 0; e < u; e++) F.ends[p + e] = tmp[e];
             } else {

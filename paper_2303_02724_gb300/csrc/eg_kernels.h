@@ -14,13 +14,10 @@ namespace eg {
 cudaError_t launch_classify_flat(int kd, uint32_t dtype, const FieldDev *fields, int nf, uint64_t bricks,
                                  cudaStream_t st);
 
-// Element types (Sec. 5).  Widening of a narrow integer field (fields[i].fraw,
-// 8/16-bit) to its float32 image fields[i].f; value copies of a non-float32
-// field's maxima and saddles (after the graph is assembled; M and S read
-// from the device counters).  Both read the descriptor at `field` (so they
-// can be captured in graphs).
+// Element types (Sec. 5): widening of a narrow integer field (field->fraw,
+// 8/16-bit, n elements) to its float32 image field->f.  Reads the descriptor
+// on the device (so it can be captured in graphs).
 cudaError_t launch_widen(uint32_t dtype, const FieldDev *field, uint64_t n, int sm_count, cudaStream_t st);
-cudaError_t launch_values(uint32_t dtype, const FieldDev *field, int sm_count, cudaStream_t st);
 
 // Steps (a)+(c), plane-marching kernel for 2D/3D fields with rows of at most
 // 1024 vertices.  lut: the 2-bit class of every 14-bit upper mask (1024 words),
