@@ -38,6 +38,11 @@ WORKLOADS = {
                    "N(0,0.01) noise, seed 0"),
     "grf384": ("3D 384^3 float32 Gaussian random field, P(k)~k^-11/3, seed 2 (profiling case: larger than "
                "L2, a few GB on the device)"),
+    "schwefel4d128": ("4D 128^4 float32 Schwefel function sum_i -x_i sin(sqrt|x_i|) sampled on [-500,500]^4 "
+                      "(window shifted by seed 5); Freudenthal 30-neighbour; plain single-field path "
+                      "(the shape of Table 3's largest 4D row)"),
+    "schwefel4d64": ("4D 64^4 float32 Schwefel function on [-500,500]^4 (seed 5); Freudenthal 30-neighbour; "
+                     "plain single-field path (the shape of a Table 3 row)"),
     "serve": ("Served stream: requests with Poisson arrivals, each a float32 2D/3D/4D field (vertex count "
               "log-uniform 1e4..1e7, sums of U{4..64} Gaussians + 1e-3 uniform noise), seed 4; admission by "
               "free HBM, continuous batching on two engines, results kept in device memory"),
@@ -58,6 +63,10 @@ def make_field(name):
         return F.config_2d_256()
     if name == "grf384":
         return F.config_3d_512(side=384)
+    if name == "schwefel4d128":
+        return F.schwefel((128, 128, 128, 128))
+    if name == "schwefel4d64":
+        return F.schwefel((64, 64, 64, 64))
     raise ValueError(name)
 
 
