@@ -41,6 +41,8 @@ WORKLOADS = {
     "schwefel4d128": ("4D 128^4 float32 Schwefel function sum_i -x_i sin(sqrt|x_i|) sampled on [-500,500]^4 "
                       "(window shifted by seed 5); Freudenthal 30-neighbour; plain single-field path "
                       "(the shape of Table 3's largest 4D row)"),
+    "schwefel4d96": ("4D 96^4 float32 Schwefel function on [-500,500]^4 (seed 5) (profiling case: larger than "
+                     "L2, a few GB on the device)"),
     "schwefel4d64": ("4D 64^4 float32 Schwefel function on [-500,500]^4 (seed 5); Freudenthal 30-neighbour; "
                      "plain single-field path (the shape of a Table 3 row)"),
     "serve": ("Served stream: requests with Poisson arrivals, each a float32 2D/3D/4D field (vertex count "
@@ -65,6 +67,8 @@ def make_field(name):
         return F.config_3d_512(side=384)
     if name == "schwefel4d128":
         return F.schwefel((128, 128, 128, 128))
+    if name == "schwefel4d96":
+        return F.schwefel((96, 96, 96, 96))
     if name == "schwefel4d64":
         return F.schwefel((64, 64, 64, 64))
     raise ValueError(name)

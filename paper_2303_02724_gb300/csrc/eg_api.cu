@@ -257,6 +257,7 @@ bool make_shape(int d, const int64_t *ext, Shape &sh)
 struct Layout {
     int kd;
     bool zm;
+    bool r4;  // 4D row classifier (row layout over (z, w) planes)
     uint32_t ty, nyb, nbricks, bcap, zc, nzc;
     size_t smem;
 };
@@ -291,6 +292,19 @@ Layout make_layout(const Shape &sh, int sm_count, const eg_config &cfg, uint32_t
         }
         L.nzc = (n2 + L.zc - 1) / L.zc;
         L.smem = zm_smem_bytes(n0, ty);
+    } else if (L.kd == 4 && n0 <= 1024 && f32_values) {
+        // 4D row classifier: one thread per kR4Vertices consecutive vertices of
+        // a row, ty whole rows of one (z, w) plane per brick
+        const uint32_t txn = (n0 + kR4Vertices - 1) / kR4Vertices;
+        const uint32_t ty = std::max<uint32_t>(1, std::min<uint32_t>(uint32_t(kR4CtaThreads) / txn, n1));
+        L.zm = false;
+        L.r4 = true;
+        L.ty = ty;
+        L.nyb = (n1 + ty - 1) / ty;
+        L.nbricks = L.nyb * n2 * sh.n[3];
+        L.bcap = ty * n0;
+        L.zc = L.nzc = 0;
+        L.smem = 0;
     } else {
         L.zm = false;
         L.ty = 0;
@@ -390,6 +404,7 @@ struct Group {
     bool zm, minimum;
     int kd;
     uint32_t cdt;  // type the classifier compares in (float32 for narrow integers)
+    bool r4;
 };
 
 // A field (table position) whose element type needs extra work.
@@ -441,6 +456,8 @@ eg_status enqueue_part(eg_ctx *h, int part, const Plan &P, const FieldDev *Dd, c
                                        static_cast<const uint32_t *>(h->lut3),
                                        reinterpret_cast<unsigned long long *>(h->ws_scan) + 2 + gi, h->sm_count,
                                        P.ctas, st);
+            else if (G.r4)
+                e = launch_classify_r4(G.minimum, Dd + G.first, G.count, G.bricks, st);
             else
                 e = launch_classify_flat(G.kd, G.cdt, Dd + G.first, G.count, G.bricks, st);
             if (e != cudaSuccess) return from_cuda(e);
@@ -618,7 +635,8 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
     // group fields by classifier kind so every launch covers a contiguous slice
     auto cdt = [&](int i) { return dtype_narrow(jobs[i].dtype) ? uint32_t(kF32) : jobs[i].dtype; };
     auto key = [&](int i) {
-        return int(cdt(i)) * 64 + (lay[i].zm ? 0 : 2) * 16 + lay[i].kd * 2 + ((jobs[i].flags & kFlagMinimum) ? 1 : 0);
+        return int(cdt(i)) * 64 + (lay[i].zm ? 0 : (lay[i].r4 ? 1 : 2)) * 16 + lay[i].kd * 2 +
+               ((jobs[i].flags & kFlagMinimum) ? 1 : 0);
     };
     std::vector<int> order(nf);
     for (int i = 0; i < nf; i++) order[i] = i;
@@ -669,7 +687,8 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
         const Job &j = jobs[i];
         const Layout &ly = lay[i];
         if (P.groups.empty() || P.groups.back().key != key(i))
-            P.groups.push_back({key(i), oi, 0, brick0, 0, 0, 0, ly.zm, (j.flags & kFlagMinimum) != 0, ly.kd, cdt(i)});
+            P.groups.push_back(
+                {key(i), oi, 0, brick0, 0, 0, 0, ly.zm, (j.flags & kFlagMinimum) != 0, ly.kd, cdt(i), ly.r4});
         Group &G = P.groups.back();
         auto r = std::make_unique<Result>();
         r->d = j.sh.d;

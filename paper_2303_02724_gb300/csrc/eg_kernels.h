@@ -14,6 +14,13 @@ namespace eg {
 cudaError_t launch_classify_flat(int kd, uint32_t dtype, const FieldDev *fields, int nf, uint64_t bricks,
                                  cudaStream_t st);
 
+// Steps (a)+(c), row classifier for 4D float32 fields with rows of at most
+// 1024 vertices (row layout: ty whole rows of one (z, w) plane per brick);
+// one CTA per brick, global ids from fields[0].brick0.
+cudaError_t launch_classify_r4(bool minimum, const FieldDev *fields, int nf, uint64_t bricks, cudaStream_t st);
+constexpr int kR4Vertices = 4;    // vertices per thread along axis 0
+constexpr int kR4CtaThreads = 256;
+
 // Element types (Sec. 5): widening of a narrow integer field (field->fraw,
 // 8/16-bit, n elements) to its float32 image field->f.  Reads the descriptor
 // on the device (so it can be captured in graphs).
