@@ -45,6 +45,10 @@ WORKLOADS = {
                      "L2, a few GB on the device)"),
     "schwefel4d64": ("4D 64^4 float32 Schwefel function on [-500,500]^4 (seed 5); Freudenthal 30-neighbour; "
                      "plain single-field path (the shape of a Table 3 row)"),
+    "schwefel5d32": ("5D 32^5 float32 Schwefel function on [-500,500]^5 (seed 5); Freudenthal 62-neighbour; "
+                     "plain single-field path (the shape of a Table 3 row)"),
+    "schwefel5d64": ("5D 64^5 float32 Schwefel function on [-500,500]^5 (seed 5); Freudenthal 62-neighbour; "
+                     "plain single-field path (1.07 G vertices: the shape of Table 3's largest 5D row)"),
     "serve": ("Served stream: requests with Poisson arrivals, each a float32 2D/3D/4D field (vertex count "
               "log-uniform 1e4..1e7, sums of U{4..64} Gaussians + 1e-3 uniform noise), seed 4; admission by "
               "free HBM, continuous batching on two engines, results kept in device memory"),
@@ -69,6 +73,10 @@ def make_field(name):
         return F.schwefel((128, 128, 128, 128))
     if name == "schwefel4d96":
         return F.schwefel((96, 96, 96, 96))
+    if name == "schwefel5d32":
+        return F.schwefel((32,) * 5)
+    if name == "schwefel5d64":
+        return F.schwefel((64,) * 5)
     if name == "schwefel4d64":
         return F.schwefel((64, 64, 64, 64))
     raise ValueError(name)

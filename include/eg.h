@@ -3,7 +3,7 @@
  *
  * The library computes the extremum graph (maximum graph by default) of a
  * scalar field (float32 by default; 8- to 64-bit integers and float64 through
- * eg_compute_typed, Sec. 5) sampled on a d-dimensional regular grid, 1 <= d <= 4,
+ * eg_compute_typed, Sec. 5) sampled on a d-dimensional regular grid, 1 <= d <= 5,
  * under the Freudenthal triangulation of the grid (Sec. 3.2, Algorithm 1), as
  * defined in Sec. 2 of Ande, Subhash & Natarajan, "Tachyon: efficient shared
  * memory parallel computation of extremum graphs":
@@ -54,7 +54,7 @@ extern "C" {
 #define EG_API
 #endif
 
-#define EG_MAX_DIM 4
+#define EG_MAX_DIM 5
 
 typedef enum eg_status {
     EG_OK = 0,
@@ -156,7 +156,7 @@ EG_API eg_status eg_destroy(eg_handle h);
 
 /* Extremum graph of one field (Sec. 3.3 classification, Sec. 3.4 arcs).
  * field: device float32[N], caller-owned, must stay valid until the result is
- * read; d in 1..4; extents[0..d-1] >= 1, product < 2^32; stream: cudaStream_t.
+ * read; d in 1..5; extents[0..d-1] >= 1, product < 2^32; stream: cudaStream_t.
  * Enqueues classification, path resolution and graph assembly on `stream`; the
  * call itself waits only for the node counts (to size the result buffers).
  * On success *out names the result.

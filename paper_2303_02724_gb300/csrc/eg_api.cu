@@ -154,7 +154,7 @@ struct Result {
     int d = 0;
     uint32_t dtype = 0;     // element type of the field and of the value copies
     void *wide = nullptr;   // float32 image of a narrow integer field (while classifying)
-    int64_t ext[kMaxDim] = {0, 0, 0, 0};
+    int64_t ext[kMaxDim] = {};
     uint64_t N = 0;
     uint32_t flags = 0;
     void *lab = nullptr;
@@ -265,7 +265,7 @@ struct Layout {
 Layout make_layout(const Shape &sh, int sm_count, const eg_config &cfg, uint32_t dtype = kF32)
 {
     Layout L{};
-    L.kd = sh.d == 4 ? 4 : 3;
+    L.kd = sh.d == 5 ? 5 : (sh.d == 4 ? 4 : 3);
     const uint32_t n0 = sh.n[0], n1 = sh.n[1], n2 = sh.n[2];
     // the plane-marching classifier reads float32 (the field, or the float32
     // image of a narrow integer field); other types take the flat classifier

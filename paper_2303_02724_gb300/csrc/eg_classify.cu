@@ -38,8 +38,10 @@ __device__ __forceinline__ typename TypeKey<DT>::B load_bits(const FieldDev &F, 
     else return B(__ldg(static_cast<const unsigned int *>(F.fraw) + v));
 }
 
-// Classify vertex v of field F.  Returns asc(v); sets b0 and the packed rep
-// slots (5 bits per component, component order arbitrary).
+// Classify vertex v of field F.  Returns asc(v); sets b0 and the
+// representatives' slots in the record format of the dimension (rec_b0,
+// rec_slots): 5-bit fields up to 4D (component order arbitrary), a slot mask
+// in 5D.
 //
 // Inside one neighbourhood the simulated perturbation needs no index
 // arithmetic: slot order is index order, so among equal values a positive
@@ -48,10 +50,11 @@ __device__ __forceinline__ typename TypeKey<DT>::B load_bits(const FieldDev &F, 
 // the keys and mirrors both rules.
 template <int D, uint32_t DT>
 __device__ __forceinline__ uint32_t classify_vertex(const FieldDev &F, const uint32_t (&s)[kMaxDim],
-                                                    uint32_t v, const uint32_t *s_adj, bool minimum,
+                                                    uint32_t v, const typename Nbr<D>::Mask *s_adj, bool minimum,
                                                     int &b0, uint64_t &codes, bool &nan)
 {
     using NB = Nbr<D>;
+    using M = typename NB::Mask;
     using TK = TypeKey<DT>;
     using B = typename TK::B;
     constexpr int K = NB::K;
@@ -74,7 +77,8 @@ __device__ __forceinline__ uint32_t classify_vertex(const FieldDev &F, const uin
     nan = TK::nan(bv);
     const B kv = TK::key(bv) ^ flip;
     B key[K];
-    uint32_t upper = 0, asc = v;
+    M upper = 0;
+    uint32_t asc = v;
     B best = 0;
     int bestk = -1;
 #pragma unroll
@@ -96,7 +100,7 @@ __device__ __forceinline__ uint32_t classify_vertex(const FieldDev &F, const uin
         }
         key[k] = kw;
         if (up) {
-            upper |= 1u << k;
+            upper |= M(1) << k;
             // the highest upper neighbour; among equal keys the later slot
             // (maximum graph) or the earlier one (minimum graph)
             if (bestk < 0 || (minimum ? kw > best : kw >= best)) {
@@ -111,13 +115,13 @@ __device__ __forceinline__ uint32_t classify_vertex(const FieldDev &F, const uin
         b0 = 0;
         return v;
     }
-    uint32_t comp = link_flood(1u << bestk, upper, s_adj);
+    const M comp = link_flood(M(1) << bestk, upper, s_adj);
     b0 = 1;
     if (comp == upper) return asc;
-    codes = uint64_t(bestk);
-    uint32_t left = upper & ~comp;
+    codes = D == 5 ? (1ull << bestk) : uint64_t(bestk);
+    M left = upper & ~comp;
     while (left) {
-        uint32_t c2 = link_flood(left & (~left + 1u), upper, s_adj);
+        const M c2 = link_flood(left & (~left + M(1)), upper, s_adj);
         left &= ~c2;
         B rb = 0;
         int rk = -1;
@@ -127,7 +131,7 @@ __device__ __forceinline__ uint32_t classify_vertex(const FieldDev &F, const uin
                 rb = key[k];
                 rk = k;
             }
-        codes |= uint64_t(rk) << (5 * b0);
+        codes |= D == 5 ? (1ull << rk) : (uint64_t(rk) << (5 * b0));
         b0++;
     }
     return asc;
@@ -138,7 +142,7 @@ template <int D, uint32_t DT>
 __device__ __forceinline__ void classify_brick(const FieldDev &F, uint32_t b)
 {
     using NB = Nbr<D>;
-    __shared__ uint32_t s_adj[NB::K];
+    __shared__ typename NB::Mask s_adj[NB::K];
     __shared__ uint32_t s_scan[33];
     __shared__ unsigned s_cnt[3];
     const int tid = threadIdx.x;
@@ -176,7 +180,7 @@ __device__ __forceinline__ void classify_brick(const FieldDev &F, uint32_t b)
         const uint32_t pos = block_excl_scan(crit ? 1u : 0u, s_scan, &tot);
         if (crit) {
             F.rec_sid[slot + running + pos] = uint32_t(v64);
-            F.rec_info[slot + running + pos] = (uint64_t(b0) << 56) | codes;
+            F.rec_info[slot + running + pos] = D == 5 ? codes : ((uint64_t(b0) << 56) | codes);
             F.rec_val[slot + running + pos] = fv;
             if (b0 == 0) nm++;
             else {
@@ -255,6 +259,7 @@ cudaError_t launch_classify_flat(int kd, uint32_t dtype, const FieldDev *fields,
     switch (kd) {
     case 3: return launch_classify_typed<3>(dtype, fields, nf, bricks, st);
     case 4: return launch_classify_typed<4>(dtype, fields, nf, bricks, st);
+    case 5: return launch_classify_typed<5>(dtype, fields, nf, bricks, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -21,13 +21,13 @@ constexpr int kEmitThreads = 256;
 // Sorted unique arc ends of one saddle; returns their count.
 template <int KD>
 __device__ __forceinline__ int saddle_ends(const uint32_t *lab, const uint32_t (&s)[kMaxDim], uint32_t sid,
-                                           uint64_t info, uint32_t (&t)[kMaxComp])
+                                           uint64_t info, uint32_t (&t)[CompBound<KD>::value])
 {
-    const int b0 = int((info >> 56) & 0xfu);
+    int ks[CompBound<KD>::value];
+    const int b0 = rec_slots<KD>(info, ks);
     int n = 0;
-    for (int c = 0; c < b0 && c < kMaxComp; c++) {
-        const int k = int((info >> (5 * c)) & 31u);
-        const uint32_t m = lab[slot_vertex<KD>(sid, k, s)];
+    for (int c = 0; c < b0; c++) {
+        const uint32_t m = lab[slot_vertex<KD>(sid, ks[c], s)];
         int j = n;
         bool dup = false;
         while (j > 0 && t[j - 1] >= m) {
@@ -98,7 +98,7 @@ k_nodes(const FieldDev *__restrict__ fields, int nf, uint64_t base, uint64_t bri
     const uint64_t slot = uint64_t(b) * F.bcap;
     uint64_t run = 0;  // maxima | saddles << 16 | paths << 32 of earlier rounds
     uint32_t asum = 0;
-    uint32_t tmp[kMaxComp];
+    uint32_t tmp[CompBound<KD>::value];
     for (uint32_t chunk = 0; chunk < nrec; chunk += 32) {
         const uint32_t r = chunk + uint32_t(lane);
         uint32_t sid = 0;
@@ -109,14 +109,14 @@ k_nodes(const FieldDev *__restrict__ fields, int nf, uint64_t base, uint64_t bri
             sid = F.rec_sid[slot + r];
             info = F.rec_info[slot + r];
             val = F.rec_val[slot + r];
-            const uint64_t b0 = info >> 56;
+            const uint64_t b0 = uint64_t(rec_b0<KD>(info));
             mine = b0 == 0 ? 1ull : ((1ull << 16) | (b0 << 32));
         }
         uint64_t tot;
         const uint64_t pos = run + warp_excl_scan_u64(mine, &tot);
         run += tot;
         if (r >= nrec) continue;
-        const uint64_t b0 = info >> 56;
+        const uint64_t b0 = uint64_t(rec_b0<KD>(info));
         const uint64_t lm = pos & 0xffffu, ls = (pos >> 16) & 0xffffu, lp = pos >> 32;
         if (b0 == 0) {
             const uint64_t q = m_off + lm;
@@ -195,7 +195,8 @@ cudaError_t launch_nodes_d(int kd, const FieldDev *fields, int nf, uint64_t base
 {
     if (bricks == 0) return cudaSuccess;
     const dim3 grid = dim3(static_cast<unsigned>((bricks + kEmitThreads / 32 - 1) / (kEmitThreads / 32)));
-    if (kd == 4) k_nodes<4><<<grid, kEmitThreads, 0, st>>>(fields, nf, base, bricks);
+    if (kd == 5) k_nodes<5><<<grid, kEmitThreads, 0, st>>>(fields, nf, base, bricks);
+    else if (kd == 4) k_nodes<4><<<grid, kEmitThreads, 0, st>>>(fields, nf, base, bricks);
     else k_nodes<3><<<grid, kEmitThreads, 0, st>>>(fields, nf, base, bricks);
     return cudaGetLastError();
 }

@@ -30,14 +30,59 @@
 // plane per brick, so brick b = plane b / nyb, row block b % nyb.
 #pragma once
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace eg {
 
-constexpr int kMaxDim = 4;
+constexpr int kMaxDim = 5;
 constexpr int kFlatBrick = 1024;
 constexpr int kMaxBrick = 4096;  // largest brick of any layout (slot capacity bound)
-constexpr int kMaxComp = 10;     // max upper-link components (4D link graph independence number)
+
+// Most upper-link components a vertex can have: the independence number of
+// the link graph (3 in 2D, 6 in 3D, 10 in 4D, 20 in 5D).
+template <int KD>
+struct CompBound {
+    static constexpr int value = KD == 5 ? 20 : 10;
+};
+
+// Record info word of a critical vertex (0 for a maximum).  Kernel
+// dimensions up to 4: beta0+ in bits 56..59 and the neighbour slot of each
+// component's representative as 5-bit fields from bit 0.  5D (62 slots, up to
+// 20 components): bit k set iff slot k is a representative; beta0+ is the
+// number of set bits.
+template <int KD>
+__device__ __forceinline__ int rec_b0(uint64_t info)
+{
+    if constexpr (KD == 5) return __popcll(info);
+    else return int(info >> 56);
+}
+
+// The representatives' slots of a saddle record in ascending order (slot
+// order is index order); returns their number.
+template <int KD>
+__device__ __forceinline__ int rec_slots(uint64_t info, int (&k)[CompBound<KD>::value])
+{
+    constexpr int kCap = CompBound<KD>::value;
+    if constexpr (KD == 5) {
+        int n = 0;
+        for (uint64_t m = info; m && n < kCap; m &= m - 1) k[n++] = __ffsll((long long)m) - 1;
+        return n;
+    } else {
+        int b0 = int((info >> 56) & 0xfu);
+        if (b0 > kCap) b0 = kCap;
+        for (int c = 0; c < b0; c++) {
+            const int v = int((info >> (5 * c)) & 31u);
+            int j = c;
+            while (j > 0 && k[j - 1] > v) {
+                k[j] = k[j - 1];
+                j--;
+            }
+            k[j] = v;
+        }
+        return b0;
+    }
+}
 
 // device status word bits (reported by eg_get_graph)
 enum : uint32_t {
@@ -210,6 +255,7 @@ template <int D>
 struct Nbr {
     static constexpr int H = (1 << D) - 1;
     static constexpr int K = 2 * H;
+    using Mask = typename std::conditional<(K > 32), uint64_t, uint32_t>::type;  // one bit per slot
     __host__ __device__ static constexpr bool neg(int k) { return k < H; }
     __host__ __device__ static constexpr uint32_t pat(int k) { return k < H ? uint32_t(H - k) : uint32_t(k - H + 1); }
     // rank in index order, centre = H
@@ -219,11 +265,11 @@ struct Nbr {
         return a != b && (neg(a) == neg(b) ? ((pat(a) & pat(b)) == pat(a) || (pat(a) & pat(b)) == pat(b))
                                            : ((pat(a) & pat(b)) == 0u));
     }
-    __host__ __device__ static constexpr uint32_t adj_mask(int a)
+    __host__ __device__ static constexpr Mask adj_mask(int a)
     {
-        uint32_t m = 0;
+        Mask m = 0;
         for (int b = 0; b < K; b++)
-            if (linked(a, b)) m |= 1u << b;
+            if (linked(a, b)) m |= Mask(1) << b;
         return m;
     }
 };
@@ -248,15 +294,19 @@ __device__ __forceinline__ uint32_t slot_vertex(uint32_t v, int k, const uint32_
     return k < NB::H ? v - o : v + o;
 }
 
+__device__ __forceinline__ int lowest_bit(uint32_t m) { return __ffs(m) - 1; }
+__device__ __forceinline__ int lowest_bit(uint64_t m) { return __ffsll((long long)m) - 1; }
+
 // Connected component of `seed` inside `upper` over the link edges (bitmask
 // flood fill; each member is expanded once).
-__device__ __forceinline__ uint32_t link_flood(uint32_t seed, uint32_t upper, const uint32_t *s_adj)
+template <typename M>
+__device__ __forceinline__ M link_flood(M seed, M upper, const M *s_adj)
 {
-    uint32_t comp = seed, frontier = seed;
+    M comp = seed, frontier = seed;
     while (frontier) {
-        const int k = __ffs(frontier) - 1;
+        const int k = lowest_bit(frontier);
         frontier &= frontier - 1;
-        const uint32_t nb = s_adj[k] & upper & ~comp;
+        const M nb = s_adj[k] & upper & ~comp;
         comp |= nb;
         frontier |= nb;
     }

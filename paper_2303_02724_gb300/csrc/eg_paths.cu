@@ -22,23 +22,6 @@ namespace eg {
 constexpr int kPathThreads = 256;
 constexpr int kScanPathThreads = 1024;
 
-// The b0 component slots of a saddle record, ascending.
-__device__ __forceinline__ int sorted_slots(uint64_t info, int (&k)[kMaxComp])
-{
-    int b0 = int((info >> 56) & 0xfu);
-    if (b0 > kMaxComp) b0 = kMaxComp;
-    for (int c = 0; c < b0; c++) {
-        const int v = int((info >> (5 * c)) & 31u);
-        int j = c;
-        while (j > 0 && k[j - 1] > v) {
-            k[j] = k[j - 1];
-            j--;
-        }
-        k[j] = v;
-    }
-    return b0;
-}
-
 // Gradient steps from r to its maximum (bounded: a path has fewer than N steps).
 __device__ __forceinline__ uint32_t gradient_steps(const uint32_t *lab, uint32_t r, uint32_t N, uint32_t *err)
 {
@@ -94,14 +77,14 @@ k_path_len(const FieldDev *__restrict__ fields, int nf, uint64_t base, uint64_t 
     for (uint32_t chunk = 0; chunk < nrec; chunk += 32) {
         const uint32_t r = chunk + uint32_t(lane);
         const uint64_t info = r < nrec ? F.rec_info[slot + r] : 0ull;
-        const uint64_t b0 = info >> 56;
+        const uint64_t b0 = uint64_t(rec_b0<KD>(info));
         uint64_t tot;
         const uint64_t lp = prun + path_warp_scan(b0, &tot);
         prun += tot;
         if (b0 == 0) continue;
         const uint32_t sid = F.rec_sid[slot + r];
-        int k[kMaxComp];
-        const int nc = sorted_slots(info, k);
+        int k[CompBound<KD>::value];
+        const int nc = rec_slots<KD>(info, k);
         for (int q = 0; q < nc; q++) {
             const uint64_t len = 2 + gradient_steps(F.lab, slot_vertex<KD>(sid, k[q], s), F.N, F.err);
             const uint64_t p = p_off + lp + uint64_t(q);
@@ -174,7 +157,7 @@ k_path_write(const FieldDev *__restrict__ fields, int nf, uint64_t base, uint64_
     for (uint32_t chunk = 0; chunk < nrec; chunk += 32) {
         const uint32_t r = chunk + uint32_t(lane);
         const uint64_t info = r < nrec ? F.rec_info[slot + r] : 0ull;
-        const uint64_t b0 = info >> 56;
+        const uint64_t b0 = uint64_t(rec_b0<KD>(info));
         // this saddle's paths and their total length (lengths from k_path_len)
         uint64_t L = 0;
         const bool mine = b0 != 0 && p_off + prun < capP;
@@ -188,8 +171,8 @@ k_path_write(const FieldDev *__restrict__ fields, int nf, uint64_t base, uint64_
         vrun += tot;
         if (b0 == 0) continue;
         const uint32_t sid = F.rec_sid[slot + r];
-        int k[kMaxComp];
-        const int nc = sorted_slots(info, k);
+        int k[CompBound<KD>::value];
+        const int nc = rec_slots<KD>(info, k);
         uint64_t at = lv;
         for (int q = 0; q < nc; q++) {
             const uint64_t p = p_off + lp + uint64_t(q);
@@ -219,7 +202,8 @@ cudaError_t launch_path_len(int kd, const FieldDev *fields, int nf, uint64_t bas
 {
     if (bricks == 0) return cudaSuccess;
     const dim3 grid = dim3(static_cast<unsigned>((bricks + kPathThreads / 32 - 1) / (kPathThreads / 32)));
-    if (kd == 4) k_path_len<4><<<grid, kPathThreads, 0, st>>>(fields, nf, base, bricks);
+    if (kd == 5) k_path_len<5><<<grid, kPathThreads, 0, st>>>(fields, nf, base, bricks);
+    else if (kd == 4) k_path_len<4><<<grid, kPathThreads, 0, st>>>(fields, nf, base, bricks);
     else k_path_len<3><<<grid, kPathThreads, 0, st>>>(fields, nf, base, bricks);
     return cudaGetLastError();
 }
@@ -236,7 +220,8 @@ cudaError_t launch_path_write(int kd, const FieldDev *fields, int nf, uint64_t b
 {
     if (bricks == 0) return cudaSuccess;
     const dim3 grid = dim3(static_cast<unsigned>((bricks + kPathThreads / 32 - 1) / (kPathThreads / 32)));
-    if (kd == 4) k_path_write<4><<<grid, kPathThreads, 0, st>>>(fields, nf, base, bricks);
+    if (kd == 5) k_path_write<5><<<grid, kPathThreads, 0, st>>>(fields, nf, base, bricks);
+    else if (kd == 4) k_path_write<4><<<grid, kPathThreads, 0, st>>>(fields, nf, base, bricks);
     else k_path_write<3><<<grid, kPathThreads, 0, st>>>(fields, nf, base, bricks);
     return cudaGetLastError();
 }

@@ -72,10 +72,14 @@ eg_status scratch_address(unsigned char **out)
 extern "C" eg_status eg_labels_static(const float *field, int d, const int64_t *extents, uint32_t flags,
                                       uint32_t *labels, void *stream)
 {
-    if (!field || !labels || !extents || d < 1 || d > kMaxDim) return EG_ERR_ARG;
+    if (!field || !labels || !extents || d < 1 || d > 4) return EG_ERR_ARG;
     if (flags & ~uint32_t(EG_FLAG_MINIMUM_GRAPH)) return EG_ERR_ARG;
     uint64_t N = 1;
-    uint32_t n[kMaxDim] = {1, 1, 1, 1}, s[kMaxDim] = {0, 0, 0, 0};
+    uint32_t n[kMaxDim], s[kMaxDim];
+    for (int i = 0; i < kMaxDim; i++) {
+        n[i] = 1;
+        s[i] = 0;
+    }
     for (int i = 0; i < d; i++) {
         if (extents[i] < 1 || extents[i] > int64_t(kStaticN)) return EG_ERR_ARG;
         s[i] = uint32_t(N);

@@ -16,7 +16,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libeg.so")
-MAX_DIM = 4
+MAX_DIM = 5
 
 EG_OK, EG_ERR_ARG, EG_ERR_NAN, EG_ERR_OOM, EG_ERR_CUDA = 0, 1, 2, 3, 4
 EG_ERR_NOT_CONVERGED, EG_ERR_TIMEOUT, EG_ERR_BUSY, EG_ERR_INTERNAL = 5, 6, 7, 8

@@ -63,7 +63,8 @@ def bundle_vectorised(saddles, sad_val, row_ptr, col, minimum=False):
     return keep
 
 
-@pytest.mark.parametrize("shape", [(12, 10), (64, 48), (6, 5, 4), (20, 18, 16), (3, 3, 3, 3), (8, 7, 6, 5)],
+@pytest.mark.parametrize("shape", [(12, 10), (64, 48), (6, 5, 4), (20, 18, 16), (3, 3, 3, 3), (8, 7, 6, 5),
+                                   (4, 4, 3, 3, 3)],
                          ids=lambda s: "x".join(map(str, s)))
 @pytest.mark.parametrize("kind", ["normal", "ties"])
 @pytest.mark.parametrize("minimum", [False, True])

@@ -54,7 +54,8 @@ def run_gpu(h, values):
 
 
 SMALL = [(1,), (2,), (7,), (1, 1), (3, 1), (1, 5), (2, 2), (5, 3), (8, 8), (17, 9), (1, 1, 1), (2, 3, 4),
-         (4, 4, 4), (5, 1, 3), (9, 7, 5), (3, 3, 3, 3), (2, 1, 3, 2), (5, 4, 3, 2), (1, 1, 1, 7)]
+         (4, 4, 4), (5, 1, 3), (9, 7, 5), (3, 3, 3, 3), (2, 1, 3, 2), (5, 4, 3, 2), (1, 1, 1, 7),
+         (2, 2, 2, 2, 2), (3, 3, 3, 3, 3), (5, 4, 3, 2, 2), (1, 1, 1, 1, 9), (7, 1, 3, 1, 2), (9, 8, 7, 6, 5)]
 
 
 @pytest.mark.parametrize("shape", SMALL, ids=lambda s: "x".join(map(str, s)))
@@ -65,7 +66,7 @@ def test_small_shapes(handle, shape, kind):
     assert_same(run_gpu(handle, f.values), oracle.compute(f.values))
 
 
-@pytest.mark.parametrize("shape", [(8, 8), (4, 4, 4), (3, 3, 3, 3), (33, 17, 5), (300,)])
+@pytest.mark.parametrize("shape", [(8, 8), (4, 4, 4), (3, 3, 3, 3), (33, 17, 5), (300,), (4, 3, 3, 3, 2)])
 def test_minimum_graph(handle_min, shape):
     f = F.white_noise(shape, 77)
     assert_same(run_gpu(handle_min, f.values), oracle.compute(f.values, minimum=True))
@@ -243,3 +244,16 @@ def test_batch_graph_replay_with_new_fields():
                 o = oracle.compute(x.values)
                 assert_same(g, o)
                 assert_same(gd, o)
+
+
+@pytest.mark.parametrize("d", [2, 3, 4, 5])
+def test_most_components(handle, handle_min, d):
+    """A vertex whose upper link is a largest independent set of its link:
+    3, 6, 10 and 20 components in 2D..5D (the record formats' limits)."""
+    from tests.test_oracle_pins import many_component_field
+    f = many_component_field(d)
+    gg = run_gpu(handle, f)
+    og = oracle.compute(f)
+    assert_same(gg, og)
+    assert int(og.sad_b0.max()) == {2: 3, 3: 6, 4: 10, 5: 20}[d]
+    assert_same(run_gpu(handle_min, -f), oracle.compute(-f, minimum=True))

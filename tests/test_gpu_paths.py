@@ -52,7 +52,7 @@ def check(h, values, minimum=False):
 
 
 SHAPES = [(7,), (33,), (5, 3), (17, 9), (64, 48), (4, 4, 4), (9, 7, 5), (40, 36, 32), (3, 3, 3, 3),
-          (6, 5, 4, 3), (12, 1500)]
+          (6, 5, 4, 3), (12, 1500), (3, 3, 3, 3, 3), (6, 5, 4, 3, 2)]
 
 
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))

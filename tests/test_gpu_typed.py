@@ -52,7 +52,8 @@ def assert_same(gg, og, labels=True):
         assert np.array_equal(gg.labels, og.label), "labels"
 
 
-EDGE_SHAPES = [(9,), (8, 8), (17, 9), (4, 4, 4), (9, 7, 5), (3, 3, 3, 3), (5, 4, 3, 2), (1, 1, 1, 7)]
+EDGE_SHAPES = [(9,), (8, 8), (17, 9), (4, 4, 4), (9, 7, 5), (3, 3, 3, 3), (5, 4, 3, 2), (1, 1, 1, 7),
+               (3, 3, 3, 3, 3)]
 
 
 @pytest.mark.parametrize("dtype", TYPES)

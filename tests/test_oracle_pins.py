@@ -110,7 +110,7 @@ def test_alg1_cases():
 # ------------------------------------------------------------ brute force ---
 
 SHAPES = [(8, 8), (4, 4, 4), (3, 3, 3, 3), (10,), (5, 3), (1, 7), (2, 1, 3), (3, 2, 2, 2),
-          (2, 2), (1,), (2,), (1, 1, 1), (5, 4, 3), (6, 1)]
+          (2, 2), (1,), (2,), (1, 1, 1), (5, 4, 3), (6, 1), (2, 2, 2, 2, 2), (3, 3, 2, 3, 2)]
 
 
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
@@ -438,3 +438,69 @@ def test_typed_bundling_uses_exact_values():
             kept = {int(s) for s, k in zip(g.saddles.tolist(), keep.tolist()) if k}
             for ss in pairs.values():
                 assert max(ss, key=lambda s: rank[s]) in kept
+
+
+# ------------------------------------------------------------------- 5D ----
+
+def link_independent_set(d):
+    """Pairwise non-adjacent neighbour offsets of the origin: every positive
+    offset whose axis pattern has a elements and every negative one with b
+    elements, a + b > d (so a positive and a negative pattern always share
+    an axis: not adjacent; two patterns of one size are incomparable: not
+    adjacent), sizes chosen to maximise the count.  The largest such sets
+    have 3, 6, 10 and 20 members in 2D..5D."""
+    from itertools import combinations
+    from math import comb
+    a, b = max(((a, b) for a in range(1, d + 1) for b in range(1, d + 1) if a + b > d),
+               key=lambda ab: comb(d, ab[0]) + comb(d, ab[1]))
+    out = []
+    for size, sign in [(a, 1), (b, -1)]:
+        for axes in combinations(range(d), size):
+            out.append(tuple(sign if i in axes else 0 for i in range(d)))
+    return out
+
+
+def many_component_field(d):
+    """3^d grid: the centre low, the offsets of link_independent_set high,
+    every other vertex lower still, so the centre's upper link is that
+    independent set: one component per member."""
+    ind = set(link_independent_set(d))
+    f = np.full((3,) * d, -20.0, np.float32)
+    for o in oracle.neighbour_offsets(d):
+        idx = tuple(1 + int(x) for x in reversed(o))  # numpy axes are reversed
+        f[idx] = 10.0 if tuple(int(x) for x in o) in ind else -10.0
+    f[(1,) * d] = 0.0
+    return f
+
+
+def test_independent_sets_are_largest():
+    """The constructed sets are independent under Algorithm 1, and (where
+    networkx is available) no larger independent set exists."""
+    for d in [2, 3, 4, 5]:
+        ind = link_independent_set(d)
+        assert all(not alg1_adjacent(p, q) for p in ind for q in ind)
+    nx = pytest.importorskip("networkx")
+    for d in [2, 3, 4, 5]:
+        off = [tuple(int(x) for x in o) for o in oracle.neighbour_offsets(d)]
+        comp = nx.Graph()
+        comp.add_nodes_from(range(len(off)))
+        comp.add_edges_from((i, j) for i in range(len(off)) for j in range(i + 1, len(off))
+                            if not alg1_adjacent(off[i], off[j]))
+        assert max(len(c) for c in nx.find_cliques(comp)) == len(link_independent_set(d))
+
+
+@pytest.mark.parametrize("d,count", [(2, 3), (3, 6), (4, 10), (5, 20)])
+def test_most_components(d, count):
+    """The independence number of the link graph bounds beta0+ (3, 6, 10 and
+    20 in 2D..5D); a field whose centre's upper link is a largest
+    independent set reaches it, and the brute force agrees."""
+    f = many_component_field(d)
+    ext = (3,) * d
+    centre = sum(3 ** i for i in range(d))
+    g = oracle.compute(f, extents=ext)
+    assert len(link_independent_set(d)) == count
+    assert int(g.beta0p[centre]) == count
+    b = brute_graph(f, ext)
+    assert int(b["beta"][centre]) == count
+    assert g.label.tolist() == b["label"].tolist()
+    assert g.arcs() == b["arcs"]
