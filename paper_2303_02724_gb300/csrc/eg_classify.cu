@@ -50,11 +50,11 @@ __device__ __forceinline__ typename TypeKey<DT>::B load_bits(const FieldDev &F, 
 // the keys and mirrors both rules.
 template <int D, uint32_t DT>
 __device__ __forceinline__ uint32_t classify_vertex(const FieldDev &F, const uint32_t (&s)[kMaxDim],
-                                                    uint32_t v, const typename Nbr<D>::Mask *s_adj, bool minimum,
-                                                    int &b0, uint64_t &codes, bool &nan)
+                                                    uint32_t v, bool minimum, int &b0, uint64_t &codes, bool &nan)
 {
     using NB = Nbr<D>;
-    using M = typename NB::Mask;
+    using PL = PatternLink<D>;
+    using M = typename PL::Mask;  // the upper link in the pattern layout
     using TK = TypeKey<DT>;
     using B = typename TK::B;
     constexpr int K = NB::K;
@@ -76,7 +76,16 @@ __device__ __forceinline__ uint32_t classify_vertex(const FieldDev &F, const uin
     const B bv = load_bits<DT>(F, v);
     nan = TK::nan(bv);
     const B kv = TK::key(bv) ^ flip;
-    B key[K];
+    // key of the neighbour in slot k (in bounds; reloaded through the cache
+    // for saddles rather than kept in registers for every vertex)
+    auto nkey = [&](int k) {
+        const uint32_t p = NB::pat(k);
+        uint32_t o = 0;
+#pragma unroll
+        for (int i = 0; i < D; i++)
+            if (p & (1u << i)) o += s[i];
+        return TK::key(load_bits<DT>(F, NB::neg(k) ? v - o : v + o)) ^ flip;
+    };
     M upper = 0;
     uint32_t asc = v;
     B best = 0;
@@ -98,9 +107,8 @@ __device__ __forceinline__ uint32_t classify_vertex(const FieldDev &F, const uin
             // ties: higher iff the slot lies above the centre in the order
             up = (NB::neg(k) == minimum) ? kw >= kv : kw > kv;
         }
-        key[k] = kw;
         if (up) {
-            upper |= M(1) << k;
+            upper |= M(1) << PL::bit(k);
             // the highest upper neighbour; among equal keys the later slot
             // (maximum graph) or the earlier one (minimum graph)
             if (bestk < 0 || (minimum ? kw > best : kw >= best)) {
@@ -115,21 +123,24 @@ __device__ __forceinline__ uint32_t classify_vertex(const FieldDev &F, const uin
         b0 = 0;
         return v;
     }
-    const M comp = link_flood(M(1) << bestk, upper, s_adj);
+    const M comp = PL::component(M(1) << PL::bit(bestk), upper);
     b0 = 1;
     if (comp == upper) return asc;
     codes = D == 5 ? (1ull << bestk) : uint64_t(bestk);
     M left = upper & ~comp;
     while (left) {
-        const M c2 = link_flood(left & (~left + M(1)), upper, s_adj);
+        const M c2 = PL::component(left & (~left + M(1)), upper);
         left &= ~c2;
         B rb = 0;
         int rk = -1;
 #pragma unroll
         for (int k = 0; k < K; k++)
-            if (((c2 >> k) & 1u) && (rk < 0 || (minimum ? key[k] > rb : key[k] >= rb))) {
-                rb = key[k];
-                rk = k;
+            if ((c2 >> PL::bit(k)) & 1u) {
+                const B kk = nkey(k);
+                if (rk < 0 || (minimum ? kk > rb : kk >= rb)) {
+                    rb = kk;
+                    rk = k;
+                }
             }
         codes |= D == 5 ? (1ull << rk) : (uint64_t(rk) << (5 * b0));
         b0++;
@@ -141,12 +152,9 @@ __device__ __forceinline__ uint32_t classify_vertex(const FieldDev &F, const uin
 template <int D, uint32_t DT>
 __device__ __forceinline__ void classify_brick(const FieldDev &F, uint32_t b)
 {
-    using NB = Nbr<D>;
-    __shared__ typename NB::Mask s_adj[NB::K];
     __shared__ uint32_t s_scan[33];
     __shared__ unsigned s_cnt[3];
     const int tid = threadIdx.x;
-    if (tid < NB::K) s_adj[tid] = NB::adj_mask(tid);
     if (tid < 3) s_cnt[tid] = 0;
     uint32_t s[kMaxDim];
 #pragma unroll
@@ -156,31 +164,43 @@ __device__ __forceinline__ void classify_brick(const FieldDev &F, uint32_t b)
     const uint64_t slot = uint64_t(b) * F.bcap;
     __syncthreads();
 
-    uint32_t running = 0, nm = 0, ns = 0, np = 0;
+    // classify this thread's vertices first (no barrier in between, so warps
+    // run ahead of one another while their loads are in flight), then place
+    // the records with one block scan per round
+    int b0s[kVpt];
+    uint64_t codess[kVpt];
     bool anynan = false;
 #pragma unroll 1
     for (int i = 0; i < kVpt; i++) {
         const uint64_t v64 = v0 + uint64_t(i) * kClassifyThreads + tid;
-        const bool valid = v64 < F.N;
-        int b0 = 1;
-        uint64_t codes = 0;
-        float fv = 0.f;
-        if (valid) {
+        b0s[i] = 1;
+        codess[i] = 0;
+        if (v64 < F.N) {
             bool nan;
+            int b0;
+            uint64_t codes;
             const uint32_t v = uint32_t(v64);
-            const uint32_t asc = classify_vertex<D, DT>(F, s, v, s_adj, minimum, b0, codes, nan);
+            F.lab[v] = classify_vertex<D, DT>(F, s, v, minimum, b0, codes, nan);
             anynan |= nan;
-            F.lab[v] = asc;
-            // (other element types get their value copies from the field
-            // itself once the graph is assembled)
-            if constexpr (DT == kF32) fv = F.f[v];
+            b0s[i] = b0;
+            codess[i] = codes;
         }
-        const bool crit = valid && b0 != 1;
+    }
+    uint32_t running = 0, nm = 0, ns = 0, np = 0;
+#pragma unroll
+    for (int i = 0; i < kVpt; i++) {
+        const uint64_t v64 = v0 + uint64_t(i) * kClassifyThreads + tid;
+        const int b0 = b0s[i];
+        const bool crit = v64 < F.N && b0 != 1;
         uint32_t tot;
         const uint32_t pos = block_excl_scan(crit ? 1u : 0u, s_scan, &tot);
         if (crit) {
             F.rec_sid[slot + running + pos] = uint32_t(v64);
-            F.rec_info[slot + running + pos] = D == 5 ? codes : ((uint64_t(b0) << 56) | codes);
+            F.rec_info[slot + running + pos] = D == 5 ? codess[i] : ((uint64_t(b0) << 56) | codess[i]);
+            // (other element types get their value copies from the field
+            // itself once the graph is assembled)
+            float fv = 0.f;
+            if constexpr (DT == kF32) fv = F.f[v64];
             F.rec_val[slot + running + pos] = fv;
             if (b0 == 0) nm++;
             else {

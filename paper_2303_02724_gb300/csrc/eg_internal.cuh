@@ -314,6 +314,56 @@ __device__ __forceinline__ M link_flood(M seed, M upper, const M *s_adj)
 }
 
 // ---------------------------------------------------------------------------
+// Link components by axis patterns.  Pattern layout of the link of a D-dim
+// vertex: the positive neighbour with axis pattern p (p = 1 .. 2^D - 1) at bit
+// p, the negative one at bit 2^D + p.  Two link vertices are joined
+// (Algorithm 1 on their difference) iff they have the same sign and
+// comparable patterns, or opposite signs and disjoint patterns.  So the link
+// neighbours of a set are the supersets of its patterns in the same half and
+// the subsets of its patterns and of their complements, where reversing the
+// 2^(D+1) bits maps pattern p of one half to pattern ~p of the other: one
+// expansion step is a superset closure and a subset closure over the D
+// pattern bits of both halves at once, register-only.
+// ---------------------------------------------------------------------------
+template <int D>
+struct PatternLink {
+    static constexpr int W = 1 << D;  // bits per half
+    using Mask = typename std::conditional<(2 * W > 32), uint64_t, uint32_t>::type;
+    // bit of neighbour slot k (slot order of Nbr<D>)
+    __host__ __device__ static constexpr int bit(int k) { return k < W - 1 ? W + (W - 1 - k) : k - (W - 1) + 1; }
+    // positions whose pattern lacks axis bit i, in both halves
+    __host__ __device__ static constexpr Mask lacks(int i)
+    {
+        Mask m = 0;
+        for (int j = 0; j < 2 * W; j++)
+            if (!((j & (W - 1)) >> i & 1)) m |= Mask(1) << j;
+        return m;
+    }
+    static __device__ __forceinline__ Mask reverse(Mask x)
+    {
+        if constexpr (sizeof(Mask) == 8) return __brevll(x);
+        else if constexpr (2 * W == 32) return __brev(x);
+        else return __brev(x) >> (32 - 2 * W);
+    }
+    // connected component of s inside u (s a subset of u); the set only
+    // grows, so the loop ends within 2W steps
+    static __device__ __forceinline__ Mask component(Mask s, Mask u)
+    {
+        while (true) {
+            Mask up = s, dn = s | reverse(s);
+#pragma unroll
+            for (int i = 0; i < D; i++) {
+                up |= (up & lacks(i)) << (1 << i);
+                dn |= (dn >> (1 << i)) & lacks(i);
+            }
+            const Mask n = (up | dn) & u;
+            if (n == s) return s;
+            s = n;
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
 // Decoupled look-back (single-pass prefix over work items taken in ticket
 // order).  Status word: bits 63..62 = 0 empty, 1 aggregate, 2 inclusive
 // prefix; bits 61..0 value.  A warp inspects 32 predecessors per step; every
