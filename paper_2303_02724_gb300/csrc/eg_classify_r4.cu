@@ -127,7 +127,7 @@ __device__ __forceinline__ int r4_top(const float (&nb)[30], uint32_t mask)
 }  // namespace
 
 template <bool MIN>
-__global__ void __launch_bounds__(kR4Threads)
+__global__ void __launch_bounds__(kR4Threads, 3)
 k_classify_r4(const FieldDev *__restrict__ fields, int nf)
 {
     __shared__ uint32_t s_scan[33];

@@ -23,11 +23,20 @@ template <int KD>
 __device__ __forceinline__ int saddle_ends(const uint32_t *lab, const uint32_t (&s)[kMaxDim], uint32_t sid,
                                            uint64_t info, uint32_t (&t)[CompBound<KD>::value])
 {
-    int ks[CompBound<KD>::value];
-    const int b0 = rec_slots<KD>(info, ks);
+    // the representatives in record order (the ends are sorted below)
+    constexpr int kCap = CompBound<KD>::value;
+    const int b0 = rec_b0<KD>(info);
+    uint64_t rest = info;
     int n = 0;
-    for (int c = 0; c < b0; c++) {
-        const uint32_t m = lab[slot_vertex<KD>(sid, ks[c], s)];
+    for (int c = 0; c < b0 && c < kCap; c++) {
+        int k;
+        if constexpr (KD == 5) {
+            k = __ffsll((long long)rest) - 1;
+            rest &= rest - 1;
+        } else {
+            k = int((info >> (5 * c)) & 31u);
+        }
+        const uint32_t m = lab[slot_vertex<KD>(sid, k, s)];
         int j = n;
         bool dup = false;
         while (j > 0 && t[j - 1] >= m) {
