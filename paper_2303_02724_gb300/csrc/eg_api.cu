@@ -270,8 +270,9 @@ Layout make_layout(const Shape &sh, int sm_count, const eg_config &cfg, uint32_t
     // the plane-marching classifier reads float32 (the field, or the float32
     // image of a narrow integer field); other types take the flat classifier
     const bool f32_values = dtype == kF32 || dtype_narrow(dtype);
-    if (L.kd == 3 && n0 <= 1024 && f32_values) {
+    if (L.kd == 3 && n0 <= kZmMaxRow && f32_values) {
         // one thread per 8 consecutive vertices of a row, 256 threads per CTA
+        // (rows of more than 1024 vertices: one row per brick)
         const uint32_t txn = (n0 + 7) / 8;
         uint32_t ty = 256 / txn;
         if (cfg.classify_rows >= 1) ty = std::min<uint32_t>(ty, uint32_t(cfg.classify_rows));
@@ -635,8 +636,10 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
     // group fields by classifier kind so every launch covers a contiguous slice
     auto cdt = [&](int i) { return dtype_narrow(jobs[i].dtype) ? uint32_t(kF32) : jobs[i].dtype; };
     auto key = [&](int i) {
-        return int(cdt(i)) * 64 + (lay[i].zm ? 0 : (lay[i].r4 ? 1 : 2)) * 16 + lay[i].kd * 2 +
-               ((jobs[i].flags & kFlagMinimum) ? 1 : 0);
+        // (the plane-marching kernel's rows longer than 1024 vertices launch
+        // on their own: their ring needs more shared memory per CTA)
+        const int kind = lay[i].zm ? (jobs[i].sh.n[0] > 1024 ? 3 : 0) : (lay[i].r4 ? 1 : 2);
+        return int(cdt(i)) * 64 + kind * 16 + lay[i].kd * 2 + ((jobs[i].flags & kFlagMinimum) ? 1 : 0);
     };
     std::vector<int> order(nf);
     for (int i = 0; i < nf; i++) order[i] = i;

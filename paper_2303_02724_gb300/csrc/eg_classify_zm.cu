@@ -1,4 +1,4 @@
-// Steps (a) + (c) for 2D and 3D fields whose rows hold at most 1024 vertices:
+// Steps (a) + (c) for 2D and 3D fields whose rows hold at most 2048 vertices:
 // plane-marching classification (Sec. 3.3, Table 1; 2D runs as 3D, n2 = 1).
 //
 // A CTA owns `ty` whole rows of the grid (a row block) and marches along the

@@ -27,8 +27,10 @@ constexpr int kR4CtaThreads = 256;
 cudaError_t launch_widen(uint32_t dtype, const FieldDev *field, uint64_t n, int sm_count, cudaStream_t st);
 
 // Steps (a)+(c), plane-marching kernel for 2D/3D fields with rows of at most
-// 1024 vertices.  lut: the 2-bit class of every 14-bit upper mask (1024 words),
-// then, as 16-bit words, the component holding each mask's lowest set bit.
+// kZmMaxRow vertices.
+// lut: the 2-bit class of every 14-bit upper mask (1024 words), then, as
+// 16-bit words, the component holding each mask's lowest set bit.
+constexpr uint32_t kZmMaxRow = 2048;
 size_t zm_smem_bytes(uint32_t n0, uint32_t ty);
 // Persistent: grid = min(total_items, sm_count * ctas_per_sm) CTAs take work
 // items from *ticket (zeroed before the launch).

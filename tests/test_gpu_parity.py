@@ -89,13 +89,16 @@ def test_multi_brick(handle, case):
     assert_same(run_gpu(handle, f.values), oracle.compute(f.values))
 
 
-@pytest.mark.parametrize("case", ["flat_2d_wide", "flat_3d_wide", "long_1d", "tall_2d", "thin_3d"])
+@pytest.mark.parametrize("case", ["flat_2d_wide", "flat_3d_wide", "wide_2d", "wide_3d", "long_1d", "tall_2d",
+                                  "thin_3d"])
 def test_layouts(handle, case):
-    """Rows longer than 1024 vertices take the flat-brick classifier; others the
+    """Rows longer than 2048 vertices take the flat-brick classifier; others the
     plane-marching one, including degenerate row/plane counts."""
     f = {
-        "flat_2d_wide": lambda: F.config_2d_256(side=1500),
-        "flat_3d_wide": lambda: F.white_noise((1100, 5, 3), 4),
+        "flat_2d_wide": lambda: F.config_2d_256(side=2500),
+        "flat_3d_wide": lambda: F.white_noise((2100, 5, 3), 4),
+        "wide_2d": lambda: F.config_2d_256(side=1500),
+        "wide_3d": lambda: F.white_noise((1100, 5, 3), 4),
         "long_1d": lambda: F.white_noise((5000,), 6),
         "tall_2d": lambda: F.white_noise((3, 2000), 7),
         "thin_3d": lambda: F.integer_ties((7, 1, 40), 2, 3),
@@ -103,13 +106,14 @@ def test_layouts(handle, case):
     assert_same(run_gpu(handle, f.values), oracle.compute(f.values))
 
 
-@pytest.mark.parametrize("n0", [1, 3, 4, 8, 12, 20, 36, 100, 252, 512, 1020, 1021, 1024, 1025])
+@pytest.mark.parametrize("n0", [1, 3, 4, 8, 12, 20, 36, 100, 252, 512, 1020, 1021, 1024, 1025, 1500, 2044,
+                                2047, 2048, 2049])
 def test_row_lengths(handle, n0):
     """Every row-length regime of the plane-marching classifier: 16-byte rows
     (n0 % 4 == 0, with a half-filled last 8-column group when n0 % 8 == 4),
-    4-byte rows, one vertex per row (126-row bricks), the 1024-vertex limit,
-    and the flat classifier just past it; 13 rows and 7 planes leave partial
-    row blocks and work items."""
+    4-byte rows, one vertex per row (126-row bricks), rows over 1024 vertices
+    (one row per brick), the 2048-vertex limit and the flat classifier just
+    past it; 13 rows and 7 planes leave partial row blocks and work items."""
     f = F.white_noise((7, 13, n0), 1000 + n0)
     assert_same(run_gpu(handle, f.values), oracle.compute(f.values))
 
