@@ -194,18 +194,19 @@ def graph_d2h_bytes(c):
     return 8 * M + 9 * S + 8 * (S + 1) + 4 * A
 
 
-def traffic_from_profiles(kernel, workload):
-    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
-    summary, if it was taken on the kernel's current source (else None)."""
+def traffic_from_profiles(step, workload):
+    """DRAM bytes per launch of `step`'s kernels on `workload` from the
+    committed ncu summary, if it was taken on the kernels' current source
+    (else None)."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
     try:
         from paper_2303_02724_gb300 import _build
-        e = json.load(open(p)).get("kernels", {}).get(kernel, {})
-        if e.get("source_fingerprint") != _build.kernel_fingerprint(e.get("source", "")):
+        e = json.load(open(p)).get("steps", {}).get(step, {}).get(workload)
+        if not e or e.get("source_fingerprint") != _build.kernel_fingerprint(e.get("source", "")):
             return None
-        return e.get("dram_bytes_per_launch", {}).get(workload)
+        return e.get("dram_bytes_per_launch")
     except Exception:
         return None
 
