@@ -26,7 +26,8 @@ def test_bad_arguments_are_status_codes(eg):
         ext = (ctypes.c_int64 * 4)(4, 4, 0, 0)
         t = torch.zeros(16, device="cuda")
         # d out of range, zero extent, NULL field
-        assert lib.eg_compute(h._h, ctypes.c_void_p(t.data_ptr()), 5, ext, None, ctypes.byref(rid)) == eg.EG_ERR_ARG
+        assert lib.eg_compute(h._h, ctypes.c_void_p(t.data_ptr()), 6, ext, None, ctypes.byref(rid)) == eg.EG_ERR_ARG
+        assert lib.eg_compute(h._h, ctypes.c_void_p(t.data_ptr()), 0, ext, None, ctypes.byref(rid)) == eg.EG_ERR_ARG
         assert lib.eg_compute(h._h, ctypes.c_void_p(t.data_ptr()), 3, ext, None, ctypes.byref(rid)) == eg.EG_ERR_ARG
         assert lib.eg_compute(h._h, None, 2, ext, None, ctypes.byref(rid)) == eg.EG_ERR_ARG
         assert lib.eg_release(h._h, 123456) == eg.EG_ERR_ARG
