@@ -504,3 +504,22 @@ def test_most_components(d, count):
     assert int(b["beta"][centre]) == count
     assert g.label.tolist() == b["label"].tolist()
     assert g.arcs() == b["arcs"]
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4, 5])
+def test_link_edges_by_axis_patterns(d):
+    """The link structure the GPU classifiers build on (link components as
+    closures over axis patterns): two neighbour offsets of a vertex are
+    adjacent under Algorithm 1 iff they have the same sign and comparable
+    axis patterns (one a subset of the other), or opposite signs and disjoint
+    patterns."""
+    off = [tuple(int(x) for x in o) for o in oracle.neighbour_offsets(d)]
+    for a in off:
+        for b in off:
+            if a == b:
+                continue
+            pa = {i for i, x in enumerate(a) if x}
+            pb = {i for i, x in enumerate(b) if x}
+            same = (sum(a) > 0) == (sum(b) > 0)
+            rule = (pa <= pb or pb <= pa) if same else not (pa & pb)
+            assert alg1_adjacent(a, b) == rule, (a, b)
