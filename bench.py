@@ -24,6 +24,7 @@ import platform
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -124,8 +125,10 @@ class ClockSampler:
     def __init__(self, device):
         self.device = device
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{device}.csv") \
-            if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/eg_clocks_{os.getpid()}.csv"
+        # raw samples go to $EG_CLOCKS_DIR when set (kept for inspection), else a temporary file
+        out = os.environ.get("EG_CLOCKS_DIR")
+        self.path = os.path.join(out, f"clocks_rank{device}.csv") if out and os.path.isdir(out) \
+            else os.path.join(tempfile.gettempdir(), f"eg_clocks_{os.getpid()}_{device}.csv")
 
     def start(self):
         try:
