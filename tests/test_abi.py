@@ -68,3 +68,19 @@ def test_graph_buffers_views():
     assert b.views(0, 0, 0, 13).labels.size == 13
     with pytest.raises(ValueError):
         b.views(6, 0, 0)
+
+
+def test_bench_byte_accounting():
+    """The roofline's algorithmic bytes: the field in its element type, the
+    labels, the records and the graph (counts of a hand-made result)."""
+    import bench
+    c = dict(n_vertices=1000, n_maxima=10, n_saddles=20, n_paths=45, n_arcs=40)
+    kb = bench.kernel_bytes(c)
+    assert kb["classify"] == 4 * 1000 + 4 * 1000 + 12 * 30
+    assert kb["resolve"] == 8 * 1000
+    assert kb["emit"] == 12 * 30 + 4 * 45 + 8 * 10 + 9 * 20 + 8 * 21 + 4 * 40
+    assert bench.path_bytes(c) == 8 * 1000 + 8 * 10 + 9 * 20 + 8 * 21 + 4 * 40
+    # a uint8 field: 1 byte per value read and per value copy
+    kb8 = bench.kernel_bytes(c, es=1)
+    assert kb8["classify"] == 1000 + 4 * 1000 + 12 * 30
+    assert bench.path_bytes(c, es=1) == 1000 + 4 * 1000 + 5 * 10 + 6 * 20 + 8 * 21 + 4 * 40
