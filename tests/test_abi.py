@@ -68,6 +68,30 @@ def test_graph_buffers_views():
     assert b.views(0, 0, 0, 13).labels.size == 13
     with pytest.raises(ValueError):
         b.views(6, 0, 0)
+    # value copies take the field's element type; buffers of another type do not fit
+    b64 = eg.GraphBuffers(5, 7, 11, dtype=np.uint64)
+    g64 = b64.views(2, 3, 4, dtype=np.uint64)
+    assert g64.max_val.dtype == np.uint64 and g64.sad_val.dtype == np.uint64
+    assert g64.maxima.dtype == np.uint32 and g64.col.dtype == np.uint32
+    assert not b64.fits(2, 3, 4) and not b.fits(2, 3, 4, dtype=np.int8)
+    with pytest.raises(ValueError):
+        b64.views(2, 3, 4)
+
+
+def test_element_type_codes():
+    """The binding's element-type codes follow eg_dtype, and the library
+    reports each type's size (no GPU needed)."""
+    from paper_2303_02724_gb300 import eg
+    lib = eg.load()
+    for dt, code in eg.DTYPES.items():
+        assert lib.eg_dtype_size(code) == dt.itemsize
+        assert eg.dtype_flag(dt) == code << 16
+    assert lib.eg_dtype_size(-1) == 0 and lib.eg_dtype_size(len(eg.DTYPES)) == 0
+    hdr = open(os.path.join(ROOT, "include", "eg.h")).read()
+    names = {"float32": "F32", "float64": "F64", "int8": "I8", "uint8": "U8", "int16": "I16", "uint16": "U16",
+             "int32": "I32", "uint32": "U32", "int64": "I64", "uint64": "U64"}
+    for dt, code in eg.DTYPES.items():
+        assert re.search(rf"EG_DTYPE_{names[dt.name]}\s*=\s*{code}\b", hdr), dt
 
 
 def test_bench_byte_accounting():
