@@ -414,8 +414,9 @@ class Handle:
         return int(self._lib.eg_debug_wait_timeout(self._h, ctypes.c_void_p(_stream_ptr(stream))))
 
     # ------------------------------------------------------------- one shot
-    def graph_of(self, field, labels: bool = True, stream=None) -> Graph:
-        rid = self.compute(field, stream)
+    def graph_of(self, field, labels: bool = True, stream=None, dtype=None) -> Graph:
+        """compute + get_graph + release (dtype as for compute)."""
+        rid = self.compute(field, stream, dtype=dtype)
         try:
             return self.get_graph(rid, labels)
         finally:
