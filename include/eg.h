@@ -285,15 +285,19 @@ EG_API eg_status eg_step_times(eg_handle h, eg_result_id id, float ms[4]);
  * extents as for eg_compute, with N <= EG_STATIC_MAX_VERTICES.  Larger fields
  * are rejected with EG_ERR_ARG before any work is enqueued.
  * Work runs on `stream`; the call returns after it has finished (it reads back
- * a status word), so labels are ready on return.
+ * a status word and synchronises the stream), so labels are ready on return.
+ * A stream that is being captured into a CUDA graph is therefore refused
+ * (EG_ERR_ARG, checked before any work is enqueued).
  * Scratch: a fixed array compiled into the library (about 16 bytes per vertex
  * of EG_STATIC_MAX_VERTICES, ~17 MB) that every GPU loading the library holds
- * until the process exits.  Its device address is looked up on the FIRST call
- * made on each device, with that device current; make that first call before
- * any stream capture begins.  All calls on a device share the one array, and
- * it keeps the last call's contents (the call clears what must start at
- * zero): calls that overlap on the GPU -- from several host threads or on
- * several streams -- race on it and must be serialised by the caller.
+ * until the process exits.  Every call looks up its device address with the
+ * caller's current device (no address is cached, so a device reset leaves
+ * nothing stale); the first call on a device loads the library's device code
+ * there, so make it before any capture begins on that device.  All calls on a
+ * device share the one array, and it keeps the last call's contents (the call
+ * clears what must start at zero): calls that overlap on the GPU -- from
+ * several host threads or on several streams -- race on it and must be
+ * serialised by the caller.
  * Needs no handle.  Errors: EG_ERR_ARG, EG_ERR_NAN, EG_ERR_NOT_CONVERGED,
  * EG_ERR_CUDA. */
 EG_API eg_status eg_labels_static(const float *field, int d, const int64_t *extents, uint32_t flags,

@@ -26,8 +26,9 @@
 //
 // Bricks: every kernel after classification works on bricks, contiguous
 // ranges of linear vertex ids, in index order.  Flat layout: 1024 ids per
-// brick.  Row layout (2D/3D, axis-0 extent <= 1024): `ty` whole rows of one
-// plane per brick, so brick b = plane b / nyb, row block b % nyb.
+// brick.  Row layout (2D/3D with axis-0 extent <= 2048, 4D with axis-0 extent
+// <= 1024): `ty` whole rows of one plane per brick (one row when it holds more
+// than 1024 vertices), so brick b = plane b / nyb, row block b % nyb.
 #pragma once
 #include <cstdint>
 #include <type_traits>

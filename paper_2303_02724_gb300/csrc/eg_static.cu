@@ -15,11 +15,13 @@
 // classification record (16 bytes) plus per-brick counts and a status word.
 //
 // Host code must not hand the array's name to a kernel: in host code it is
-// only a stand-in for the symbol.  The device address is looked up once per
-// device with cudaGetSymbolAddress, with that device current, on the first
-// call made on it.
+// only a stand-in for the symbol.  The device address is looked up with
+// cudaGetSymbolAddress, with the caller's device current, at the start of
+// every call.  The lookup is a host-side query; the first one on a device
+// loads this library's device code there, which is what creates the array.
+// No address is cached, so a device reset (which unloads the module and may
+// move the array) cannot leave a stale address behind.
 #include <cstdint>
-#include <mutex>
 
 #include "eg.h"
 #include "eg_internal.cuh"
@@ -41,29 +43,15 @@ constexpr size_t kScratchBytes = kOffErr + 256;
 
 static __device__ __align__(256) unsigned char g_static_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-unsigned char *g_dev_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device (looked up once).
+// Device address of the scratch array on the current device.
 eg_status scratch_address(unsigned char **out)
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
         cudaGetLastError();
         return EG_ERR_CUDA;
     }
-    if (dev < 0 || dev >= kMaxDevices) return EG_ERR_ARG;
-    std::lock_guard<std::mutex> g(g_mu);
-    if (!g_dev_ptr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
-            cudaGetLastError();
-            return EG_ERR_CUDA;
-        }
-        g_dev_ptr[dev] = static_cast<unsigned char *>(p);
-    }
-    *out = g_dev_ptr[dev];
+    *out = static_cast<unsigned char *>(p);
     return EG_OK;
 }
 
@@ -88,10 +76,18 @@ extern "C" eg_status eg_labels_static(const float *field, int d, const int64_t *
         n[i] = uint32_t(extents[i]);
     }
     for (int i = d; i < kMaxDim; i++) s[i] = uint32_t(N);
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    // the call ends in a read-back and a stream synchronisation, neither of
+    // which a stream under capture allows
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(cs, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return EG_ERR_CUDA;
+    }
+    if (cap != cudaStreamCaptureStatusNone) return EG_ERR_ARG;
     unsigned char *scr = nullptr;
     eg_status st = scratch_address(&scr);
     if (st != EG_OK) return st;
-    cudaStream_t cs = static_cast<cudaStream_t>(stream);
 
     FieldDev F{};
     F.f = field;

@@ -426,9 +426,23 @@ class Handle:
 def labels_static(field, labels, minimum: bool = False, stream=None):
     """Allocation-free labels (eg_labels_static): field and labels are CUDA
     tensors (float32 / int32-sized, same shape); returns the status code."""
+    import torch
+    # every check runs before the library is touched: a labels buffer smaller
+    # than the field would be written past its end by the kernels
+    if field.dtype != torch.float32:
+        raise ValueError("field must be a float32 tensor")
+    if labels.dtype.itemsize != 4 or labels.dtype.is_floating_point:
+        raise ValueError("labels must be a 4-byte integer tensor")
+    if labels.numel() != field.numel():
+        raise ValueError(f"labels hold {labels.numel()} elements, the field {field.numel()}")
+    if not field.is_contiguous() or not labels.is_contiguous():
+        raise ValueError("field and labels must be contiguous")
+    if not field.is_cuda or not labels.is_cuda:
+        raise ValueError("field and labels must be CUDA tensors")
+    cur = torch.cuda.current_device()
+    if field.device.index != cur or labels.device.index != cur:
+        raise ValueError(f"field and labels must be on the current device (cuda:{cur})")
     lib = load()
-    if not field.is_cuda or not labels.is_cuda or field.dtype.itemsize != 4 or labels.dtype.itemsize != 4:
-        raise ValueError("field and labels must be 4-byte CUDA tensors")
     ext = _extents_of(field.shape)
     e = (ctypes.c_int64 * max(1, len(ext)))(*ext)
     return int(lib.eg_labels_static(ctypes.c_void_p(field.data_ptr()), len(ext), e,

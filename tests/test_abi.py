@@ -108,3 +108,21 @@ def test_bench_byte_accounting():
     kb8 = bench.kernel_bytes(c, es=1)
     assert kb8["classify"] == 1000 + 4 * 1000 + 12 * 30
     assert bench.path_bytes(c, es=1) == 1000 + 4 * 1000 + 5 * 10 + 6 * 20 + 8 * 21 + 4 * 40
+
+
+def test_labels_static_checks_arguments_before_any_launch():
+    """eg_labels_static's binding rejects a labels buffer of another size, a
+    non-float32 field, a float labels buffer and strided views before it
+    touches the library (CPU tensors here: no device is involved)."""
+    torch = pytest.importorskip("torch")
+    f = torch.zeros((4, 5), dtype=torch.float32)
+    with pytest.raises(ValueError, match="elements"):
+        eg.labels_static(f, torch.zeros(19, dtype=torch.int32))
+    with pytest.raises(ValueError, match="float32"):
+        eg.labels_static(f.to(torch.int32), torch.zeros(20, dtype=torch.int32))
+    with pytest.raises(ValueError, match="integer"):
+        eg.labels_static(f, torch.zeros(20, dtype=torch.float32))
+    with pytest.raises(ValueError, match="contiguous"):
+        eg.labels_static(torch.zeros((5, 4), dtype=torch.float32).t(), torch.zeros((4, 5), dtype=torch.int32))
+    with pytest.raises(ValueError, match="CUDA"):
+        eg.labels_static(f, torch.zeros((4, 5), dtype=torch.int32))

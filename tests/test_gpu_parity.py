@@ -114,8 +114,22 @@ def test_row_lengths(handle, n0):
     4-byte rows, one vertex per row (126-row bricks), rows over 1024 vertices
     (one row per brick), the 2048-vertex limit and the flat classifier just
     past it; 13 rows and 7 planes leave partial row blocks and work items."""
-    f = F.white_noise((7, 13, n0), 1000 + n0)
+    f = F.white_noise((n0, 13, 7), 1000 + n0)  # extents: axis 0 (the row) first
+    assert f.values.shape[-1] == n0
     assert_same(run_gpu(handle, f.values), oracle.compute(f.values))
+
+
+@pytest.mark.parametrize("ext", [(1024, 3, 3, 2), (1025, 2, 3, 2), (1100, 3, 3, 2), (2049, 2, 2, 2)],
+                         ids=lambda e: "x".join(map(str, e)))
+@pytest.mark.parametrize("kind", ["normal", "ties"])
+def test_4d_rows_over_1024(handle, handle_min, ext, kind):
+    """float32 4D fields whose rows hold more than 1024 vertices take the flat
+    classifier (the 4D row classifier stops at 1024): both graphs, against the
+    oracle, on either side of that limit."""
+    f = F.white_noise(ext, 4000 + ext[0]) if kind == "normal" else F.integer_ties(ext, 4000 + ext[0], 3)
+    assert f.values.shape[-1] == ext[0]
+    assert_same(run_gpu(handle, f.values), oracle.compute(f.values))
+    assert_same(run_gpu(handle_min, f.values), oracle.compute(f.values, minimum=True))
 
 
 def test_unaligned_field_pointer(handle):
