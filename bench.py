@@ -278,30 +278,30 @@ def run_reference(args, ws, rank):
     print(json.dumps(line), flush=True)
 
 
-def run_batch(args, ws, rank, local):
-    """Batched submission of the uneven 256-field mix vs per-field plain launches."""
+def batch_leg(args, ws, rank, local, steps, warmup):
+    """Batched submission of the uneven 256-field mix vs per-field plain
+    launches, both arms on the knobs the autotuner picked for the batch (and
+    the plain arm once more on the library defaults).  Returns a dict."""
     import numpy as np
     import torch
     from paper_2303_02724_gb300 import _build, eg, fields as F
+    from paper_2303_02724_gb300 import replicas
     _build.build()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    from paper_2303_02724_gb300 import replicas
     specs = F.batch_specs(3, args.batch_count)
     sizes = [int(np.prod(e)) for (e, _, _) in specs]
     mine = replicas.my_share(sizes, rank, ws)  # fields are independent: no data exchange
     flds = [F.batch_field(*specs[i]) for i in mine]
     ts = [torch.from_numpy(x.values).to(dev) for x in flds]
-    nv_total = sum(sizes)
+    nv_mine = sum(sizes[i] for i in mine)
     del flds
     stream = torch.cuda.current_stream(dev)
     h = eg.Handle(local)
-    # knobs (rows per tile, planes per work item, persistent CTAs per SM,
-    # resolver walks) tuned on this batch for the batched arm; the plain arm
-    # keeps the library defaults on its own handle
     tuned = h.autotune(ts, stream)
-    hp = eg.Handle(local)
-
+    knobs = {k: tuned[k] for k in ["classify_rows", "classify_planes", "resolve_walks", "persistent_ctas"]}
+    hp = eg.Handle(local, config=eg.EGConfig(**knobs))  # plain arm, same knobs
+    hd = eg.Handle(local)  # plain arm, library defaults
     h.set_timing(True)
     bsteps = []
 
@@ -313,47 +313,58 @@ def run_batch(args, ws, rank, local):
         for rid in ids:
             h.release(rid)
 
-    def plain():
-        for t in ts:
-            rid = hp.compute(t, stream)
-            hp.get_graph_device(rid)
-            hp.release(rid)
+    def plain_on(hh):
+        def run():
+            for t in ts:
+                rid = hh.compute(t, stream)
+                hh.get_graph_device(rid)
+                hh.release(rid)
+        return run
 
     out = {}
-    for name, fn in [("batched", batched), ("plain", plain)]:
-        for _ in range(args.warmup):
+    for name, fn, hh in [("batched", batched, h), ("plain", plain_on(hp), hp), ("plain_default", plain_on(hd), hd)]:
+        for _ in range(warmup):
             fn()
         torch.cuda.synchronize(dev)
         if ws > 1:
             import torch.distributed as tdist
             tdist.barrier()
-        hh = h if name == "batched" else hp
         l0 = hh.launch_count()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             fn()
         e1.record(stream)
         torch.cuda.synchronize(dev)
-        ms = replicas.reduce_max(e0.elapsed_time(e1) / args.steps, device=dev)
-        out[name] = {"ms_per_step": ms, "value": nv_total / (ms / 1e3) / 1e6,
+        ms = replicas.reduce_max(e0.elapsed_time(e1) / steps, device=dev)
+        out[name] = {"ms_per_step": ms, "value": sum(sizes) / (ms / 1e3) / 1e6,
                      "gpu_launches": int(hh.launch_count() - l0)}
+    for hh in (h, hp, hd):
+        hh.close()
+    return {"workload": WORKLOADS["batch"], "fields": len(specs), "vertices": sum(sizes),
+            "fields_this_rank": len(mine), "vertices_this_rank": nv_mine, "steps": steps, "warmup": warmup,
+            "timing": "CUDA events on the launching stream around all steps; one step = every field of the "
+                      "batch through the full path (results read back as device buffers)",
+            "batched": out["batched"], "plain": out["plain"], "plain_default": out["plain_default"],
+            "speedup_vs_plain": out["batched"]["value"] / out["plain"]["value"],
+            "speedup_vs_plain_default": out["batched"]["value"] / out["plain_default"]["value"],
+            "autotuned": knobs,
+            "step_ms": {nm: statistics.mean(x[i] for x in bsteps[-steps:])
+                        for i, nm in enumerate(["classify", "resolve", "emit"])}}
+
+
+def run_batch(args, ws, rank, local):
+    b = batch_leg(args, ws, rank, local, args.steps, args.warmup)
     if rank == 0:
         line = {"metric": "Mvertices/s full extremum graph (bit-exact), batched vs plain",
-                "value": out["batched"]["value"], "unit": "Mvertices/s", "n_gpus": ws, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": out["batched"]["ms_per_step"], "higher_is_better": True,
+                "value": b["batched"]["value"], "unit": "Mvertices/s", "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": b["batched"]["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOADS["batch"], "fields": len(specs), "vertices": nv_total,
+                "config": {"workload": WORKLOADS["batch"], "fields": b["fields"], "vertices": b["vertices"],
                            "parallelism": f"fields sharded over {ws} ranks"},
-                "plain": out["plain"], "speedup_vs_plain": out["batched"]["value"] / out["plain"]["value"],
-                "autotuned": tuned,
-                "step_ms": {nm: statistics.mean(x[i] for x in bsteps[-args.steps:])
-                            for i, nm in enumerate(["classify", "resolve", "emit"])},
-                "gpu_launches": out["batched"]["gpu_launches"]}
+                "batch": b, "gpu_launches": b["batched"]["gpu_launches"]}
         print(json.dumps(line), flush=True)
-    h.close()
-    hp.close()
 
 
 def serve_fields(count, seed=4):
@@ -377,44 +388,50 @@ def serve_fields(count, seed=4):
     return out
 
 
-def run_serve(args, ws, rank, local):
+def serve_leg(args, ws, rank, local, n_requests, fractions):
+    """Served stream: capacity (every request queued at once) and Poisson
+    arrivals at fractions of it, through the continuous-batching loop; the
+    client consumes each result as it completes (releases it), and the same
+    requests one by one through the plain path for comparison."""
     import numpy as np
     import torch
-    from paper_2303_02724_gb300 import _build, serve
+    from paper_2303_02724_gb300 import _build, eg, serve
     _build.build()
     torch.cuda.set_device(local)
-    vals = serve_fields(args.serve_requests)
+    dev = torch.device("cuda", local)
+    vals = serve_fields(n_requests)
     nv = sum(int(v.size) for v in vals)
     free, _total = torch.cuda.mem_get_info(local)
-    # results stay in device memory (the client releases them once consumed)
+    # results stay in device memory until the client, called as each request
+    # completes, releases them
     engines = [serve.GpuEngine(local, results="device"), serve.GpuEngine(local, results="device")]
     budget = int(free * 0.6)
 
+    def consume(r):
+        if r.result is not None:
+            r.result.release()
+
     def run(offsets):
-        srv = serve.Server(engines, budget_bytes=budget, max_batch=64, max_batch_vertices=1 << 27)
-        reqs = serve.replay(srv, vals[:len(offsets)], offsets)
+        srv = serve.Server(engines, budget_bytes=budget, max_batch=64, max_batch_vertices=1 << 27,
+                           on_done=consume)
+        serve.replay(srv, vals[:len(offsets)], offsets)
         srv.drain(3600)
         srv.close()
-        for r in reqs:
-            if r.result is not None:
-                r.result.release()
         return srv.stats()
 
-    run(np.zeros(min(len(vals), 64)))  # warm-up (pools, kernels)
+    run(np.zeros(len(vals)))  # warm-up: pools and staging buffers reach their steady size
     cap = run(np.zeros(len(vals)))  # everything queued at once: capacity
     rate_v = cap["throughput_mvps"] * 1e6
     mean_n = nv / len(vals)
     res = {}
-    for frac in args.serve_fractions:
+    for frac in fractions:
         offs = serve.poisson_arrivals(frac * rate_v / mean_n, len(vals), 4)
         res[str(frac)] = run(offs)
     for e in engines:
         e.close()
     # the same requests one at a time through the plain path (upload, compute,
     # wait, release), for comparison with the served throughput
-    from paper_2303_02724_gb300 import eg
     hp = eg.Handle(local)
-    dev = torch.device("cuda", local)
     for v in vals[:16]:
         rid = hp.compute(torch.from_numpy(v).to(dev))
         hp.get_graph_device(rid)
@@ -430,15 +447,22 @@ def run_serve(args, ws, rank, local):
     hp.close()
     plain = {"throughput_mvps": nv / plain_s / 1e6, "seconds": plain_s,
              "mode": "each request alone: upload, eg_compute, wait, release"}
+    return {"workload": WORKLOADS["serve"], "requests": len(vals), "vertices": nv, "budget_bytes": budget,
+            "engines": len(engines), "timing": "host wall clock from the first arrival to the last completion",
+            "capacity": cap, "poisson": res, "plain_one_by_one": plain,
+            "speedup_vs_plain": cap["throughput_mvps"] / plain["throughput_mvps"]}
+
+
+def run_serve(args, ws, rank, local):
+    sv = serve_leg(args, ws, rank, local, args.serve_requests, args.serve_fractions)
     if rank == 0:
-        line = {"metric": "served throughput (Mvertices/s) and latency", "value": cap["throughput_mvps"],
+        line = {"metric": "served throughput (Mvertices/s) and latency", "value": sv["capacity"]["throughput_mvps"],
                 "unit": "Mvertices/s", "n_gpus": ws, "steps": len(args.serve_fractions) + 1, "warmup": 1,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
-                "config": {"workload": WORKLOADS["serve"], "requests": len(vals), "vertices": nv,
-                           "budget_bytes": budget, "engines": len(engines)},
-                "capacity": cap, "poisson": res, "plain_one_by_one": plain,
-                "speedup_vs_plain": cap["throughput_mvps"] / plain["throughput_mvps"]}
+                "config": {"workload": WORKLOADS["serve"], "requests": sv["requests"], "vertices": sv["vertices"],
+                           "budget_bytes": sv["budget_bytes"], "engines": sv["engines"]},
+                "serve": sv}
         print(json.dumps(line), flush=True)
 
 
@@ -450,7 +474,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="grf512", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-sample-vertices", type=int, default=4 * 1024 * 1024)
-    ap.add_argument("--ref-sample-vertices", type=int, default=2 * 1024 * 1024)
+    ap.add_argument("--ref-sample-vertices", type=int, default=4 * 1024 * 1024,
+                    help="oracle sample of the reference arm (the same slabs as the cpu_baseline leg)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-threads", type=int, default=4,
@@ -465,6 +490,10 @@ def main():
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--serve-requests", type=int, default=4096)
     ap.add_argument("--serve-fractions", type=float, nargs="+", default=[0.5, 0.8, 0.95])
+    ap.add_argument("--no-legs", action="store_true",
+                    help="default workload only: skip the batched-vs-plain and served legs of the line")
+    ap.add_argument("--leg-steps", type=int, default=10, help="timed passes of the batched-vs-plain leg")
+    ap.add_argument("--leg-requests", type=int, default=1024, help="requests of the served leg")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -657,6 +686,17 @@ def main():
                "sample": desc + f", mean of 5 of 7 runs (best and worst dropped), {dt:.2f} s per run",
                "host": host_cpu()}
 
+    # the metric's second half on the default line: the batched form against
+    # per-field plain launches on the uneven mix, and a short served stream
+    legs = {}
+    if args.workload == "grf512" and not args.no_legs and not args.paths and not typed:
+        h.close()
+        torch.cuda.empty_cache()
+        legs["batch"] = batch_leg(args, ws, rank, local, args.leg_steps, args.warmup)
+        torch.cuda.empty_cache()
+        if ws == 1:
+            legs["serve"] = serve_leg(args, ws, rank, local, args.leg_requests, [0.8])
+
     if rank == 0:
         line = {
             "metric": "Mvertices/s full extremum graph (bit-exact)", "value": value, "unit": "Mvertices/s",
@@ -684,6 +724,7 @@ def main():
         }
         if bundle is not None:
             line["bundle"] = bundle
+        line.update(legs)
         print(json.dumps(line), flush=True)
     h.close()
     if dist is not None:

@@ -100,11 +100,38 @@ class GpuEngine:
         # CUDA graph per batch would never be repaid by a replay: launch directly
         self.handle = eg.Handle(device, minimum=minimum, config=eg.EGConfig(flags=eg.EG_FLAG_NO_GRAPH))
         self.stream = torch.cuda.Stream(device=device)
+        # one page-locked staging buffer and one device buffer per engine,
+        # grown on demand and reused: a batch's fields travel in ONE copy
+        self._pinned = None
+        self._dev = None
+        self._staged = None  # event: the last upload has left the staging buffer
+
+    def _upload(self, reqs: List[Request]):
+        """Device views of the batch's fields after one host-to-device copy."""
+        torch = self.torch
+        sizes = [r.n for r in reqs]
+        offs = np.concatenate([[0], np.cumsum([(n + 3) & ~3 for n in sizes])])  # 16-byte aligned fields
+        total = int(offs[-1])
+        if self._pinned is None or self._pinned.numel() < total:
+            if self._staged is not None:
+                self._staged.synchronize()
+            cap = max(total, 1 << 20)
+            self._pinned = torch.empty(cap, dtype=torch.float32, pin_memory=True)
+            self._dev = torch.empty(cap, dtype=torch.float32, device=self.device)
+        elif self._staged is not None:
+            self._staged.synchronize()  # the previous batch's copy has read the buffer
+        host = self._pinned.numpy()
+        for r, o in zip(reqs, offs[:-1]):
+            host[int(o):int(o) + r.n] = r.values.reshape(-1)
+        self._dev[:total].copy_(self._pinned[:total], non_blocking=True)
+        self._staged = torch.cuda.Event()
+        self._staged.record(self.stream)
+        return [self._dev[int(o):int(o) + r.n].view(r.values.shape) for r, o in zip(reqs, offs[:-1])]
 
     def run(self, reqs: List[Request]) -> None:
         torch = self.torch
         with torch.cuda.stream(self.stream):
-            ts = [torch.from_numpy(r.values).to(self.device) for r in reqs]
+            ts = self._upload(reqs)
             ids = self.handle.batch_submit(ts, self.stream)
             keep = []
             try:
@@ -129,8 +156,10 @@ class Server:
 
     def __init__(self, engines: list, budget_bytes: int, max_batch: int = 128,
                  max_batch_vertices: int = 1 << 28,
-                 bytes_fn: Callable[[int, int], int] = request_bytes):
+                 bytes_fn: Callable[[int, int], int] = request_bytes,
+                 on_done: Optional[Callable[[Request], None]] = None):
         self.engines = engines
+        self.on_done = on_done  # called by the worker for every finished request
         self.budget = int(budget_bytes)
         self.max_batch = max_batch
         self.max_batch_vertices = max_batch_vertices
@@ -228,6 +257,10 @@ class Server:
             except Exception as e:  # a failed batch reports its status per request
                 status = getattr(e, "status", -1)
             t_done = time.perf_counter()
+            if self.on_done is not None:
+                for r in batch:
+                    r.status = status
+                    self.on_done(r)
             with self.cv:
                 for r in batch:
                     r.admitted, r.done, r.batch, r.engine = t_adm, t_done, seq, ei
