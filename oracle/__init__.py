@@ -22,6 +22,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "eg_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "eg_cancel.c")]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libeg_oracle.so")
 _lock = threading.Lock()
@@ -44,12 +45,12 @@ def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no fast-math: IEEE comparisons only)."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(p) for p in _SRCS)):
         return _LIB_PATH
     fd, tmp = tempfile.mkstemp(suffix=".so", dir=_BUILD)
     os.close(fd)
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fno-fast-math",
-           "-ffp-contract=off", _SRC, "-o", tmp, "-lm"]
+           "-ffp-contract=off", *_SRCS, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -82,6 +83,9 @@ def _load():
         lib.eo_neighbour_offsets.restype = ctypes.c_int
         lib.eo_grid_adjacent.argtypes = [ctypes.c_int, P, P]
         lib.eo_grid_adjacent.restype = ctypes.c_int
+        lib.ec_cancel.argtypes = [ctypes.c_int64, P, P, ctypes.c_int64, P, P, P, P, ctypes.c_int,
+                                  ctypes.c_float, P, P, P]
+        lib.ec_cancel.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -199,6 +203,54 @@ def bundle(g: OracleGraph, minimum: bool = False) -> np.ndarray:
         pairs = [(e[a], e[b]) for a in range(len(e)) for b in range(a + 1, len(e))]
         keep[i] = 1 if not pairs or any(best[p] == i for p in pairs) else 0
     return keep
+
+
+@dataclass
+class Cancellation:
+    """Persistence-directed cancellation of an extremum graph (Sec. 3.5)."""
+    alive: np.ndarray     # uint8[S]  1 = the saddle is still in the graph
+    survivor: np.ndarray  # uint32[M] vertex id of the maximum each maximum was merged into
+    n_cancelled: int
+
+    def simplified_arcs(self, g) -> set:
+        """(saddle, maximum) pairs of the simplified graph: the kept saddles
+        with the survivors of their arc ends."""
+        surv = dict(zip(g.maxima.tolist(), self.survivor.tolist()))
+        out = set()
+        for i, s in enumerate(g.saddles.tolist()):
+            if self.alive[i]:
+                for m in g.col[g.row_ptr[i]:g.row_ptr[i + 1]].tolist():
+                    out.add((s, surv[m]))
+        return out
+
+
+def cancel(maxima, max_val, saddles, sad_val, row_ptr, col, tau: float,
+           minimum: bool = False) -> Cancellation:
+    """Persistence-directed cancellation (Sec. 3.5) of an extremum graph
+    given as arrays (maxima and saddles ascending, float32 values, the CSR of
+    arc ends as maximum vertex ids) with persistence threshold tau (float32).
+    The steps and the readings of the open cases are listed in eg_cancel.c."""
+    lib = _load()
+    mx = np.ascontiguousarray(maxima, np.uint32)
+    mv = np.ascontiguousarray(max_val, np.float32)
+    sd = np.ascontiguousarray(saddles, np.uint32)
+    sv = np.ascontiguousarray(sad_val, np.float32)
+    rp = np.ascontiguousarray(row_ptr, np.uint64)
+    cl = np.ascontiguousarray(col, np.uint32)
+    alive = np.empty(sd.size, np.uint8)
+    surv = np.empty(mx.size, np.uint32)
+    n = ctypes.c_int64(0)
+    st = lib.ec_cancel(mx.size, mx.ctypes.data, mv.ctypes.data, sd.size, sd.ctypes.data, sv.ctypes.data,
+                       rp.ctypes.data, cl.ctypes.data, int(minimum), ctypes.c_float(tau), alive.ctypes.data,
+                       surv.ctypes.data, ctypes.byref(n))
+    if st != EO_OK:
+        raise OracleError({EO_ERR_ARG: "bad argument", EO_ERR_OOM: "out of memory"}.get(st, str(st)))
+    return Cancellation(alive, surv, int(n.value))
+
+
+def cancel_graph(g: OracleGraph, tau: float, minimum: bool = False) -> Cancellation:
+    """cancel() on an oracle result (float32 fields)."""
+    return cancel(g.maxima, g.max_val, g.saddles, g.sad_val, g.row_ptr, g.col, tau, minimum)
 
 
 def neighbour_offsets(d: int) -> np.ndarray:
