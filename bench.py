@@ -482,6 +482,9 @@ def main():
                     help="host threads (one library handle each) taking turns in the end-to-end loop")
     ap.add_argument("--bundle", action="store_true",
                     help="also time arc bundling (eg_get_bundled) on one result of the workload")
+    ap.add_argument("--cancel", type=float, nargs="*", default=None,
+                    help="also time persistence-directed cancellation (eg_get_cancelled) on one result of the "
+                         "workload at these thresholds (fractions of the range of maximum values)")
     ap.add_argument("--paths", action="store_true",
                     help="also gather the arc geometry (EG_FLAG_PATHS) in every timed step")
     ap.add_argument("--dtype", default="float32", choices=list(SHORT_DTYPE),
@@ -614,6 +617,23 @@ def main():
         bundle = {"ms": bms, "timing": "host wall clock per eg_get_bundled call (device work, two waits, "
                   "copy of the keep mask)", "saddles": int(keep.size), "kept": int(keep.sum())}
 
+    cancel = None
+    if args.cancel is not None:
+        rid, g = step()
+        gh = h.get_graph(rid, labels=False)
+        spread = float(np.float32(gh.max_val.max()) - np.float32(gh.max_val.min()))
+        cancel = []
+        for frac in (args.cancel or [0.01, 0.1, float("inf")]):
+            tau = float(np.float32(spread * frac)) if np.isfinite(frac) else float("inf")
+            h.get_cancelled(rid, tau)  # warm-up
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            alive, surv, n, rounds = h.get_cancelled(rid, tau)
+            cancel.append({"tau_fraction_of_range": frac, "tau": tau, "ms": (time.perf_counter() - t0) * 1e3,
+                           "cancelled": n, "rounds": rounds, "saddles": int(alive.size),
+                           "surviving_maxima": int(np.unique(surv).size)})
+        h.release(rid)
+
     # end to end through the C ABI with host buffers: H2D of the field and
     # D2H of the graph inside the timed region
     e2e = None
@@ -724,6 +744,9 @@ def main():
         }
         if bundle is not None:
             line["bundle"] = bundle
+        if cancel is not None:
+            line["cancel"] = {"timing": "host wall clock per eg_get_cancelled call (device rounds, a count "
+                                        "read-back per group of rounds, copies of the results)", "runs": cancel}
         line.update(legs)
         print(json.dumps(line), flush=True)
     h.close()

@@ -242,7 +242,35 @@ EG_API eg_status eg_get_paths(eg_handle h, eg_result_id id, uint64_t *path_ptr, 
  * deferred device status as eg_get_graph. */
 EG_API eg_status eg_get_bundled(eg_handle h, eg_result_id id, uint8_t *keep);
 
-/* Autotuner: time candidate values of every eg_config knob on this batch of
+/* Persistence-directed cancellation (Sec. 3.5) on a finished float32 result,
+ * with persistence threshold tau.  The cost of a saddle is the difference in
+ * value between it and the second highest maximum its arcs currently reach
+ * (for a simple saddle: the lower of its two maxima; the lowest for a minimum
+ * graph), computed in float32 (0 for equal values).  Saddles are cancelled in
+ * increasing order of (current cost, vertex id) while that cost is at most
+ * tau; cancelling a saddle merges every maximum it reaches except the highest
+ * (the survivor) into the survivor, so arcs that ended at a merged maximum
+ * end at the survivor afterwards.  A saddle whose arcs all reach one maximum
+ * is never cancelled.  Where a merge lowers the cost of a multi-saddle (two of
+ * its maxima merge), the lower cost counts at once: the paper assumes costs
+ * never fall and leaves that case open.  The order of cancellations is the
+ * paper's serial queue; it runs on the device in data-parallel rounds that
+ * cancel, at once, every saddle that no neighbouring saddle could precede.
+ * alive: caller-owned host uint8[n_saddles], in the order of eg_graph.saddles,
+ *        1 = the saddle stays in the simplified graph, 0 = cancelled;
+ * survivor: caller-owned host uint32[n_maxima], in the order of
+ *        eg_graph.maxima: the vertex id of the maximum it was merged into
+ *        (itself when it survives);
+ * n_cancelled, n_rounds (may be NULL): cancelled saddles, device rounds run.
+ * The simplified graph is the kept saddles with the survivors of their arc
+ * ends.  Runs on the handle's own stream and waits for it.
+ * Errors: EG_ERR_ARG (unknown id, NaN tau, a result that is not float32,
+ * NULL outputs with saddles or maxima present), EG_ERR_OOM, EG_ERR_INTERNAL,
+ * plus any deferred device status as eg_get_graph. */
+EG_API eg_status eg_get_cancelled(eg_handle h, eg_result_id id, float tau, uint8_t *alive, uint32_t *survivor,
+                                  int64_t *n_cancelled, int32_t *n_rounds);
+
+/* Autotuner: time candidate values/* Autotuner: time candidate values of every eg_config knob on this batch of
  * fields (coordinate descent over the knobs, each candidate a full run of the
  * pipeline timed with CUDA events on `stream`), keep the fastest in the
  * handle's configuration for later calls, and return it in *best (may be

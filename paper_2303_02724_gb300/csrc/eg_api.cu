@@ -1400,6 +1400,92 @@ eg_status eg_get_bundled(eg_handle h, eg_result_id id, uint8_t *keep)
     return done(herr ? EG_ERR_INTERNAL : EG_OK);
 }
 
+eg_status eg_get_cancelled(eg_handle h, eg_result_id id, float tau, uint8_t *alive, uint32_t *survivor,
+                           int64_t *n_cancelled, int32_t *n_rounds)
+{
+    if (!h || tau != tau) return EG_ERR_ARG;
+    std::lock_guard<std::mutex> g(h->mu);
+    cudaSetDevice(h->device);
+    auto it = h->results.find(id);
+    if (it == h->results.end()) return EG_ERR_ARG;
+    Result &r = *it->second;
+    eg_status s = collect(h, r);
+    if (s != EG_OK) return s;
+    if (r.dtype != kF32 || (r.S && !alive) || (r.M && !survivor)) return EG_ERR_ARG;
+    cudaStream_t st = h->side;
+    void *buf[13] = {};
+    auto done = [&](eg_status x) {
+        cudaStreamSynchronize(st);
+        for (void *p : buf) h->pool.release(p);
+        return x;
+    };
+    const uint64_t M = r.M, S = r.S, A = r.A;
+    const size_t sizes[13] = {4 * A, 4 * A, 4 * M, 8 * M, 8 * M, 8 * M, 8 * S, 8 * S, 4 * S, S, 32, S, 4 * M};
+    cudaError_t e;
+    for (int i = 0; i < 13; i++)
+        if ((e = h->pool.alloc(&buf[i], std::max<size_t>(sizes[i], 16))) != cudaSuccess) return done(from_cuda(e));
+    CancelDev C{};
+    C.maxima = static_cast<const uint32_t *>(r.maxima);
+    C.max_val = static_cast<const float *>(r.max_val);
+    C.sad_val = static_cast<const float *>(r.sad_val);
+    C.row_ptr = static_cast<const uint64_t *>(r.row_ptr);
+    C.end = static_cast<uint32_t *>(buf[0]);
+    C.aroot = static_cast<uint32_t *>(buf[1]);
+    C.root = static_cast<uint32_t *>(buf[2]);
+    C.merge = static_cast<unsigned long long *>(buf[3]);
+    C.minlb = static_cast<unsigned long long *>(buf[4]);
+    C.min2 = static_cast<unsigned long long *>(buf[5]);
+    C.costkey = static_cast<unsigned long long *>(buf[6]);
+    C.lbkey = static_cast<unsigned long long *>(buf[7]);
+    C.high = static_cast<uint32_t *>(buf[8]);
+    C.state = static_cast<uint8_t *>(buf[9]);
+    C.ctrl = static_cast<unsigned long long *>(buf[10]);
+    C.err = reinterpret_cast<uint32_t *>(C.ctrl + 3);
+    C.M = uint32_t(M);
+    C.S = uint32_t(S);
+    C.tau = tau;
+    C.minimum = (r.flags & kFlagMinimum) ? 1 : 0;
+    if ((e = cudaMemsetAsync(C.ctrl, 0, 32, st)) != cudaSuccess) return done(from_cuda(e));
+    if ((e = launch_cancel_setup(C, static_cast<const uint32_t *>(r.col), A, st)) != cudaSuccess)
+        return done(from_cuda(e));
+    h->launches += 2;
+    // rounds in growing groups between looks at the last round's count; a
+    // round cancels at least one saddle until none is left to cancel, so
+    // S + 1 rounds always suffice
+    uint32_t round = 0, group = 1;
+    unsigned long long last = 1;
+    while (last != 0) {
+        if (round > S + 1) return done(EG_ERR_INTERNAL);
+        for (uint32_t k = 0; k < group; k++) {
+            if ((e = launch_cancel_round(C, ++round, st)) != cudaSuccess) return done(from_cuda(e));
+            h->launches += 4;
+        }
+        if ((e = cudaMemcpyAsync(&last, C.ctrl + 1, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+            return done(from_cuda(e));
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return done(from_cuda(e));
+        group = std::min<uint32_t>(group * 2, 16);
+    }
+    uint8_t *dalive = static_cast<uint8_t *>(buf[11]);
+    uint32_t *dsurv = static_cast<uint32_t *>(buf[12]);
+    if ((e = launch_cancel_out(C, dalive, dsurv, st)) != cudaSuccess) return done(from_cuda(e));
+    h->launches += 1;
+    uint32_t herr = 0;
+    if (S && (e = cudaMemcpyAsync(alive, dalive, S, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return done(from_cuda(e));
+    if (M && (e = cudaMemcpyAsync(survivor, dsurv, 4 * M, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return done(from_cuda(e));
+    if ((e = cudaMemcpyAsync(&herr, C.err, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return done(from_cuda(e));
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return done(from_cuda(e));
+    if (herr) return done(EG_ERR_INTERNAL);
+    if (n_cancelled) {
+        int64_t c = 0;
+        for (uint64_t i = 0; i < S; i++) c += alive[i] ? 0 : 1;
+        *n_cancelled = c;
+    }
+    if (n_rounds) *n_rounds = int32_t(round);
+    return done(EG_OK);
+}
+
 eg_status eg_get_graph_device(eg_handle h, eg_result_id id, eg_graph *out)
 {
     if (!h || !out) return EG_ERR_ARG;

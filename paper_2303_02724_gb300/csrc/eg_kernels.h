@@ -94,4 +94,31 @@ cudaError_t launch_bundle_typed(uint32_t dtype, const uint64_t *row_ptr, const u
                                 unsigned long long *keys, unsigned long long *best, unsigned int *best_id,
                                 uint32_t lg, uint8_t *keep, uint32_t *err, cudaStream_t st);
 
+// Persistence-directed cancellation on a finished float32 graph, in rounds
+// (see eg_cancel.cu).  Every array is device memory sized as noted.
+struct CancelDev {
+    const uint32_t *maxima;      // [M] vertex ids, ascending
+    const float *max_val;        // [M]
+    const float *sad_val;        // [S]
+    const uint64_t *row_ptr;     // [S+1] arcs of every saddle
+    uint32_t *end;               // [A] arc end as an index into maxima
+    uint32_t *aroot;             // [A] current survivor of every arc end (this round)
+    uint32_t *root;              // [M] current survivor of every maximum
+    unsigned long long *merge;   // [M] (round << 32) | target of a merge marked this round
+    unsigned long long *minlb;   // [M] smallest lb key of the saddles reaching it
+    unsigned long long *min2;    // [M] smallest lb key but the smallest one's holder
+    unsigned long long *costkey; // [S]
+    unsigned long long *lbkey;   // [S]
+    uint32_t *high;              // [S] highest current maximum of the saddle
+    uint8_t *state;              // [S] 0 waiting, 1 cancelled, 2 never cancelled
+    unsigned long long *ctrl;    // [0] cheapest cancellable key, [1] cancellations this round
+    uint32_t *err;               // status word
+    uint32_t M, S;
+    float tau;
+    int minimum;
+};
+cudaError_t launch_cancel_setup(const CancelDev &C, const uint32_t *col, uint64_t A, cudaStream_t st);
+cudaError_t launch_cancel_round(const CancelDev &C, uint32_t stamp, cudaStream_t st);
+cudaError_t launch_cancel_out(const CancelDev &C, uint8_t *alive, uint32_t *survivor, cudaStream_t st);
+
 }  // namespace eg

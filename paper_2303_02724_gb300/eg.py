@@ -88,6 +88,8 @@ SIGNATURES = {
     "eg_get_graph_device": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(EGGraphC)]),
     "eg_get_paths": (ctypes.c_int, [_P, ctypes.c_uint64, _P, _P, ctypes.POINTER(ctypes.c_uint64)]),
     "eg_get_bundled": (ctypes.c_int, [_P, ctypes.c_uint64, _P]),
+    "eg_get_cancelled": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_float, _P, _P,
+                                        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]),
     "eg_release": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "eg_workspace_bytes": (ctypes.c_uint64, [ctypes.c_int, _P]),
     "eg_mem_info": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
@@ -357,6 +359,21 @@ class Handle:
         _check(self._lib.eg_get_bundled(self._h, ctypes.c_uint64(rid), ctypes.c_void_p(keep.ctypes.data)),
                "eg_get_bundled")
         return keep[:g.n_saddles]
+
+    def get_cancelled(self, rid: int, tau: float):
+        """Persistence-directed cancellation of a finished float32 result with
+        threshold tau: (alive uint8[S], survivor uint32[M], n_cancelled,
+        rounds)."""
+        g = EGGraphC()
+        _check(self._lib.eg_get_graph(self._h, ctypes.c_uint64(rid), ctypes.byref(g)), "eg_get_graph")
+        alive = np.empty(max(1, g.n_saddles), np.uint8)
+        surv = np.empty(max(1, g.n_maxima), np.uint32)
+        n = ctypes.c_int64()
+        rounds = ctypes.c_int32()
+        _check(self._lib.eg_get_cancelled(self._h, ctypes.c_uint64(rid), ctypes.c_float(tau),
+                                          ctypes.c_void_p(alive.ctypes.data), ctypes.c_void_p(surv.ctypes.data),
+                                          ctypes.byref(n), ctypes.byref(rounds)), "eg_get_cancelled")
+        return alive[:g.n_saddles], surv[:g.n_maxima], int(n.value), int(rounds.value)
 
     def path_count(self, rid: int) -> int:
         """Number of path vertices of a result computed with EG_FLAG_PATHS."""
