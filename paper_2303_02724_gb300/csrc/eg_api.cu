@@ -163,6 +163,7 @@ struct Result {
     void *maxima = nullptr, *max_val = nullptr, *saddles = nullptr, *sad_b0 = nullptr, *sad_val = nullptr,
          *row_ptr = nullptr, *col = nullptr, *ends = nullptr, *ucnt = nullptr;
     void *path_ptr = nullptr, *path_vtx = nullptr, *pbrick = nullptr;  // arc geometry (EG_FLAG_PATHS)
+    void *code = nullptr;   // 4-bit gradient codes (until the result completes)
     uint64_t M = 0, S = 0, P = 0, A = 0, V = 0;
     bool have_A = false;
     uint32_t err = 0;
@@ -207,6 +208,8 @@ struct eg_ctx {
     uint64_t ws_bricks = 0;
     void *ws_scan = nullptr;
     uint64_t ws_tiles = 0;
+    void *ws_xlist = nullptr;  // exit list of the code resolver (one u64 per entry)
+    uint64_t ws_xcap = 0;
     void *lut3 = nullptr;  // saddle class table of the 3D link graph + two-component table
     void *stage = nullptr;  // device staging for eg_compute_host
     size_t stage_bytes = 0;
@@ -257,6 +260,7 @@ bool make_shape(int d, const int64_t *ext, Shape &sh)
 struct Layout {
     int kd;
     bool zm;
+    bool code;  // gradient codes + tiled code resolution (plane-marching fields below 2^31 vertices)
     bool r4;  // 4D row classifier (row layout over (z, w) planes)
     uint32_t ty, nyb, nbricks, bcap, zc, nzc;
     size_t smem;
@@ -293,6 +297,7 @@ Layout make_layout(const Shape &sh, int sm_count, const eg_config &cfg, uint32_t
         }
         L.nzc = (n2 + L.zc - 1) / L.zc;
         L.smem = zm_smem_bytes(n0, ty);
+        L.code = sh.N < (1ull << 31);
     } else if (L.kd == 4 && n0 <= 1024 && f32_values) {
         // 4D row classifier: one thread per kR4Vertices consecutive vertices of
         // a row, ty whole rows of one (z, w) plane per brick
@@ -332,9 +337,10 @@ eg_status grow(eg_ctx *h, void **p, uint64_t &cap, uint64_t want, size_t elem)
     return EG_OK;
 }
 
-eg_status ensure_workspace(eg_ctx *h, uint64_t recs, uint64_t bricks, uint64_t tiles)
+eg_status ensure_workspace(eg_ctx *h, uint64_t recs, uint64_t bricks, uint64_t tiles, uint64_t xents)
 {
-    if (recs <= h->ws_rec_cap && bricks <= h->ws_bricks && tiles <= h->ws_tiles) return EG_OK;
+    if (recs <= h->ws_rec_cap && bricks <= h->ws_bricks && tiles <= h->ws_tiles && xents <= h->ws_xcap)
+        return EG_OK;
     // earlier computations may still use the old workspace
     cudaEventSynchronize(h->ws_free);
     h->ws_gen++;
@@ -368,13 +374,23 @@ eg_status ensure_workspace(eg_ctx *h, uint64_t recs, uint64_t bricks, uint64_t t
         (void)t;
         h->ws_tiles = c;
     }
+    if (xents > h->ws_xcap) {
+        h->pool.release(h->ws_xlist);
+        h->ws_xlist = nullptr;
+        h->ws_xcap = 0;
+        const uint64_t c = std::max<uint64_t>(xents, 1024);
+        cudaError_t e = h->pool.alloc(&h->ws_xlist, c * sizeof(uint64_t));
+        if (e != cudaSuccess) return from_cuda(e);
+        h->ws_xcap = c;
+    }
     return EG_OK;
 }
 
 void free_result_buffers(eg_ctx *h, Result *r)
 {
     void **bufs[] = {&r->lab, &r->maxima,   &r->max_val,  &r->saddles, &r->sad_b0, &r->sad_val, &r->row_ptr,
-                     &r->col, &r->ends,     &r->ucnt,     &r->path_ptr, &r->path_vtx, &r->pbrick, &r->wide};
+                     &r->col, &r->ends,     &r->ucnt,     &r->path_ptr, &r->path_vtx, &r->pbrick, &r->wide,
+                     &r->code};
     for (void **b : bufs) {
         h->pool.release(*b);
         *b = nullptr;
@@ -421,12 +437,18 @@ struct Plan {
     std::vector<Group> groups;
     uint64_t total_bricks = 0, total_tiles = 0;
     uint64_t total_rtiles = 0;  // tiled resolution pass (3D kernels)
+    uint64_t total_ctiles = 0;  // code resolver tiles (code fields)
     size_t desc_bytes = 0;
     int walks = 4, ctas = 3;
     int sm_count = 0;
     std::vector<TypedField> widen;   // narrow integer fields: float32 image before classification
     std::string signature;  // identical for calls that can share a captured graph
 };
+
+// Header slot of the scan workspace holding the code resolver's exit count
+// (slots 0-1: scan tickets; 2..: one work-queue ticket per plane-marching
+// group, of which there are at most four: two row classes x two graphs).
+constexpr int kXcountSlot = 31;
 
 // Enqueue one phase of the pipeline on st, reading descriptors from Dd:
 //   0: descriptor upload, scan state reset, counters reset, classification
@@ -450,12 +472,13 @@ eg_status enqueue_part(eg_ctx *h, int part, const Plan &P, const FieldDev *Dd, c
             if ((e = launch_widen(t.dtype, Dd + t.pos, t.n, P.sm_count, st)) != cudaSuccess) return from_cuda(e);
             nl++;
         }
+        int zi = 0;  // work-queue tickets of the plane-marching groups: header slots 2, 3, ...
         for (size_t gi = 0; gi < P.groups.size(); gi++) {
             const Group &G = P.groups[gi];
             if (G.zm)
                 e = launch_classify_zm(G.minimum, Dd + G.first, G.count, G.items, G.smem,
                                        static_cast<const uint32_t *>(h->lut3),
-                                       reinterpret_cast<unsigned long long *>(h->ws_scan) + 2 + gi, h->sm_count,
+                                       reinterpret_cast<unsigned long long *>(h->ws_scan) + 2 + zi++, h->sm_count,
                                        P.ctas, st);
             else if (G.r4)
                 e = launch_classify_r4(G.minimum, Dd + G.first, G.count, G.bricks, st);
@@ -473,6 +496,13 @@ eg_status enqueue_part(eg_ctx *h, int part, const Plan &P, const FieldDev *Dd, c
         }
         if ((e = launch_resolve(Dd, P.nf, P.total_bricks, P.walks, st)) != cudaSuccess) return from_cuda(e);
         nl++;
+        if (P.total_ctiles) {
+            unsigned long long *xcount = reinterpret_cast<unsigned long long *>(h->ws_scan) + kXcountSlot;
+            if ((e = launch_resolve_codes(Dd, P.nf, P.total_ctiles, static_cast<uint64_t *>(h->ws_xlist), xcount,
+                                          h->sm_count, st)) != cudaSuccess)
+                return from_cuda(e);
+            nl += 2;
+        }
     } else {
         if ((e = cudaMemcpyAsync(const_cast<FieldDev *>(Dd), desc_host, P.desc_bytes, cudaMemcpyHostToDevice, st)) !=
             cudaSuccess)
@@ -651,13 +681,15 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
     P.ctas = cfg.persistent_ctas > 0 ? cfg.persistent_ctas : 3;
     P.sm_count = h->sm_count;
     uint64_t total_recs = 0;
+    uint64_t total_xents = 0;  // exit list capacity: the vertices of the code fields
     for (int i = 0; i < nf; i++) {
         P.total_bricks += lay[i].nbricks;
         total_recs += uint64_t(lay[i].nbricks) * lay[i].bcap;
         P.total_tiles += scan_tiles(lay[i].nbricks);
+        if (lay[i].code) total_xents += jobs[i].sh.N;
     }
     P.desc_bytes = sizeof(FieldDev) * size_t(nf);
-    eg_status es = ensure_workspace(h, total_recs, P.total_bricks, P.total_tiles);
+    eg_status es = ensure_workspace(h, total_recs, P.total_bricks, P.total_tiles, total_xents);
     if (es != EG_OK) return es;
 
     auto L = std::make_shared<Launch>();
@@ -702,6 +734,9 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
         r->launch = L;
         e = h->pool.alloc(&r->lab, j.sh.N * sizeof(uint32_t));
         if (e == cudaSuccess && dtype_narrow(j.dtype)) e = h->pool.alloc(&r->wide, j.sh.N * sizeof(float));
+        const uint32_t n0p = (j.sh.n[0] + 7u) & ~7u;
+        if (e == cudaSuccess && ly.code)
+            e = h->pool.alloc(&r->code, uint64_t(n0p) / 8 * j.sh.n[1] * j.sh.n[2] * sizeof(uint32_t));
         r->small = static_cast<SmallBlock *>(L->smalls) + i;
         r->slot = i;
         res[i] = std::move(r);
@@ -748,6 +783,10 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
             resolve_tile_shape(F.n[0], F.n[1], F.n[2], F.rt, &nt);
             P.total_rtiles += nt;
         }
+        F.code = static_cast<uint32_t *>(R.code);
+        F.n0p = n0p;
+        F.ctile0 = P.total_ctiles;
+        if (ly.code) P.total_ctiles += code_tiles(F.n[0], F.n[1], F.n[2]);
         G.count++;
         G.bricks += ly.nbricks;
         G.items += ly.zm ? uint64_t(ly.nyb) * ly.nzc : ly.nbricks;
@@ -942,7 +981,8 @@ eg_status collect(eg_ctx *h, Result &r)
         h->pool.release(r.ucnt);
         h->pool.release(r.pbrick);
         h->pool.release(r.wide);
-        r.ends = r.ucnt = r.pbrick = r.wide = nullptr;
+        h->pool.release(r.code);
+        r.ends = r.ucnt = r.pbrick = r.wide = r.code = nullptr;
         if (r.launch && r.launch.use_count() == 1) release_launch(h, r.launch.get());
     }
     if (r.err & kErrNaN) return EG_ERR_NAN;
@@ -1413,16 +1453,18 @@ eg_status eg_get_cancelled(eg_handle h, eg_result_id id, float tau, uint8_t *ali
     if (s != EG_OK) return s;
     if (r.dtype != kF32 || (r.S && !alive) || (r.M && !survivor)) return EG_ERR_ARG;
     cudaStream_t st = h->side;
-    void *buf[13] = {};
+    constexpr int kBufs = 14;
+    void *buf[kBufs] = {};
     auto done = [&](eg_status x) {
         cudaStreamSynchronize(st);
         for (void *p : buf) h->pool.release(p);
         return x;
     };
     const uint64_t M = r.M, S = r.S, A = r.A;
-    const size_t sizes[13] = {4 * A, 4 * A, 4 * M, 8 * M, 8 * M, 8 * M, 8 * S, 8 * S, 4 * S, S, 32, S, 4 * M};
+    const size_t sizes[kBufs] = {4 * A, 4 * A, 4 * M, 8 * M, 8 * M, 8 * S, 8 * S, 4 * S, S,
+                                 4 * S, 4 * S, 64, S, 4 * M};
     cudaError_t e;
-    for (int i = 0; i < 13; i++)
+    for (int i = 0; i < kBufs; i++)
         if ((e = h->pool.alloc(&buf[i], std::max<size_t>(sizes[i], 16))) != cudaSuccess) return done(from_cuda(e));
     CancelDev C{};
     C.maxima = static_cast<const uint32_t *>(r.maxima);
@@ -1431,42 +1473,53 @@ eg_status eg_get_cancelled(eg_handle h, eg_result_id id, float tau, uint8_t *ali
     C.row_ptr = static_cast<const uint64_t *>(r.row_ptr);
     C.end = static_cast<uint32_t *>(buf[0]);
     C.aroot = static_cast<uint32_t *>(buf[1]);
-    C.root = static_cast<uint32_t *>(buf[2]);
-    C.merge = static_cast<unsigned long long *>(buf[3]);
-    C.minlb = static_cast<unsigned long long *>(buf[4]);
-    C.min2 = static_cast<unsigned long long *>(buf[5]);
-    C.costkey = static_cast<unsigned long long *>(buf[6]);
-    C.lbkey = static_cast<unsigned long long *>(buf[7]);
-    C.high = static_cast<uint32_t *>(buf[8]);
-    C.state = static_cast<uint8_t *>(buf[9]);
-    C.ctrl = static_cast<unsigned long long *>(buf[10]);
-    C.err = reinterpret_cast<uint32_t *>(C.ctrl + 3);
+    C.parent = static_cast<uint32_t *>(buf[2]);
+    C.minlb = static_cast<unsigned long long *>(buf[3]);
+    C.min2 = static_cast<unsigned long long *>(buf[4]);
+    C.costkey = static_cast<unsigned long long *>(buf[5]);
+    C.lbkey = static_cast<unsigned long long *>(buf[6]);
+    C.high = static_cast<uint32_t *>(buf[7]);
+    C.state = static_cast<uint8_t *>(buf[8]);
+    C.list[0] = static_cast<uint32_t *>(buf[9]);
+    C.list[1] = static_cast<uint32_t *>(buf[10]);
+    C.ctrl = static_cast<unsigned long long *>(buf[11]);
+    C.err = reinterpret_cast<uint32_t *>(C.ctrl + 4);
     C.M = uint32_t(M);
     C.S = uint32_t(S);
     C.tau = tau;
     C.minimum = (r.flags & kFlagMinimum) ? 1 : 0;
-    if ((e = cudaMemsetAsync(C.ctrl, 0, 32, st)) != cudaSuccess) return done(from_cuda(e));
+    const unsigned long long ctrl0[5] = {~0ull, 0ull, S, 0ull, 0ull};
+    if ((e = cudaMemcpyAsync(C.ctrl, ctrl0, sizeof ctrl0, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return done(from_cuda(e));
     if ((e = launch_cancel_setup(C, static_cast<const uint32_t *>(r.col), A, st)) != cudaSuccess)
         return done(from_cuda(e));
     h->launches += 2;
-    // rounds in growing groups between looks at the last round's count; a
-    // round cancels at least one saddle until none is left to cancel, so
-    // S + 1 rounds always suffice
-    uint32_t round = 0, group = 1;
-    unsigned long long last = 1;
-    while (last != 0) {
-        if (round > S + 1) return done(EG_ERR_INTERNAL);
-        for (uint32_t k = 0; k < group; k++) {
-            if ((e = launch_cancel_round(C, ++round, st)) != cudaSuccess) return done(from_cuda(e));
-            h->launches += 4;
-        }
-        if ((e = cudaMemcpyAsync(&last, C.ctrl + 1, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    // multi-CTA rounds while many saddles wait (each round cancels at least
+    // one saddle until none is left to cancel), then the one-CTA tail
+    constexpr uint64_t kTail = 32768;
+    int p = 0, rounds = 0;
+    uint64_t waiting = S;
+    bool finished = S == 0;
+    while (!finished && waiting > kTail) {
+        if ((e = launch_cancel_round(C, p, waiting, st)) != cudaSuccess) return done(from_cuda(e));
+        h->launches += 4;
+        rounds++;
+        p ^= 1;
+        unsigned long long back[4];
+        if ((e = cudaMemcpyAsync(back, C.ctrl, sizeof back, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
             return done(from_cuda(e));
         if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return done(from_cuda(e));
-        group = std::min<uint32_t>(group * 2, 16);
+        waiting = back[2 + p];
+        finished = back[1] == 0 || waiting == 0;
+        if (rounds > int64_t(S) + 1) return done(EG_ERR_INTERNAL);
     }
-    uint8_t *dalive = static_cast<uint8_t *>(buf[11]);
-    uint32_t *dsurv = static_cast<uint32_t *>(buf[12]);
+    if (!finished) {
+        if ((e = launch_cancel_tail(C, p, st)) != cudaSuccess) return done(from_cuda(e));
+        h->launches += 1;
+        rounds++;
+    }
+    uint8_t *dalive = static_cast<uint8_t *>(buf[12]);
+    uint32_t *dsurv = static_cast<uint32_t *>(buf[13]);
     if ((e = launch_cancel_out(C, dalive, dsurv, st)) != cudaSuccess) return done(from_cuda(e));
     h->launches += 1;
     uint32_t herr = 0;
@@ -1482,7 +1535,7 @@ eg_status eg_get_cancelled(eg_handle h, eg_result_id id, float tau, uint8_t *ali
         for (uint64_t i = 0; i < S; i++) c += alive[i] ? 0 : 1;
         *n_cancelled = c;
     }
-    if (n_rounds) *n_rounds = int32_t(round);
+    if (n_rounds) *n_rounds = int32_t(rounds);
     return done(EG_OK);
 }
 

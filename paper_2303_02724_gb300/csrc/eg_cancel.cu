@@ -9,20 +9,27 @@
 // below) every cancellation takes the saddle of lowest current (cost, id),
 // cost = second highest adjacent maximum minus the saddle, in float32.
 //
-// Rounds.  Two saddles that reach no common maximum (after the merges so far)
-// do not affect each other's cost.  A saddle s may be cancelled in the current
-// round, ahead of the serial order, when no saddle x sharing a maximum with it
-// could come first: x's cost can only fall to lb(x) = lowest adjacent maximum
-// minus x (merges replace a maximum by a higher one, and a multi-saddle whose
-// maxima merge can drop to its lowest one), so s is safe when
-//   (cost(s), id(s)) < (lb(x), id(x))  for every such x.
-// Safe saddles share no maximum with one another (two of them would each have
-// to be below the other), so their merges are disjoint and all of them are
-// cancelled at once, together with the global cheapest saddle, which the serial
-// order takes next anyway.  Every round therefore cancels at least one saddle
-// and the result equals the serial one.  A saddle that joins one maximum, or
-// whose lb exceeds the threshold, can never be cancelled (lb never falls) and
-// leaves the rounds for good.
+// Rounds.  Cancelling s merges its dying maxima D(s) (all it reaches but the
+// highest, h(s)) into h(s).  Until s is cancelled, its cost and D(s) can only
+// change through a cancellation that merges a maximum of D(s) away, and such a
+// cancellation must come from a saddle that reaches that maximum now (or one
+// that reaches it later through a merge into it, which again needs a saddle
+// that reaches it now).  A saddle x's cost can only fall to lb(x) = lowest
+// maximum it reaches minus x (merges replace a maximum by a higher one, and a
+// multi-saddle whose maxima merge can drop to its lowest one).  So s may be
+// cancelled now, ahead of the serial order and with the serial result, when
+//   (cost(s), id(s)) < (lb(x), id(x))  for every other saddle x reaching a
+//   maximum of D(s).
+// Merging h(s) itself away (into a higher maximum) leaves cost(s) and D(s)
+// unchanged and only relabels the survivor, so saddles that share nothing but
+// h(s) with s do not constrain it.  Two safe saddles never share a dying
+// maximum (each would have to be below the other), so all safe saddles are
+// cancelled at once, together with the global cheapest saddle, which the
+// serial order takes next anyway; a survivor of one may die in another, and
+// the merges of a round are followed as chains.  Every round cancels at least
+// one saddle.  A saddle that joins one maximum, or whose lb exceeds the
+// threshold, can never be cancelled (lb never falls) and leaves the rounds for
+// good.
 //
 // Multi-saddles: merging two maxima of a multi-saddle can lower its second
 // highest maximum, so its cost can fall, which the paper's discard rule does
@@ -30,11 +37,16 @@
 // cancelled as soon as it is the cheapest), which is what the serial queue
 // does whenever costs never fall.
 //
-// One round = four kernels: evaluate (current maxima, cost and lb keys, the
-// per-maximum minimum of lb keys, the global cheapest), second minima per
-// maximum, decide + mark the merges, apply the merges.  Keys are
-// (float32 bits of a non-negative cost) << 32 | saddle index, so one 64-bit
-// atomicMin orders by cost, then by vertex id (saddles are in id order).
+// One round, over the list of waiting saddles: evaluate (current maxima by
+// following the merges, cost and lb keys, the per-maximum minimum of lb keys,
+// the global cheapest), second minima per maximum, decide (cancel, and point
+// each dying maximum at its survivor), reset the per-maximum minima and keep
+// the still-waiting saddles for the next round.  While many saddles wait, a
+// round is four launches over all CTAs; the tail (few saddles, often many
+// rounds of one or two cancellations between a few large maxima) runs in one
+// CTA with block barriers.  Keys are (float32 bits of a non-negative cost)
+// << 32 | saddle index, so one 64-bit atomicMin orders by cost, then by
+// vertex id (saddles are in id order).
 #include "eg_internal.cuh"
 #include "eg_kernels.h"
 
@@ -68,6 +80,21 @@ __device__ __forceinline__ unsigned long long c_key(float cost, uint32_t s)
     return (static_cast<unsigned long long>(__float_as_uint(cost)) << 32) | s;
 }
 
+// Current survivor of maximum m: follow the merges (each goes to a strictly
+// higher maximum) and shorten the chain behind (any ancestor is a valid
+// parent, so concurrent shortening is harmless).
+__device__ __forceinline__ uint32_t c_find(const CancelDev &C, uint32_t m)
+{
+    uint32_t r = m;
+    for (uint32_t hops = 0; hops < C.M; hops++) {
+        const uint32_t p = C.parent[r];
+        if (p == r) break;
+        r = p;
+    }
+    if (C.parent[m] != r) C.parent[m] = r;
+    return r;
+}
+
 // Distinct current maxima of saddle s from the per-arc snapshot.
 __device__ __forceinline__ int c_adjacent(const CancelDev &C, uint32_t s, uint32_t (&u)[kMaxAdj])
 {
@@ -79,6 +106,93 @@ __device__ __forceinline__ int c_adjacent(const CancelDev &C, uint32_t s, uint32
         if (!dup && n < kMaxAdj) u[n++] = r;
     }
     return n;
+}
+
+// Phase 1 for one waiting saddle: its current maxima, keys, the per-maximum
+// minimum lb key; returns its cost key if it may be cancelled (else kNoKey).
+__device__ __forceinline__ unsigned long long c_eval(const CancelDev &C, uint32_t s)
+{
+    for (uint64_t a = C.row_ptr[s]; a < C.row_ptr[s + 1]; a++) C.aroot[a] = c_find(C, C.end[a]);
+    uint32_t u[kMaxAdj];
+    const int n = c_adjacent(C, s, u);
+    if (n < 2) {
+        C.state[s] = 2;  // joins one maximum: never cancelled
+        return kNoKey;
+    }
+    uint32_t h1 = u[0], h2 = 0xffffffffu, lo = u[0];
+    for (int k = 1; k < n; k++) {
+        if (c_higher(C, u[k], h1)) {
+            h2 = h1;
+            h1 = u[k];
+        } else if (h2 == 0xffffffffu || c_higher(C, u[k], h2)) {
+            h2 = u[k];
+        }
+        if (c_higher(C, lo, u[k])) lo = u[k];
+    }
+    const float fs = C.sad_val[s];
+    const float cost = c_cost(C, fs, h2), lb = c_cost(C, fs, lo);
+    if (lb > C.tau) {
+        C.state[s] = 2;  // its cost never falls below lb: never cancelled
+        return kNoKey;
+    }
+    const unsigned long long ck = c_key(cost, s), lk = c_key(lb, s);
+    C.costkey[s] = ck;
+    C.lbkey[s] = lk;
+    C.high[s] = h1;
+    for (int k = 0; k < n; k++) atomicMin(C.minlb + u[k], lk);
+    return cost <= C.tau ? ck : kNoKey;
+}
+
+// Phase 2: per maximum, the smallest lb key other than the minimum's holder.
+__device__ __forceinline__ void c_second(const CancelDev &C, uint32_t s)
+{
+    if (C.state[s] != 0) return;
+    uint32_t u[kMaxAdj];
+    const int n = c_adjacent(C, s, u);
+    const unsigned long long lk = C.lbkey[s];
+    for (int k = 0; k < n; k++)
+        if (C.minlb[u[k]] != lk) atomicMin(C.min2 + u[k], lk);
+}
+
+// Phase 3: cancel the saddle if it is safe or the global cheapest; its dying
+// maxima get their survivor as parent.  Returns 1 when it is cancelled.
+__device__ __forceinline__ int c_decide(const CancelDev &C, uint32_t s, unsigned long long gmin)
+{
+    if (C.state[s] != 0) return 0;
+    const unsigned long long ck = C.costkey[s];
+    if (__uint_as_float(uint32_t(ck >> 32)) > C.tau) return 0;
+    uint32_t u[kMaxAdj];
+    const int n = c_adjacent(C, s, u);
+    const uint32_t h1 = C.high[s];
+    bool safe = ck == gmin;
+    if (!safe) {
+        const unsigned long long lk = C.lbkey[s];
+        safe = true;
+        for (int k = 0; k < n; k++) {
+            if (u[k] == h1) continue;  // the survivor: see above
+            const unsigned long long m1 = C.minlb[u[k]];
+            const unsigned long long other = m1 == lk ? C.min2[u[k]] : m1;
+            safe &= other > ck;
+        }
+    }
+    if (!safe) return 0;
+    C.state[s] = 1;
+    // the next round's finds read these (every eval of this round is done)
+    for (int k = 0; k < n; k++)
+        if (u[k] != h1) C.parent[u[k]] = h1;
+    return 1;
+}
+
+// Phase 4: clear the per-maximum minima this saddle set (from its snapshot:
+// the maxima of this round), and keep it for the next round if it waits.
+__device__ __forceinline__ bool c_reset(const CancelDev &C, uint32_t s)
+{
+    for (uint64_t a = C.row_ptr[s]; a < C.row_ptr[s + 1]; a++) {
+        const uint32_t r = C.aroot[a];
+        C.minlb[r] = kNoKey;
+        C.min2[r] = kNoKey;
+    }
+    return C.state[s] == 0;
 }
 
 // Arc ends as indices into the (sorted) maxima list.
@@ -104,49 +218,23 @@ __global__ void k_cancel_init(CancelDev C)
 {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < C.M) {
-        C.root[i] = i;
-        C.merge[i] = 0;
+        C.parent[i] = i;
+        C.minlb[i] = kNoKey;
+        C.min2[i] = kNoKey;
     }
-    if (i < C.S) C.state[i] = 0;
+    if (i < C.S) {
+        C.state[i] = 0;
+        C.list[0][i] = i;  // every saddle waits
+    }
 }
 
-// 1: current maxima of every waiting saddle, its keys, the per-maximum
-// minimum lb key and the global cheapest cancellable saddle.
-__global__ void __launch_bounds__(kCancelThreads) k_cancel_eval(CancelDev C)
+// Multi-CTA round over the waiting list `in` (count ctrl[2 + p]); the next
+// list goes to `out` (count ctrl[2 + !p], zeroed by the host).
+__global__ void __launch_bounds__(kCancelThreads) k_cancel_eval(CancelDev C, int p)
 {
-    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long gk = kNoKey;
-    if (s < C.S && C.state[s] == 0) {
-        for (uint64_t a = C.row_ptr[s]; a < C.row_ptr[s + 1]; a++) C.aroot[a] = C.root[C.end[a]];
-        uint32_t u[kMaxAdj];
-        const int n = c_adjacent(C, s, u);
-        if (n < 2) {
-            C.state[s] = 2;  // joins one maximum: never cancelled
-        } else {
-            uint32_t h1 = u[0], h2 = 0xffffffffu, lo = u[0];
-            for (int k = 1; k < n; k++) {
-                if (c_higher(C, u[k], h1)) {
-                    h2 = h1;
-                    h1 = u[k];
-                } else if (h2 == 0xffffffffu || c_higher(C, u[k], h2)) {
-                    h2 = u[k];
-                }
-                if (c_higher(C, lo, u[k])) lo = u[k];
-            }
-            const float fs = C.sad_val[s];
-            const float cost = c_cost(C, fs, h2), lb = c_cost(C, fs, lo);
-            if (lb > C.tau) {
-                C.state[s] = 2;  // its cost never falls below lb: never cancelled
-            } else {
-                const unsigned long long ck = c_key(cost, s), lk = c_key(lb, s);
-                C.costkey[s] = ck;
-                C.lbkey[s] = lk;
-                C.high[s] = h1;
-                for (int k = 0; k < n; k++) atomicMin(C.minlb + u[k], lk);
-                if (cost <= C.tau) gk = ck;
-            }
-        }
-    }
+    if (i < uint32_t(C.ctrl[2 + p])) gk = c_eval(C, C.list[p][i]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long y = __shfl_xor_sync(0xffffffffu, gk, o);
@@ -155,53 +243,78 @@ __global__ void __launch_bounds__(kCancelThreads) k_cancel_eval(CancelDev C)
     if ((threadIdx.x & 31) == 0 && gk != kNoKey) atomicMin(C.ctrl, gk);
 }
 
-// 2: per maximum, the smallest lb key other than the minimum's own holder.
-__global__ void __launch_bounds__(kCancelThreads) k_cancel_second(CancelDev C)
-{
-    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= C.S || C.state[s] != 0) return;
-    uint32_t u[kMaxAdj];
-    const int n = c_adjacent(C, s, u);
-    const unsigned long long lk = C.lbkey[s];
-    for (int k = 0; k < n; k++)
-        if (C.minlb[u[k]] != lk) atomicMin(C.min2 + u[k], lk);
-}
-
-// 3: cancel every safe saddle and the global cheapest; mark their merges.
-__global__ void __launch_bounds__(kCancelThreads) k_cancel_decide(CancelDev C, uint32_t stamp)
-{
-    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= C.S || C.state[s] != 0) return;
-    const unsigned long long ck = C.costkey[s];
-    if (__uint_as_float(uint32_t(ck >> 32)) > C.tau) return;
-    uint32_t u[kMaxAdj];
-    const int n = c_adjacent(C, s, u);
-    bool safe = ck == C.ctrl[0];
-    if (!safe) {
-        const unsigned long long lk = C.lbkey[s];
-        safe = true;
-        for (int k = 0; k < n; k++) {
-            const unsigned long long m1 = C.minlb[u[k]];
-            const unsigned long long other = m1 == lk ? C.min2[u[k]] : m1;
-            safe &= other > ck;
-        }
-    }
-    if (!safe) return;
-    C.state[s] = 1;
-    atomicAdd(C.ctrl + 1, 1ull);
-    const uint32_t h1 = C.high[s];
-    for (int k = 0; k < n; k++)
-        if (u[k] != h1) C.merge[u[k]] = (static_cast<unsigned long long>(stamp) << 32) | h1;
-}
-
-// 4: every maximum follows the merge of its current survivor (one hop: a
-// survivor of this round is merged nowhere this round).
-__global__ void k_cancel_apply(CancelDev C, uint32_t stamp)
+__global__ void __launch_bounds__(kCancelThreads) k_cancel_second(CancelDev C, int p)
 {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= C.M) return;
-    const unsigned long long m = C.merge[C.root[i]];
-    if (uint32_t(m >> 32) == stamp) C.root[i] = uint32_t(m);
+    if (i < uint32_t(C.ctrl[2 + p])) c_second(C, C.list[p][i]);
+}
+
+__global__ void __launch_bounds__(kCancelThreads) k_cancel_decide(CancelDev C, int p)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    int c = 0;
+    if (i < uint32_t(C.ctrl[2 + p])) c = c_decide(C, C.list[p][i], C.ctrl[0]);
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(C.ctrl + 1, (unsigned long long)c);
+}
+
+__global__ void __launch_bounds__(kCancelThreads) k_cancel_reset(CancelDev C, int p)
+{
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    bool keep = false;
+    uint32_t s = 0;
+    if (i < uint32_t(C.ctrl[2 + p])) {
+        s = C.list[p][i];
+        keep = c_reset(C, s);
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, keep);
+    if (!m) return;
+    unsigned long long b = 0;
+    if (lane == __ffs(m) - 1) b = atomicAdd(C.ctrl + 2 + (p ^ 1), (unsigned long long)__popc(m));
+    b = __shfl_sync(0xffffffffu, b, __ffs(m) - 1);
+    if (keep) C.list[p ^ 1][b + __popc(m & ((1u << lane) - 1u))] = s;
+}
+
+// The tail: once few saddles wait, one CTA runs the remaining rounds (block
+// barriers instead of launches) until a round cancels nothing.  The round
+// count is bounded by the waiting saddles (each round cancels at least one).
+__global__ void __launch_bounds__(1024) k_cancel_tail(CancelDev C, int p)
+{
+    __shared__ unsigned long long s_gmin;
+    __shared__ unsigned s_count, s_next;
+    const int tid = threadIdx.x;
+    unsigned n = unsigned(C.ctrl[2 + p]);
+    for (unsigned round = 0; round <= n + 1 && n > 0; round++) {
+        if (tid == 0) {
+            s_gmin = kNoKey;
+            s_count = 0;
+            s_next = 0;
+        }
+        __syncthreads();
+        for (unsigned i = tid; i < n; i += blockDim.x) {
+            const unsigned long long k = c_eval(C, C.list[p][i]);
+            if (k != kNoKey) atomicMin(&s_gmin, k);
+        }
+        __syncthreads();
+        for (unsigned i = tid; i < n; i += blockDim.x) c_second(C, C.list[p][i]);
+        __syncthreads();
+        const unsigned long long gmin = s_gmin;
+        for (unsigned i = tid; i < n; i += blockDim.x)
+            if (c_decide(C, C.list[p][i], gmin)) atomicAdd(&s_count, 1u);
+        __syncthreads();
+        for (unsigned i = tid; i < n; i += blockDim.x) {
+            const uint32_t s = C.list[p][i];
+            if (c_reset(C, s)) C.list[p ^ 1][atomicAdd(&s_next, 1u)] = s;
+        }
+        __syncthreads();
+        const unsigned cancelled = s_count;
+        n = s_next;
+        p ^= 1;
+        __syncthreads();
+        if (cancelled == 0) break;
+    }
+    if (tid == 0) C.ctrl[1] = 0;
 }
 
 // Results: keep flag per saddle, vertex id of each maximum's survivor.
@@ -209,7 +322,7 @@ __global__ void k_cancel_out(CancelDev C, uint8_t *alive, uint32_t *survivor)
 {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < C.S) alive[i] = C.state[i] != 1 ? 1 : 0;
-    if (i < C.M) survivor[i] = C.maxima[C.root[i]];
+    if (i < C.M) survivor[i] = C.maxima[c_find(C, i)];
 }
 
 static inline dim3 grid_of(uint64_t n) { return dim3(unsigned((n + kCancelThreads - 1) / kCancelThreads)); }
@@ -222,19 +335,24 @@ cudaError_t launch_cancel_setup(const CancelDev &C, const uint32_t *col, uint64_
     return cudaGetLastError();
 }
 
-cudaError_t launch_cancel_round(const CancelDev &C, uint32_t stamp, cudaStream_t st)
+cudaError_t launch_cancel_round(const CancelDev &C, int p, uint64_t waiting, cudaStream_t st)
 {
     cudaError_t e;
-    if ((e = cudaMemsetAsync(C.minlb, 0xff, sizeof(unsigned long long) * C.M, st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(C.min2, 0xff, sizeof(unsigned long long) * C.M, st)) != cudaSuccess) return e;
+    // ctrl[0] = no key, ctrl[1] = 0, next list count = 0
     if ((e = cudaMemsetAsync(C.ctrl, 0xff, sizeof(unsigned long long), st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(C.ctrl + 1, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
-    if (C.S) {
-        k_cancel_eval<<<grid_of(C.S), kCancelThreads, 0, st>>>(C);
-        k_cancel_second<<<grid_of(C.S), kCancelThreads, 0, st>>>(C);
-        k_cancel_decide<<<grid_of(C.S), kCancelThreads, 0, st>>>(C, stamp);
-    }
-    if (C.M) k_cancel_apply<<<grid_of(C.M), kCancelThreads, 0, st>>>(C, stamp);
+    if ((e = cudaMemsetAsync(C.ctrl + 2 + (p ^ 1), 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
+    if (waiting == 0) return cudaSuccess;
+    k_cancel_eval<<<grid_of(waiting), kCancelThreads, 0, st>>>(C, p);
+    k_cancel_second<<<grid_of(waiting), kCancelThreads, 0, st>>>(C, p);
+    k_cancel_decide<<<grid_of(waiting), kCancelThreads, 0, st>>>(C, p);
+    k_cancel_reset<<<grid_of(waiting), kCancelThreads, 0, st>>>(C, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cancel_tail(const CancelDev &C, int p, cudaStream_t st)
+{
+    k_cancel_tail<<<1, 1024, 0, st>>>(C, p);
     return cudaGetLastError();
 }
 

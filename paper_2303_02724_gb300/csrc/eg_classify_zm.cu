@@ -466,7 +466,17 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
             um4[0] = make_uint4(um[0], um[1], um[2], um[3]);
             um4[1] = make_uint4(um[4], um[5], um[6], um[7]);
             uint32_t *dst = F.lab + vrow;
-            if (vec) {
+            if (F.code) {
+                // 4-bit codes, the 8 vertices of this thread in one word (x is a
+                // multiple of 8 and rows are padded to n0p codes)
+                uint32_t w = 0;
+#pragma unroll
+                for (int i = 0; i < kVx; i++) {
+                    const uint32_t c = (um[i] & 0x3fffu) ? ((um[i] >> 14) & 15u) : kCodeMax;
+                    w |= (x + i < G.n0 ? c : kCodeMax) << (4 * i);
+                }
+                F.code[code_word(F.n0p, uint64_t(z) * G.n1 + y0 + r, x)] = w;
+            } else if (vec) {
                 // n0 is a multiple of 4, so x+3 < n0; the second half may be past the row
                 *reinterpret_cast<uint4 *>(dst) = make_uint4(asc[0], asc[1], asc[2], asc[3]);
                 if (x + 7 < G.n0) *reinterpret_cast<uint4 *>(dst + 4) = make_uint4(asc[4], asc[5], asc[6], asc[7]);

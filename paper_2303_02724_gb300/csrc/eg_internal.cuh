@@ -217,6 +217,13 @@ struct FieldDev {
     uint32_t *path_vtx;      // [V] saddle, representative, ..., maximum per path
     uint64_t *pbrick;        // [nbricks + 1] path vertices per brick, then offsets and the total
     uint32_t *err;           // device status word
+    // gradient codes (3D plane-marching classifier, fields of fewer than 2^31
+    // vertices; null otherwise, and the gradient pointers go to lab[]): 4 bits
+    // per vertex, the gradient's neighbour slot or kCodeMax, rows padded to
+    // n0p (a multiple of 8) codes, 8 codes per word, lowest nibble first
+    uint32_t *code;
+    uint32_t n0p;
+    uint64_t ctile0;         // first tile of this field in the code resolver's grid
     uint32_t n[kMaxDim];     // extents (1 beyond the kernel dimension)
     uint32_t s[kMaxDim];     // strides
     uint32_t N;              // vertex count (< 2^32)
@@ -236,6 +243,18 @@ struct FieldDev {
     uint32_t flags;
     uint32_t dtype;          // element type of fraw
 };
+
+// Gradient codes: the 4-bit code of a maximum; a label whose top bit is set is
+// not a label but the vertex where a gradient path left its resolution tile
+// (code fields only, fields of fewer than 2^31 vertices).
+constexpr uint32_t kCodeMax = 15u;
+constexpr uint32_t kLabelExit = 0x80000000u;
+
+// Word index and bit shift of the code of vertex (x, row), row = z * n1 + y.
+__host__ __device__ __forceinline__ uint64_t code_word(uint32_t n0p, uint64_t row, uint32_t x)
+{
+    return (row * n0p + x) >> 3;
+}
 
 __host__ __device__ __forceinline__ void brick_range(const FieldDev &F, uint32_t b, uint64_t &v0, uint32_t &len)
 {
@@ -293,6 +312,17 @@ __device__ __forceinline__ uint32_t slot_vertex(uint32_t v, int k, const uint32_
     uint32_t p = k < NB::H ? uint32_t(NB::H - k) : uint32_t(k - NB::H + 1);
     uint32_t o = pattern_offset(p, s);
     return k < NB::H ? v - o : v + o;
+}
+
+// The gradient target of vertex u before resolution: decoded from the 3D
+// gradient codes, or read from the gradient pointers in lab[].
+__device__ __forceinline__ uint32_t grad_next(const FieldDev &F, uint32_t u)
+{
+    if (!F.code) return F.lab[u];
+    const uint32_t row = u / F.n[0], x = u - row * F.n[0];
+    const uint32_t c = (F.code[code_word(F.n0p, row, x)] >> ((x & 7u) * 4u)) & 15u;
+    if (c == kCodeMax) return u;
+    return slot_vertex<3>(u, int(c), F.s);
 }
 
 __device__ __forceinline__ int lowest_bit(uint32_t m) { return __ffs(m) - 1; }

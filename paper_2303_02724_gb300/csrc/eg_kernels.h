@@ -66,6 +66,11 @@ cudaError_t launch_resolve_tiles(const FieldDev *fields, int nf, uint64_t tiles,
 // Resolution tile extents (log2) of a field of extents n0 x n1 x n2, and the
 // number of its tiles.
 void resolve_tile_shape(uint32_t n0, uint32_t n1, uint32_t n2, uint32_t rt[3], uint64_t *tiles);
+// Resolution from gradient codes: tiles (code_tiles per code field, numbered
+// from FieldDev::ctile0), then the exit list (xlist / xcount, zeroed count).
+uint64_t code_tiles(uint32_t n0, uint32_t n1, uint32_t n2);
+cudaError_t launch_resolve_codes(const FieldDev *fields, int nf, uint64_t tiles, uint64_t *xlist,
+                                 unsigned long long *xcount, int sm_count, cudaStream_t st);
 
 // Steps (d)+(e): nodes and arc ends per brick (one kernel dimension), then CSR.
 cudaError_t launch_nodes_d(int kd, const FieldDev *fields, int nf, uint64_t base, uint64_t bricks, cudaStream_t st);
@@ -102,23 +107,28 @@ struct CancelDev {
     const float *sad_val;        // [S]
     const uint64_t *row_ptr;     // [S+1] arcs of every saddle
     uint32_t *end;               // [A] arc end as an index into maxima
-    uint32_t *aroot;             // [A] current survivor of every arc end (this round)
-    uint32_t *root;              // [M] current survivor of every maximum
-    unsigned long long *merge;   // [M] (round << 32) | target of a merge marked this round
+    uint32_t *aroot;             // [A] survivor of every arc end (this round)
+    uint32_t *parent;            // [M] merge target of a merged maximum, else itself
     unsigned long long *minlb;   // [M] smallest lb key of the saddles reaching it
     unsigned long long *min2;    // [M] smallest lb key but the smallest one's holder
     unsigned long long *costkey; // [S]
     unsigned long long *lbkey;   // [S]
     uint32_t *high;              // [S] highest current maximum of the saddle
     uint8_t *state;              // [S] 0 waiting, 1 cancelled, 2 never cancelled
-    unsigned long long *ctrl;    // [0] cheapest cancellable key, [1] cancellations this round
+    uint32_t *list[2];           // [S] each: waiting saddles of this / the next round
+    unsigned long long *ctrl;    // [0] cheapest cancellable key, [1] cancellations this
+                                 // round, [2], [3] counts of list[0], list[1]
     uint32_t *err;               // status word
     uint32_t M, S;
     float tau;
     int minimum;
 };
+// Set-up (every saddle waits, in list[0]); one multi-CTA round over list[p]
+// (`waiting` = its count, read back by the host); the one-CTA tail from
+// list[p] to the end; the results.
 cudaError_t launch_cancel_setup(const CancelDev &C, const uint32_t *col, uint64_t A, cudaStream_t st);
-cudaError_t launch_cancel_round(const CancelDev &C, uint32_t stamp, cudaStream_t st);
+cudaError_t launch_cancel_round(const CancelDev &C, int p, uint64_t waiting, cudaStream_t st);
+cudaError_t launch_cancel_tail(const CancelDev &C, int p, cudaStream_t st);
 cudaError_t launch_cancel_out(const CancelDev &C, uint8_t *alive, uint32_t *survivor, cudaStream_t st);
 
 }  // namespace eg

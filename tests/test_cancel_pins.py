@@ -253,3 +253,88 @@ def test_field_invariants(case):
         gm = _field_graph(F.Field(-f.values, f.extents), minimum=True)
         cm = oracle.cancel_graph(gm, tau, minimum=True)
         assert np.array_equal(c.alive, cm.alive) and np.array_equal(c.survivor, cm.survivor)
+
+
+# ------------------------------------------- the device's round schedule ----
+
+def rounds_model(maxima, max_val, saddles, sad_val, row_ptr, col, tau, minimum=False):
+    """The schedule the device runs (data-parallel rounds), written out in
+    Python on the graph arrays: in every round each waiting saddle computes its
+    current maxima, cost and lb (lowest maximum minus the saddle); a saddle is
+    cancelled when its (cost, id) is below the (lb, id) of every other waiting
+    saddle that reaches one of its dying maxima, or when it is the globally
+    cheapest; merges follow chains.  Must reproduce the serial queue."""
+    mv = {int(m): np.float32(v) for m, v in zip(maxima, max_val)}
+    root = {int(m): int(m) for m in maxima}
+    state = [0] * len(saddles)  # 0 waiting, 1 cancelled, 2 never
+    tau32 = np.float32(tau)
+    order = (lambda r: (-mv[r], -r)) if minimum else (lambda r: (mv[r], r))
+    rounds = 0
+    while True:
+        rounds += 1
+        info = {}
+        for i in range(len(saddles)):
+            if state[i]:
+                continue
+            rs = sorted({root[int(e)] for e in col[row_ptr[i]:row_ptr[i + 1]]}, key=order, reverse=True)
+            if len(rs) < 2:
+                state[i] = 2
+                continue
+            fs = np.float32(sad_val[i])
+
+            def cost_to(m):
+                fm = mv[m]
+                return np.float32(0) if fm == fs else (fs - fm if minimum else fm - fs)
+            c, lb = cost_to(rs[1]), cost_to(rs[-1])
+            if lb > tau32:
+                state[i] = 2
+                continue
+            info[i] = (rs, (float(c), int(saddles[i])), (float(lb), int(saddles[i])))
+        cand = [k[1] for k in info.values() if k[1][0] <= tau32]
+        if not cand:
+            return np.array([0 if s == 1 else 1 for s in state], np.uint8), \
+                np.array([root[int(m)] for m in maxima], np.uint32), rounds
+        gmin = min(cand)
+        reach = {}
+        for i, (rs, _, lk) in info.items():
+            for r in rs:
+                reach.setdefault(r, []).append((lk, i))
+        merge = {}
+        for i, (rs, ck, _) in info.items():
+            if ck[0] > tau32:
+                continue
+            safe = ck == gmin or all(lk > ck for r in rs[1:] for lk, j in reach[r] if j != i)
+            if safe:
+                state[i] = 1
+                for r in rs[1:]:
+                    assert r not in merge  # dying maxima of one round are disjoint
+                    merge[r] = rs[0]
+        for m in root:
+            r = root[m]
+            while r in merge:
+                r = merge[r]
+            root[m] = r
+
+
+@pytest.mark.parametrize("seed", range(80))
+def test_round_schedule_matches_serial_queue(seed):
+    rng = random.Random(5000 + seed)
+    nm, ns = rng.randint(2, 30), rng.randint(1, 60)
+    g = random_graph(rng, nm, ns, 5, ints=seed % 4 == 0, simple=seed % 5 == 1)
+    for tau in [0.0, float(np.float32(rng.uniform(0, 3))), float(np.float32(rng.uniform(0, 8))), np.inf]:
+        for minimum in (False, True):
+            gg = (g[0], -g[1], g[2], -g[3], g[4], g[5]) if minimum else g
+            c = oracle.cancel(*gg, tau, minimum=minimum)
+            alive, surv, _ = rounds_model(*gg, tau, minimum=minimum)
+            assert np.array_equal(alive, c.alive), (seed, tau, minimum)
+            assert np.array_equal(surv, c.survivor), (seed, tau, minimum)
+
+
+def test_round_schedule_on_a_field_graph_takes_few_rounds():
+    """On the extremum graph of a random field the rounds stay far below the
+    number of cancellations (the schedule is parallel, not serial)."""
+    g = oracle.compute(F.grf((24, 20, 18), 2).values)
+    c = oracle.cancel_graph(g, np.inf)
+    alive, surv, rounds = rounds_model(g.maxima, g.max_val, g.saddles, g.sad_val, g.row_ptr, g.col, np.inf)
+    assert np.array_equal(alive, c.alive) and np.array_equal(surv, c.survivor)
+    assert rounds < c.n_cancelled / 4, (rounds, c.n_cancelled)
