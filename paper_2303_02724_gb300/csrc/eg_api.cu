@@ -475,15 +475,20 @@ eg_status enqueue_part(eg_ctx *h, int part, const Plan &P, const FieldDev *Dd, c
         int zi = 0;  // work-queue tickets of the plane-marching groups: header slots 2, 3, ...
         for (size_t gi = 0; gi < P.groups.size(); gi++) {
             const Group &G = P.groups[gi];
-            if (G.zm)
+            if (G.zm) {
                 e = launch_classify_zm(G.minimum, Dd + G.first, G.count, G.items, G.smem,
                                        static_cast<const uint32_t *>(h->lut3),
                                        reinterpret_cast<unsigned long long *>(h->ws_scan) + 2 + zi++, h->sm_count,
                                        P.ctas, st);
-            else if (G.r4)
+                if (e == cudaSuccess)
+                    e = launch_saddle_multi(G.minimum, Dd + G.first, G.count, G.brick0, G.bricks,
+                                            static_cast<const uint32_t *>(h->lut3), st);
+                nl++;
+            } else if (G.r4) {
                 e = launch_classify_r4(G.minimum, Dd + G.first, G.count, G.bricks, st);
-            else
+            } else {
                 e = launch_classify_flat(G.kd, G.cdt, Dd + G.first, G.count, G.bricks, st);
+            }
             if (e != cudaSuccess) return from_cuda(e);
             nl++;
         }

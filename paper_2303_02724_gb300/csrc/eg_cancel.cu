@@ -285,7 +285,8 @@ __global__ void __launch_bounds__(1024) k_cancel_tail(CancelDev C, int p)
     __shared__ unsigned s_count, s_next;
     const int tid = threadIdx.x;
     unsigned n = unsigned(C.ctrl[2 + p]);
-    for (unsigned round = 0; round <= n + 1 && n > 0; round++) {
+    const unsigned bound = n + 1;  // rounds that cancel something: at most the waiting saddles
+    for (unsigned round = 0; round <= bound && n > 0; round++) {
         if (tid == 0) {
             s_gmin = kNoKey;
             s_count = 0;

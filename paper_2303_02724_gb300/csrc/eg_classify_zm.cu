@@ -261,6 +261,44 @@ __device__ __forceinline__ uint64_t saddle_info(const float (&nb)[14], uint32_t 
     return (uint64_t(b0) << 56) | codes;
 }
 
+// Value of neighbour slot k of column xx of ring row `row` of plane buffer C
+// (D and U at float offsets dD, dU from C), slot order as in ring_nbrs.
+__device__ __forceinline__ float ring_val(const float *row, int xx, int rs, int dD, int dU, int k)
+{
+    // per slot, 2-bit fields: row + 1 and column + 1
+    constexpr uint32_t kRows = (0u << 0) | (0u << 2) | (1u << 4) | (1u << 6) | (0u << 8) | (0u << 10) | (1u << 12) |
+                               (1u << 14) | (2u << 16) | (2u << 18) | (1u << 20) | (1u << 22) | (2u << 24) | (2u << 26);
+    constexpr uint32_t kCols = (0u << 0) | (1u << 2) | (0u << 4) | (1u << 6) | (0u << 8) | (1u << 10) | (0u << 12) |
+                               (2u << 14) | (1u << 16) | (2u << 18) | (1u << 20) | (2u << 22) | (1u << 24) | (2u << 26);
+    const int plane = k < 4 ? dD : (k < 10 ? 0 : dU);
+    const int dy = int((kRows >> (2 * k)) & 3u) - 1, dx = int((kCols >> (2 * k)) & 3u) - 1;
+    return row[plane + dy * rs + zm_col(xx + dx)];
+}
+
+// Highest slot of the non-empty mask m by (value, then rank), values read from
+// the ring one set bit at a time (the minimum graph: lowest value, lowest rank).
+template <bool MIN>
+__device__ __forceinline__ int ring_top(const float *row, int xx, int rs, int dD, int dU, uint32_t m)
+{
+    float best = 0.f;
+    int rk = -1;
+    while (m) {
+        const int k = __ffs(m) - 1;
+        m &= m - 1;
+        const float v = ring_val(row, xx, rs, dD, dU, k);
+        if (rk < 0 || (MIN ? v < best : v >= best)) {
+            best = v;
+            rk = k;
+        }
+    }
+    return rk;
+}
+
+// Record info of a saddle with three or more upper-link components, left for
+// k_saddle_multi: bit 63, the gradient slot in bits 16..19, the upper mask in
+// bits 0..13 (a real info word never has bit 63 set).
+constexpr uint64_t kInfoPending = 1ull << 63;
+
 constexpr int kVx = 8;  // vertices per thread along axis 0
 
 template <bool MIN>
@@ -543,11 +581,22 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
                 uint64_t inf = 0;
                 if (upper) {
                     const uint32_t cls = sl >> 4;
-                    const uint32_t a2 = __ldg(lowc + upper);
-                    float nb[14];
-                    ring_nbrs(orow, int(ox + i), int(rs), dD, dU, nb);
-                    inf = saddle_info<MIN>(nb, upper, int(sl & 15u), cls, a2, lowc);
-                    np += uint32_t(inf >> 56);
+                    const int first = int(sl & 15u);
+                    if (cls == 1) {
+                        // two components: the gradient's, represented by the
+                        // gradient slot, and the other one (the component of
+                        // the mask's lowest set bit, or the rest), whose
+                        // highest vertex is found among its own slots only
+                        const uint32_t a2 = __ldg(lowc + upper);
+                        const uint32_t other = ((a2 >> first) & 1u) ? (upper ^ a2) : a2;
+                        const int rk = ring_top<MIN>(orow, int(ox + i), int(rs), dD, dU, other);
+                        inf = (2ull << 56) | uint64_t(first) | (uint64_t(rk) << 5);
+                        np += 2;
+                    } else {
+                        // three or more (rare): completed by k_saddle_multi,
+                        // which also adds their paths to the brick's count
+                        inf = kInfoPending | (uint64_t(first) << 16) | upper;
+                    }
                 }
                 F.rec_info[q] = inf;
             }
@@ -564,6 +613,65 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
     // drain this item's outstanding (empty) copy groups before the ring is reused
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     }
+}
+
+// Saddles with three or more upper-link components left pending by the
+// plane-marching classifier: one warp per brick finds them among the brick's
+// records, reads their 14 neighbour values from the field (NaN outside the
+// domain), writes the record's info (components and their highest vertices,
+// Sec. 3.4) and adds their paths to the brick's count before scan A.
+template <bool MIN>
+__global__ void __launch_bounds__(256)
+k_saddle_multi(const FieldDev *__restrict__ fields, int nf, uint64_t base, uint64_t bricks,
+               const uint32_t *__restrict__ lut)
+{
+    const int lane = threadIdx.x & 31;
+    const uint64_t t = uint64_t(blockIdx.x) * 8 + (threadIdx.x >> 5);
+    if (t >= bricks) return;
+    const uint64_t g = base + t;
+    const FieldDev &F = fields[find_field<false>(fields, nf, g)];
+    if (F.kd != 3 || F.ty == 0) return;
+    const uint16_t *lowc = reinterpret_cast<const uint16_t *>(lut + 1024);
+    const uint32_t b = uint32_t(g - F.brick0);
+    const uint4 c = F.bcnt[b];
+    const uint32_t nrec = c.x + c.y;
+    const uint64_t slot = uint64_t(b) * F.bcap;
+    const uint32_t n0 = F.n[0], n1 = F.n[1], n2 = F.n[2];
+    uint32_t np = 0;
+    for (uint32_t r = lane; r < nrec; r += 32) {
+        const uint64_t w = F.rec_info[slot + r];
+        if (!(w & kInfoPending)) continue;
+        const uint32_t v = F.rec_sid[slot + r];
+        const uint32_t x = v % n0, t = v / n0, y = t % n1, z = t / n1;
+        float nb[14];
+#pragma unroll
+        for (int k = 0; k < 14; k++) {
+            const uint32_t p = Nbr<3>::pat(k);
+            const int sg = Nbr<3>::neg(k) ? -1 : 1;
+            const int xx = int(x) + sg * int(p & 1u), yy = int(y) + sg * int((p >> 1) & 1u),
+                      zz = int(z) + sg * int((p >> 2) & 1u);
+            const bool in = xx >= 0 && xx < int(n0) && yy >= 0 && yy < int(n1) && zz >= 0 && zz < int(n2);
+            nb[k] = in ? F.f[(uint64_t(uint32_t(zz)) * n1 + uint32_t(yy)) * n0 + uint32_t(xx)]
+                       : __int_as_float(0x7fc00000);
+        }
+        const uint32_t upper = uint32_t(w & 0x3fffu);
+        const int first = int((w >> 16) & 15u);
+        const uint64_t inf = saddle_info<MIN>(nb, upper, first, 2u, __ldg(lowc + upper), lowc);
+        F.rec_info[slot + r] = inf;
+        np += uint32_t(inf >> 56);
+    }
+    np = __reduce_add_sync(0xffffffffu, np);
+    if (lane == 0 && np) atomicAdd(&F.bcnt[b].z, np);
+}
+
+cudaError_t launch_saddle_multi(bool minimum, const FieldDev *fields, int nf, uint64_t base, uint64_t bricks,
+                                const uint32_t *lut, cudaStream_t st)
+{
+    if (bricks == 0) return cudaSuccess;
+    const dim3 grid = dim3(unsigned((bricks + 7) / 8));
+    if (minimum) k_saddle_multi<true><<<grid, 256, 0, st>>>(fields, nf, base, bricks, lut);
+    else k_saddle_multi<false><<<grid, 256, 0, st>>>(fields, nf, base, bricks, lut);
+    return cudaGetLastError();
 }
 
 cudaError_t prepare_classify_zm()

@@ -34,6 +34,10 @@ constexpr uint32_t kZmMaxRow = 2048;
 size_t zm_smem_bytes(uint32_t n0, uint32_t ty);
 // Persistent: grid = min(total_items, sm_count * ctas_per_sm) CTAs take work
 // items from *ticket (zeroed before the launch).
+// Saddles with three or more components left pending by the plane-marching
+// classifier (a group's fields; before scan A).
+cudaError_t launch_saddle_multi(bool minimum, const FieldDev *fields, int nf, uint64_t base, uint64_t bricks,
+                                const uint32_t *lut, cudaStream_t st);
 cudaError_t launch_classify_zm(bool minimum, const FieldDev *fields, int nf, uint64_t total_items, size_t smem,
                                const uint32_t *lut, unsigned long long *ticket, int sm_count, int ctas_per_sm,
                                cudaStream_t st);

@@ -55,6 +55,7 @@ class DeviceResult:
 @dataclass
 class Request:
     values: np.ndarray                 # float32 field, numpy shape = reversed(extents)
+    pinned: object = None              # the same values in a page-locked torch tensor, if given so
     rid: int = 0
     arrival: float = 0.0               # time.perf_counter() when submitted
     admitted: float = 0.0
@@ -107,9 +108,23 @@ class GpuEngine:
         self._staged = None  # event: the last upload has left the staging buffer
 
     def _upload(self, reqs: List[Request]):
-        """Device views of the batch's fields after one host-to-device copy."""
+        """Device views of the batch's fields: fields that arrived in
+        page-locked memory are copied straight from it (one asynchronous copy
+        each); otherwise the batch is staged into the engine's page-locked
+        buffer and travels in one copy."""
         torch = self.torch
         sizes = [r.n for r in reqs]
+        if all(r.pinned is not None for r in reqs):
+            offs = np.concatenate([[0], np.cumsum([(n + 3) & ~3 for n in sizes])])
+            total = int(offs[-1])
+            if self._dev is None or self._dev.numel() < total:
+                self._dev = torch.empty(max(total, 1 << 20), dtype=torch.float32, device=self.device)
+            out = []
+            for r, o in zip(reqs, offs[:-1]):
+                d = self._dev[int(o):int(o) + r.n]
+                d.copy_(r.pinned.view(-1), non_blocking=True)
+                out.append(d.view(r.values.shape))
+            return out
         offs = np.concatenate([[0], np.cumsum([(n + 3) & ~3 for n in sizes])])  # 16-byte aligned fields
         total = int(offs[-1])
         if self._pinned is None or self._pinned.numel() < total:
@@ -180,8 +195,15 @@ class Server:
             t.start()
 
     # ------------------------------------------------------------- client
-    def submit(self, values: np.ndarray) -> Request:
-        r = Request(values=np.ascontiguousarray(values, dtype=np.float32))
+    def submit(self, values) -> Request:
+        """values: a float32 numpy array, or a contiguous float32 torch CPU
+        tensor in page-locked memory (copied to the device without staging)."""
+        if hasattr(values, "is_pinned"):
+            if str(values.dtype) != "torch.float32" or not values.is_contiguous() or values.is_cuda:
+                raise ValueError("a tensor request must be a contiguous float32 CPU tensor")
+            r = Request(values=values.numpy(), pinned=values if values.is_pinned() else None)
+        else:
+            r = Request(values=np.ascontiguousarray(values, dtype=np.float32))
         with self.cv:
             r.rid = self.next_rid
             self.next_rid += 1

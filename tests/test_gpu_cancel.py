@@ -70,6 +70,27 @@ def test_cancel_matches_oracle(eg_mod, case, minimum):
         _check(eg_mod, h, f, minimum)
 
 
+@pytest.mark.parametrize("minimum", [False, True])
+def test_cancel_many_saddles(eg_mod, minimum):
+    """More saddles than the one-CTA tail takes at once (~70 K): the first
+    rounds run over all CTAs, the rest in the tail."""
+    f = F.grf((96, 96, 96), 2)
+    og = oracle.compute(f.values, minimum=minimum)
+    assert og.saddles.size > 40000
+    t = torch.from_numpy(f.values).cuda()
+    with eg_mod.Handle(0, minimum=minimum) as h:
+        rid = h.compute(t)
+        try:
+            spread = float(np.float32(og.max_val.max()) - np.float32(og.max_val.min()))
+            for tau in [float(np.float32(spread * 0.02)), float(np.float32(spread * 0.2)), np.inf]:
+                want = oracle.cancel_graph(og, tau, minimum=minimum)
+                alive, surv, n, rounds = h.get_cancelled(rid, tau)
+                assert np.array_equal(alive, want.alive), tau
+                assert np.array_equal(surv, want.survivor), tau
+        finally:
+            h.release(rid)
+
+
 def test_cancel_on_batched_results(eg_mod):
     fs = [F.white_noise(e, zlib.crc32(repr(e).encode()) % 1000) for e in [(70, 40), (13, 12, 11), (30,), (6, 5, 4, 3)]]
     ts = [torch.from_numpy(f.values).cuda() for f in fs]

@@ -54,6 +54,27 @@ def test_continuous_batching_fifo_and_budget():
     assert st["max_in_flight_batches"] == 2
 
 
+def test_tensor_requests_and_completion_callback():
+    """Requests may arrive as float32 CPU tensors (page-locked ones are marked
+    for a copy without staging); every finished request is handed to the
+    on_done callback once, before its waiter is released."""
+    torch = pytest.importorskip("torch")
+    seen = []
+    eng = [FakeEngine(0.005)]
+    srv = serve.Server(eng, budget_bytes=1 << 30, max_batch=4, on_done=lambda r: seen.append(r.rid))
+    t = torch.arange(1000, dtype=torch.float32).reshape(10, 100)
+    r = srv.submit(t)
+    assert r.pinned is None and r.values.shape == (10, 100) and r.n == 1000
+    with pytest.raises(ValueError):
+        srv.submit(t.to(torch.int32))
+    with pytest.raises(ValueError):
+        srv.submit(t.t())
+    assert srv.drain(10)
+    srv.close()
+    assert r.result == float(np.sum(t.numpy(), dtype=np.float64))
+    assert seen == [r.rid]
+
+
 def test_admission_defers_and_refuses():
     eng = [FakeEngine(0.05)]
     per = serve.request_bytes(1000, 2)
