@@ -259,7 +259,8 @@ bool make_shape(int d, const int64_t *ext, Shape &sh)
 // plane-marching classifier when the rows are short enough, else flat.
 struct Layout {
     int kd;
-    bool zm;
+    bool zm;    // warp-marching classifier (warp brick layout)
+    uint32_t gpr = 0, wpp = 0;
     bool code;  // gradient codes + tiled code resolution (plane-marching fields below 2^31 vertices)
     bool r4;  // 4D row classifier (row layout over (z, w) planes)
     uint32_t ty, nyb, nbricks, bcap, zc, nzc;
@@ -274,29 +275,26 @@ Layout make_layout(const Shape &sh, int sm_count, const eg_config &cfg, uint32_t
     // the plane-marching classifier reads float32 (the field, or the float32
     // image of a narrow integer field); other types take the flat classifier
     const bool f32_values = dtype == kF32 || dtype_narrow(dtype);
-    if (L.kd == 3 && n0 <= kZmMaxRow && f32_values) {
-        // one thread per 8 consecutive vertices of a row, 256 threads per CTA
-        // (rows of more than 1024 vertices: one row per brick)
-        const uint32_t txn = (n0 + 7) / 8;
-        uint32_t ty = 256 / txn;
-        if (cfg.classify_rows >= 1) ty = std::min<uint32_t>(ty, uint32_t(cfg.classify_rows));
-        // rows per brick: the saddle queue of the classifier stores ring rows in 7 bits
-        ty = std::max<uint32_t>(1, std::min(std::min(ty, 126u), n1));
+    if (L.kd == 3 && n0 <= kWMaxRow && f32_values) {
+        // warp layout: rows cut into groups of 8 vertices (one per lane), a
+        // brick is 32 consecutive groups of one plane (one warp's vertices)
         L.zm = true;
-        L.ty = ty;
-        L.nyb = (n1 + ty - 1) / ty;
-        L.nbricks = L.nyb * n2;
-        L.bcap = ty * n0;
+        L.ty = 0;
+        L.nyb = 0;
+        L.gpr = (n0 + 7) / 8;
+        L.wpp = uint32_t((uint64_t(n1) * L.gpr + 31) / 32);
+        L.nbricks = L.wpp * n2;
+        L.bcap = 256;
         if (cfg.classify_planes > 0) {
             L.zc = std::min<uint32_t>(n2, uint32_t(cfg.classify_planes));
         } else {
-            // enough work items to fill the GPU a few times over
-            const uint64_t want = uint64_t(std::max(sm_count, 1)) * 8;
-            const uint32_t nzc = uint32_t(std::min<uint64_t>(n2, std::max<uint64_t>(1, (want + L.nyb - 1) / L.nyb)));
+            // enough work items (one warp each) to fill the GPU a few times over
+            const uint64_t want = uint64_t(std::max(sm_count, 1)) * 64;
+            const uint32_t nzc = uint32_t(std::min<uint64_t>(n2, std::max<uint64_t>(1, (want + L.wpp - 1) / L.wpp)));
             L.zc = (n2 + nzc - 1) / nzc;
         }
         L.nzc = (n2 + L.zc - 1) / L.zc;
-        L.smem = zm_smem_bytes(n0, ty);
+        L.smem = 0;
         L.code = sh.N < (1ull << 31);
     } else if (L.kd == 4 && n0 <= 1024 && f32_values) {
         // 4D row classifier: one thread per kR4Vertices consecutive vertices of
@@ -476,10 +474,10 @@ eg_status enqueue_part(eg_ctx *h, int part, const Plan &P, const FieldDev *Dd, c
         for (size_t gi = 0; gi < P.groups.size(); gi++) {
             const Group &G = P.groups[gi];
             if (G.zm) {
-                e = launch_classify_zm(G.minimum, Dd + G.first, G.count, G.items, G.smem,
-                                       static_cast<const uint32_t *>(h->lut3),
-                                       reinterpret_cast<unsigned long long *>(h->ws_scan) + 2 + zi++, h->sm_count,
-                                       P.ctas, st);
+                e = launch_classify_w(G.minimum, Dd + G.first, G.count, G.items,
+                                      static_cast<const uint32_t *>(h->lut3),
+                                      reinterpret_cast<unsigned long long *>(h->ws_scan) + 2 + zi++, h->sm_count,
+                                      P.ctas, st);
                 if (e == cudaSuccess)
                     e = launch_saddle_multi(G.minimum, Dd + G.first, G.count, G.brick0, G.bricks,
                                             static_cast<const uint32_t *>(h->lut3), st);
@@ -572,7 +570,6 @@ eg_status capture_graphs(eg_ctx *h, const Plan &P, const void *desc_host, GraphE
 {
     cudaError_t e = h->pool.alloc(&E.desc_dev, P.desc_bytes);
     if (e != cudaSuccess) return from_cuda(e);
-    if ((e = prepare_classify_zm()) != cudaSuccess) return from_cuda(e);
     for (int p = 0; p < 3; p++) {
         if ((e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return from_cuda(e);
         eg_status s = enqueue_part(h, p, P, static_cast<const FieldDev *>(E.desc_dev), desc_host, cap, &E.launches[p]);
@@ -683,7 +680,7 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
     Plan P;
     P.nf = nf;
     P.walks = cfg.resolve_walks > 0 ? cfg.resolve_walks : 4;
-    P.ctas = cfg.persistent_ctas > 0 ? cfg.persistent_ctas : 3;
+    P.ctas = cfg.persistent_ctas > 0 ? cfg.persistent_ctas : 2;
     P.sm_count = h->sm_count;
     uint64_t total_recs = 0;
     uint64_t total_xents = 0;  // exit list capacity: the vertices of the code fields
@@ -774,6 +771,8 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
         F.bcap = ly.bcap;
         F.ty = ly.ty;
         F.nyb = ly.nyb;
+        F.gpr = ly.gpr;
+        F.wpp = ly.wpp;
         F.zc = ly.zc;
         F.nzc = ly.nzc;
         F.vec = (j.sh.n[0] % 4 == 0 && (reinterpret_cast<uintptr_t>(F.f) & 15) == 0) ? 1u : 0u;
@@ -791,16 +790,16 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
         F.code = static_cast<uint32_t *>(R.code);
         F.n0p = n0p;
         F.ctile0 = P.total_ctiles;
-        if (ly.code) P.total_ctiles += code_tiles(F.n[0], F.n[1], F.n[2]);
+        if (ly.code) P.total_ctiles += walk_blocks(F.n[0], F.n[1], F.n[2]);
         G.count++;
         G.bricks += ly.nbricks;
-        G.items += ly.zm ? uint64_t(ly.nyb) * ly.nzc : ly.nbricks;
+        G.items += ly.zm ? uint64_t(ly.wpp) * ly.nzc : ly.nbricks;
         G.smem = std::max(G.smem, ly.smem);
         brick0 += ly.nbricks;
         rec0 += uint64_t(ly.nbricks) * ly.bcap;
         tile0 += scan_tiles(ly.nbricks);
         char fs[192];
-        std::snprintf(fs, sizeof fs, "%d,%d,%u,%u,%u,%u,%u,%u,%u,%u,%u,%u,%u,%u;", key(i), ly.kd, F.N, ly.ty, ly.nyb,
+        std::snprintf(fs, sizeof fs, "%d,%d,%u,%u,%u,%u,%u,%u,%u,%u,%u,%u,%u,%u;", key(i), ly.kd, F.N, ly.ty, ly.wpp,
                       ly.nbricks, ly.zc, ly.nzc, F.vec, F.n[0], F.n[1], F.n[2], F.n[3], j.dtype);
         P.signature += fs;
     }
@@ -1292,7 +1291,7 @@ eg_status eg_autotune(eg_handle h, const eg_field_desc *fields, int n, void *str
     h->timing = true;
     eg_config cur = h->cfg;
     if (cur.resolve_walks <= 0) cur.resolve_walks = 4;
-    if (cur.persistent_ctas <= 0) cur.persistent_ctas = 3;
+    if (cur.persistent_ctas <= 0) cur.persistent_ctas = 2;
     float ms[4];
     eg_status s = timed_trial(h, jobs, st, cur, 2, ms);  // also warms the workspace
     float cur_total = ms[3];
@@ -1300,8 +1299,7 @@ eg_status eg_autotune(eg_handle h, const eg_field_desc *fields, int n, void *str
     struct Knob { int32_t eg_config::*field; std::vector<int32_t> values; };
     const std::vector<Knob> knobs = {
         {&eg_config::classify_planes, {0, 16, 32, 64, 128}},
-        {&eg_config::classify_rows, {0, 8, 4, 2}},
-        {&eg_config::persistent_ctas, {2, 3}},
+        {&eg_config::persistent_ctas, {1, 2}},
         {&eg_config::resolve_walks, {2, 4, 8}},
     };
     for (const Knob &k : knobs) {

@@ -26,9 +26,11 @@
 //
 // Bricks: every kernel after classification works on bricks, contiguous
 // ranges of linear vertex ids, in index order.  Flat layout: 1024 ids per
-// brick.  Row layout (2D/3D with axis-0 extent <= 2048, 4D with axis-0 extent
-// <= 1024): `ty` whole rows of one plane per brick (one row when it holds more
-// than 1024 vertices), so brick b = plane b / nyb, row block b % nyb.
+// brick.  Warp layout (2D/3D float32 with axis-0 extent <= 2048): each row is
+// cut into groups of 8 vertices, and a brick is 32 consecutive groups of one
+// plane in row-major order (a contiguous id range of at most 256 vertices).
+// Row layout (4D with axis-0 extent <= 1024): `ty` whole rows of one (z, w)
+// plane per brick, so brick b = plane b / nyb, row block b % nyb.
 #pragma once
 #include <cstdint>
 #include <type_traits>
@@ -229,7 +231,9 @@ struct FieldDev {
     uint32_t N;              // vertex count (< 2^32)
     uint32_t nbricks;
     uint32_t bcap;           // record slot capacity per brick (= brick size)
-    uint32_t ty;             // rows per brick (0: flat layout)
+    uint32_t ty;             // rows per brick (0: flat or warp layout)
+    uint32_t gpr;            // warp layout: groups of 8 vertices per row (ceil(n0 / 8))
+    uint32_t wpp;            // warp layout: warps (bricks) per plane, 0 for other layouts
     uint32_t nyb;            // row blocks per plane (row layout)
     uint32_t zc;             // planes per classification work item (row layout)
     uint32_t nzc;            // work items along the slowest axis (row layout)
@@ -258,7 +262,18 @@ __host__ __device__ __forceinline__ uint64_t code_word(uint32_t n0p, uint64_t ro
 
 __host__ __device__ __forceinline__ void brick_range(const FieldDev &F, uint32_t b, uint64_t &v0, uint32_t &len)
 {
-    if (F.ty == 0) {
+    if (F.wpp) {
+        // warp layout: brick = plane p, groups [32 w, 32 w + 32) of its row-major
+        // groups of 8 vertices (whole rows are split only at group boundaries)
+        const uint32_t p = b / F.wpp, w = b - p * F.wpp;
+        const uint64_t G = uint64_t(F.n[1]) * F.gpr;
+        const uint64_t g0 = uint64_t(w) * 32, g1 = (g0 + 32 < G ? g0 + 32 : G) - 1;
+        const uint64_t r0 = g0 / F.gpr, r1 = g1 / F.gpr;
+        const uint64_t x0 = 8 * (g0 - r0 * F.gpr), x1 = 8 * (g1 - r1 * F.gpr) + 8;
+        const uint64_t plane = uint64_t(p) * F.n[1];
+        v0 = (plane + r0) * F.n[0] + x0;
+        len = uint32_t((plane + r1) * F.n[0] + (x1 < F.n[0] ? x1 : F.n[0]) - v0);
+    } else if (F.ty == 0) {
         v0 = uint64_t(b) * kFlatBrick;
         const uint64_t rem = uint64_t(F.N) - v0;
         len = rem < kFlatBrick ? uint32_t(rem) : uint32_t(kFlatBrick);

@@ -151,8 +151,8 @@ k_resolve_tile(const FieldDev *__restrict__ fields, int nf)
         else hi = mid - 1;
     }
     const FieldDev &F = fields[lo];
-    // dense maxima: short paths, the brick walks are faster on their own
-    if (F.kd != 3 || F.code || uint64_t(F.totals[0]) * 100 >= uint64_t(F.N)) return;
+    // dense maxima: short paths, the walks are faster on their own
+    if (F.kd != 3 || uint64_t(F.totals[0]) * 100 >= uint64_t(F.N)) return;
     const uint32_t lx = F.rt[0], ly = F.rt[1], lz = F.rt[2];
     const uint32_t TX = 1u << lx, TY = 1u << ly, T = 1u << (lx + ly + lz);
     const uint32_t n0 = F.n[0], n1 = F.n[1], n2 = F.n[2];
@@ -171,13 +171,21 @@ k_resolve_tile(const FieldDev *__restrict__ fields, int nf)
     auto gid = [&](uint32_t i) {
         return (z0 + (i >> (lx + ly))) * s2 + (y0 + ((i >> lx) & (TY - 1))) * s1 + x0 + (i & (TX - 1));
     };
+    // gradient target of tile vertex i: its pointer, or decoded from its code
+    auto target = [&](uint32_t i) {
+        const uint32_t v = gid(i);
+        if (!F.code) return lab[v];
+        const uint32_t row = (z0 + (i >> (lx + ly))) * n1 + y0 + ((i >> lx) & (TY - 1)), x = x0 + (i & (TX - 1));
+        const uint32_t c = (F.code[code_word(F.n0p, row, x)] >> ((x & 7u) * 4u)) & 15u;
+        return c == kCodeMax ? v : slot_vertex<3>(v, int(c), F.s);
+    };
     // 1: tile-local gradient targets (every thread runs the same trip counts)
     for (uint32_t i0 = 0; i0 < T; i0 += kTb * kTileThreads) {
         uint32_t a[kTb];
 #pragma unroll
         for (int b = 0; b < kTb; b++) {
             const uint32_t i = i0 + b * kTileThreads + threadIdx.x;
-            a[b] = inside(i) ? lab[gid(i)] : 0u;
+            a[b] = inside(i) ? target(i) : 0u;
         }
 #pragma unroll
         for (int b = 0; b < kTb; b++) {
@@ -221,66 +229,44 @@ k_resolve_tile(const FieldDev *__restrict__ fields, int nf)
         if (!__syncthreads_or(changed)) break;
     }
     // 3: the label of every vertex that ends on a maximum; for the others the
-    // first vertex outside the tile: their terminal's gradient target, still
-    // in lab[] (terminals keep their entry)
+    // first vertex outside the tile: their terminal's gradient target (with
+    // pointers, terminals keep their entry; with codes every vertex is written)
     for (uint32_t i0 = 0; i0 < T; i0 += kTb * kTileThreads) {
 #pragma unroll
         for (int b = 0; b < kTb; b++) {
             const uint32_t i = i0 + b * kTileThreads + threadIdx.x;
             const uint16_t w = s_w[i];
-            if (inside(i) && (w & kIdx) != i) lab[gid(i)] = (w & kOut) ? lab[gid(w & kIdx)] : gid(w & kIdx);
+            if (!inside(i)) continue;
+            if (F.code) lab[gid(i)] = (w & kOut) ? target(w & kIdx) : gid(w & kIdx);
+            else if ((w & kIdx) != i) lab[gid(i)] = (w & kOut) ? lab[gid(w & kIdx)] : gid(w & kIdx);
         }
     }
 }
 
 // ---------------------------------------------------------------------------
-// Resolution from gradient codes (fields classified by the plane-marching
-// kernel): one CTA per tile of 32 x 16 x 16 vertices (32 x 256 in 2D).  The
-// CTA copies the 4-bit codes of the tile and of a halo of kCodeHalo vertices
-// on every side into shared memory, one byte per vertex; cells outside the
-// field and the outermost layer of the halo are marked kShell.  Every vertex
-// of the tile then follows its gradient path through shared memory: a path
-// that reaches a maximum gives the label; a path that reaches the shell leaves
-// the tile's neighbourhood, and the vertex gets that shell vertex with
-// kLabelExit set and goes on the exit list.  Paths are short on most fields,
-// so the halo keeps most of them inside; k_resolve_exits follows the rest,
-// from exit to exit (each crossing at least kCodeHalo + 1 steps), to a label.
+// Resolution of code fields (gradients as 4-bit codes): one thread per group
+// of 8 consecutive vertices of a row (the classifier's groups; one code word).
+// Fields with dense maxima (short paths): the 8 gradient paths are followed
+// through the codes in lock-step (the code array is 1/8 of the pointers', so
+// it mostly stays in L2); a path still going after kWalkCap steps leaves its
+// current vertex with kLabelExit set and goes on the exit list, which
+// k_resolve_exits finishes.  Fields with few maxima (long paths) had the tiled
+// pass first, which left a label or the first vertex outside its tile in
+// every entry of lab[]: the walks follow lab[] to a fixed point.
 // ---------------------------------------------------------------------------
-constexpr int kCodeThreads = 256;
-constexpr int kCodeHalo = 4;
-constexpr int kCodeIlp = 4;
-constexpr uint8_t kShell = 0xff;
-constexpr uint32_t kCodeSmem3 = (32 + 2 * kCodeHalo) * (16 + 2 * kCodeHalo) * (16 + 2 * kCodeHalo);
-constexpr uint32_t kCodeSmem2 = (32 + 2 * kCodeHalo) * (256 + 2 * kCodeHalo);
-constexpr uint32_t kCodeSmem = kCodeSmem3 > kCodeSmem2 ? kCodeSmem3 : kCodeSmem2;
+constexpr int kWalkThreads = 256;
+constexpr int kWalkCap = 64;
 
-// log2 of the core tile extents of a code field
-__host__ __device__ __forceinline__ void code_tile_shape(uint32_t n2, uint32_t &lx, uint32_t &ly, uint32_t &lz)
+uint64_t walk_blocks(uint32_t n0, uint32_t n1, uint32_t n2)
 {
-    lx = 5;
-    if (n2 > 1) {
-        ly = 4;
-        lz = 4;
-    } else {
-        ly = 8;
-        lz = 0;
-    }
+    const uint64_t groups = uint64_t((n0 + 7) / 8) * n1 * n2;
+    return (groups + kWalkThreads - 1) / kWalkThreads;
 }
 
-uint64_t code_tiles(uint32_t n0, uint32_t n1, uint32_t n2)
+__global__ void __launch_bounds__(kWalkThreads)
+k_resolve_cwalk(const FieldDev *__restrict__ fields, int nf, uint64_t *xlist, unsigned long long *xcount)
 {
-    uint32_t lx, ly, lz;
-    code_tile_shape(n2, lx, ly, lz);
-    return ((uint64_t(n0) + (1u << lx) - 1) >> lx) * ((uint64_t(n1) + (1u << ly) - 1) >> ly) *
-           ((uint64_t(n2) + (1u << lz) - 1) >> lz);
-}
-
-__global__ void __launch_bounds__(kCodeThreads)
-k_resolve_codes(const FieldDev *__restrict__ fields, int nf, uint64_t *xlist, unsigned long long *xcount)
-{
-    __shared__ uint8_t s_c[kCodeSmem];
-    __shared__ int32_t s_loff[14];
-    __shared__ uint32_t s_goff[14];
+    __shared__ uint32_t s_coff[14], s_voff[14];
     const uint64_t g = blockIdx.x;
     int fi = 0;
     {
@@ -294,114 +280,111 @@ k_resolve_codes(const FieldDev *__restrict__ fields, int nf, uint64_t *xlist, un
     }
     const FieldDev &F = fields[fi];
     if (!F.code) return;
-    uint32_t lx, ly, lz;
-    code_tile_shape(F.n[2], lx, ly, lz);
-    const uint32_t n0 = F.n[0], n1 = F.n[1], n2 = F.n[2];
-    const int H = kCodeHalo;
-    const int HZ = n2 > 1 ? kCodeHalo : 0;
-    const int EX = (1 << lx) + 2 * H, EY = (1 << ly) + 2 * H, EZ = (1 << lz) + 2 * HZ;
-    const uint32_t ntx = (n0 + (1u << lx) - 1) >> lx, nty = (n1 + (1u << ly) - 1) >> ly;
-    uint32_t t = uint32_t(g - F.ctile0);
-    const uint32_t tx = t % ntx;
-    t /= ntx;
-    const uint32_t tyi = t % nty, tz = t / nty;
-    const int x0 = int(tx << lx), y0 = int(tyi << ly), z0 = int(tz << lz);
-    const int tid = threadIdx.x;
+    const uint32_t n0 = F.n[0], n1 = F.n[1], n0p = F.n0p, gpr = (n0 + 7) / 8;
+    const int tid = threadIdx.x, lane = tid & 31;
     if (tid < 14) {
         const uint32_t p = Nbr<3>::pat(tid);
-        const int lo = int(p & 1u) + EX * int((p >> 1) & 1u) + EX * EY * int((p >> 2) & 1u);
-        const uint32_t go = (p & 1u) + ((p & 2u) ? F.s[1] : 0u) + ((p & 4u) ? F.s[2] : 0u);
-        s_loff[tid] = Nbr<3>::neg(tid) ? -lo : lo;
-        s_goff[tid] = Nbr<3>::neg(tid) ? 0u - go : go;
-    }
-    // 1: codes of the tile and its halo, one byte per cell (each extended row
-    // spans the 6 code words from x0 - 8 to x0 + 40)
-    const int nrows = EY * EZ;
-    const int wpr = ((1 << lx) + 16) / 8;  // words per extended row
-    const int xw0 = (x0 - 8) >> 3;          // first word (may be -1)
-    for (int i = tid; i < nrows * wpr; i += kCodeThreads) {
-        const int row = i / wpr, wi = i - row * wpr;
-        const int ry = row % EY, rz = row / EY;
-        const int gy = y0 - H + ry, gz = z0 - HZ + rz;
-        const int w = xw0 + wi;
-        const bool rowin = gy >= 0 && gy < int(n1) && gz >= 0 && gz < int(n2);
-        const bool win = rowin && w >= 0 && w < int(F.n0p >> 3);
-        const uint32_t word = win ? F.code[(uint64_t(uint32_t(gz)) * n1 + uint32_t(gy)) * (F.n0p >> 3) + uint32_t(w)] : 0u;
-        const bool edge_yz = ry == 0 || ry == EY - 1 || (HZ && (rz == 0 || rz == EZ - 1));
-#pragma unroll
-        for (int j = 0; j < 8; j++) {
-            const int gx = 8 * w + j, ux = gx - (x0 - H);
-            if (ux < 0 || ux >= EX) continue;
-            const bool in = win && gx < int(n0);
-            const bool shell = !in || edge_yz || ux == 0 || ux == EX - 1;
-            s_c[(rz * EY + ry) * EX + ux] = shell ? kShell : uint8_t((word >> (4 * j)) & 15u);
-        }
+        const uint32_t co = (p & 1u) + ((p & 2u) ? n0p : 0u) + ((p & 4u) ? n0p * n1 : 0u);
+        const uint32_t vo = (p & 1u) + ((p & 2u) ? n0 : 0u) + ((p & 4u) ? n0 * n1 : 0u);
+        s_coff[tid] = Nbr<3>::neg(tid) ? 0u - co : co;
+        s_voff[tid] = Nbr<3>::neg(tid) ? 0u - vo : vo;
     }
     __syncthreads();
-    // 2: walks from every vertex of the tile (kCodeIlp in lock-step)
-    const uint32_t T = 1u << (lx + ly + lz);
-    const uint32_t s1 = F.s[1], s2 = F.s[2];
+    const uint64_t gi = (g - F.ctile0) * kWalkThreads + uint64_t(tid);
+    const bool valid = gi < uint64_t(gpr) * n1 * F.n[2];
+    const uint32_t row = valid ? uint32_t(gi / gpr) : 0u, x = valid ? 8u * uint32_t(gi - uint64_t(row) * gpr) : 0u;
+    const uint32_t nv = valid ? min(8u, n0 - x) : 0u;
+    const uint32_t vrow = row * n0 + x;
     uint32_t *lab = F.lab;
-    const int lane = tid & 31;
-    for (uint32_t base = 0; base < T; base += kCodeIlp * kCodeThreads) {
-        int u[kCodeIlp];
-        uint32_t gv[kCodeIlp], gu[kCodeIlp];
-        uint32_t live = 0, inmask = 0;
+    uint32_t v[8];
+    uint32_t live = 0;
+    if (uint64_t(F.totals[0]) * 100 < uint64_t(F.N)) {
+        // after the tiled pass: follow lab[] (a label is a fixed point)
 #pragma unroll
-        for (int q = 0; q < kCodeIlp; q++) {
-            const uint32_t i = base + uint32_t(q * kCodeThreads + tid);
-            const uint32_t cx = i & ((1u << lx) - 1), cy = (i >> lx) & ((1u << ly) - 1), cz = i >> (lx + ly);
-            const uint32_t gx = uint32_t(x0) + cx, gy = uint32_t(y0) + cy, gz = uint32_t(z0) + cz;
-            u[q] = int(cx + H) + EX * (int(cy + H) + EY * int(cz + HZ));
-            gv[q] = gx + gy * s1 + gz * s2;
-            gu[q] = gv[q];
-            if (i < T && gx < n0 && gy < n1 && gz < n2) {
-                inmask |= 1u << q;
-                live |= 1u << q;
+        for (int i = 0; i < 8; i++) {
+            v[i] = vrow + i;
+            if (uint32_t(i) < nv) {
+                const uint32_t u = lab[vrow + i];
+                if (u != vrow + i) {
+                    v[i] = u;
+                    live |= 1u << i;
+                }
             }
         }
-        uint32_t exits = 0, steps = 0;
+        const uint32_t moved = live;
+        uint32_t steps = 0;
         while (live) {
 #pragma unroll
-            for (int q = 0; q < kCodeIlp; q++)
-                if ((live >> q) & 1u) {
-                    const uint32_t c = s_c[u[q]];
-                    if (c == kCodeMax) {
-                        live &= ~(1u << q);
-                    } else if (c == kShell) {
-                        live &= ~(1u << q);
-                        exits |= 1u << q;
-                    } else {
-                        u[q] += s_loff[c];
-                        gu[q] += s_goff[c];
-                    }
+            for (int i = 0; i < 8; i++)
+                if ((live >> i) & 1u) {
+                    const uint32_t w = lab[v[i]];
+                    if (w == v[i]) live &= ~(1u << i);
+                    else v[i] = w;
                 }
-            if (++steps > uint32_t(EX * EY * EZ)) {  // a path visits each cell once
+            if (++steps > F.N) {
                 atomicOr(F.err, kErrNotConverged);
                 break;
             }
         }
 #pragma unroll
-        for (int q = 0; q < kCodeIlp; q++) {
-            const bool ex = (exits >> q) & 1u;
-            if ((inmask >> q) & 1u) lab[gv[q]] = ex ? (gu[q] | kLabelExit) : gu[q];
-            // exit list: warp-aggregated append
-            const unsigned m = __ballot_sync(0xffffffffu, ex);
-            if (m) {
-                unsigned long long b0 = 0;
-                if (lane == __ffs(m) - 1) b0 = atomicAdd(xcount, (unsigned long long)__popc(m));
-                b0 = __shfl_sync(0xffffffffu, b0, __ffs(m) - 1);
-                if (ex) xlist[b0 + __popc(m & ((1u << lane) - 1u))] = (uint64_t(uint32_t(fi)) << 32) | gv[q];
-            }
+        for (int i = 0; i < 8; i++)
+            if ((moved >> i) & 1u) lab[vrow + i] = v[i];
+        return;
+    }
+    // dense maxima: walk the codes
+    uint32_t ci[8];
+    const uint32_t crow = row * n0p + x;
+    const uint32_t w0 = valid ? F.code[crow >> 3] : 0xffffffffu;
+#pragma unroll
+    for (int i = 0; i < 8; i++) {
+        const uint32_t c = (w0 >> (4 * i)) & 15u;
+        v[i] = vrow + i;
+        ci[i] = crow + i;
+        if (uint32_t(i) < nv && c != kCodeMax) {
+            ci[i] += s_coff[c];
+            v[i] += s_voff[c];
+            live |= 1u << i;
         }
     }
+    for (int step = 1; live && step < kWalkCap; step++) {
+#pragma unroll
+        for (int i = 0; i < 8; i++)
+            if ((live >> i) & 1u) {
+                const uint32_t c = (F.code[ci[i] >> 3] >> ((ci[i] & 7u) * 4u)) & 15u;
+                if (c == kCodeMax) {
+                    live &= ~(1u << i);
+                } else {
+                    ci[i] += s_coff[c];
+                    v[i] += s_voff[c];
+                }
+            }
+    }
+    // walks still going: their current vertex lies on the path; k_resolve_exits
+    // continues from its entry
+#pragma unroll
+    for (int i = 0; i < 8; i++)
+        if (uint32_t(i) < nv) lab[vrow + i] = ((live >> i) & 1u) ? (v[i] | kLabelExit) : v[i];
+    const uint32_t ne = __popc(live);
+    uint32_t inc = ne;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
+    if (tot == 0) return;
+    unsigned long long b0 = 0;
+    if (lane == 31) b0 = atomicAdd(xcount, (unsigned long long)tot);
+    b0 = __shfl_sync(0xffffffffu, b0, 31) + (inc - ne);
+    for (uint32_t m = live; m; m &= m - 1)
+        xlist[b0++] = (uint64_t(uint32_t(fi)) << 32) | (vrow + uint32_t(__ffs(m) - 1));
 }
 
 // Vertices whose path left the neighbourhood of their tile: follow exits to a
 // label (every vertex carries its label or an exit by now).  Concurrent
 // threads may replace an exit by the label on the same path: either leads to
 // the same maximum.
-__global__ void __launch_bounds__(kCodeThreads)
+__global__ void __launch_bounds__(kWalkThreads)
 k_resolve_exits(const FieldDev *__restrict__ fields, const uint64_t *xlist, const unsigned long long *xcount)
 {
     const unsigned long long n = *xcount;
@@ -427,12 +410,12 @@ k_resolve_exits(const FieldDev *__restrict__ fields, const uint64_t *xlist, cons
     }
 }
 
-cudaError_t launch_resolve_codes(const FieldDev *fields, int nf, uint64_t tiles, uint64_t *xlist,
+cudaError_t launch_resolve_codes(const FieldDev *fields, int nf, uint64_t blocks, uint64_t *xlist,
                                  unsigned long long *xcount, int sm_count, cudaStream_t st)
 {
-    if (tiles == 0) return cudaSuccess;
-    k_resolve_codes<<<dim3(static_cast<unsigned>(tiles)), kCodeThreads, 0, st>>>(fields, nf, xlist, xcount);
-    k_resolve_exits<<<dim3(unsigned(std::max(sm_count, 1) * 8)), kCodeThreads, 0, st>>>(fields, xlist, xcount);
+    if (blocks == 0) return cudaSuccess;
+    k_resolve_cwalk<<<dim3(static_cast<unsigned>(blocks)), kWalkThreads, 0, st>>>(fields, nf, xlist, xcount);
+    k_resolve_exits<<<dim3(unsigned(std::max(sm_count, 1) * 8)), kWalkThreads, 0, st>>>(fields, xlist, xcount);
     return cudaGetLastError();
 }
 
