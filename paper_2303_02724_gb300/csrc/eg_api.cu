@@ -570,6 +570,7 @@ eg_status capture_graphs(eg_ctx *h, const Plan &P, const void *desc_host, GraphE
 {
     cudaError_t e = h->pool.alloc(&E.desc_dev, P.desc_bytes);
     if (e != cudaSuccess) return from_cuda(e);
+    if ((e = prepare_classify_w()) != cudaSuccess) return from_cuda(e);
     for (int p = 0; p < 3; p++) {
         if ((e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return from_cuda(e);
         eg_status s = enqueue_part(h, p, P, static_cast<const FieldDev *>(E.desc_dev), desc_host, cap, &E.launches[p]);

@@ -33,6 +33,8 @@
 // are read again from L1); a saddle with three or more is completed by
 // k_saddle_multi.  The minimum graph mirrors every comparison and the tie
 // rule.
+#include <atomic>
+
 #include "eg_internal.cuh"
 #include "eg_kernels.h"
 
@@ -169,30 +171,85 @@ struct WGeom {
     bool vec;  // rows start on 16-byte boundaries (n0 % 4 == 0, aligned field)
 };
 
-// Columns x-1 .. x+8 of row (yy, zz), NaN outside the field.  Every lane of
-// the warp calls it (the end columns come from the neighbouring lanes).
-__device__ __forceinline__ void load_row(const WGeom &G, bool valid, int yy, int zz, uint32_t x, bool first_t,
-                                         bool last_t, int lane, float (&v)[10])
+__device__ __forceinline__ void cp_async16(float *smem, const float *gmem)
+{
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(float *smem, const float *gmem)
+{
+    const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Per-warp staging of one plane: three row tracks (rows y-1, y, y+1 of every
+// lane), each 32 lanes x 8 values plus the two end columns of the warp (x-1 of
+// lane 0, x+8 of lane 31).  A lane's two 16-byte halves are stored swapped
+// when bit 2 of the lane is set, so the eight lanes of a quarter-warp read
+// distinct banks.
+constexpr int kTrack = 32 * kVx + 4;  // (the two end columns, padded to 16 bytes)
+constexpr int kSlot = 3 * kTrack;
+
+__device__ __forceinline__ int half_pos(int lane, int i) { return ((i & 4) ^ (((lane >> 2) & 1) << 2)) | (i & 3); }
+
+// Copy rows y-1, y, y+1 of plane zz into a slot (NaN outside the field);
+// always commits one group of asynchronous copies.
+__device__ __forceinline__ void stage_plane(const WGeom &G, float *slot, bool valid, int y, int zz, uint32_t x,
+                                            bool first_t, bool last_t, int lane)
 {
     const float qnan = __int_as_float(0x7fc00000);
-    const bool in = valid && yy >= 0 && yy < int(G.n1) && zz >= 0 && zz < int(G.n2);
-    const float *row = G.f + (in ? (uint64_t(uint32_t(zz)) * G.n1 + uint32_t(yy)) * G.n0 : 0ull);
-    if (in && G.vec && x + kVx <= G.n0) {
-        const float4 a = __ldg(reinterpret_cast<const float4 *>(row + x));
-        const float4 b = __ldg(reinterpret_cast<const float4 *>(row + x + 4));
-        v[1] = a.x; v[2] = a.y; v[3] = a.z; v[4] = a.w;
-        v[5] = b.x; v[6] = b.y; v[7] = b.z; v[8] = b.w;
-    } else {
 #pragma unroll
-        for (int i = 0; i < kVx; i++) v[1 + i] = (in && x + i < G.n0) ? __ldg(row + x + i) : qnan;
+    for (int t = 0; t < 3; t++) {
+        const int yy = y - 1 + t;
+        float *dst = slot + t * kTrack;
+        float *mine = dst + lane * kVx;
+        const bool in = valid && yy >= 0 && yy < int(G.n1) && zz >= 0 && zz < int(G.n2);
+        const float *row = G.f + (in ? (uint64_t(uint32_t(zz)) * G.n1 + uint32_t(yy)) * G.n0 : 0ull);
+        if (in && G.vec && x + kVx <= G.n0) {
+            const int h = ((lane >> 2) & 1) << 2;
+            cp_async16(mine + h, row + x);
+            cp_async16(mine + (h ^ 4), row + x + 4);
+        } else {
+#pragma unroll
+            for (int i = 0; i < kVx; i++) {
+                if (in && x + i < G.n0) cp_async4(mine + half_pos(lane, i), row + x + i);
+                else mine[half_pos(lane, i)] = qnan;
+            }
+        }
+        if (lane == 0) {
+            if (in && !first_t) cp_async4(dst + 32 * kVx, row + x - 1);
+            else dst[32 * kVx] = qnan;
+        }
+        if (lane == 31) {
+            if (in && !last_t) cp_async4(dst + 32 * kVx + 1, row + x + kVx);
+            else dst[32 * kVx + 1] = qnan;
+        }
     }
+    cp_async_commit();
+}
+
+// Columns x-1 .. x+8 of one staged row track (end columns from the
+// neighbouring lanes, or the warp's end columns).
+__device__ __forceinline__ void read_row(const float *src, int lane, bool first_t, bool last_t, float (&v)[10])
+{
+    const float qnan = __int_as_float(0x7fc00000);
+    const int h = ((lane >> 2) & 1) << 2;
+    const float4 a = *reinterpret_cast<const float4 *>(src + lane * kVx + h);
+    const float4 b = *reinterpret_cast<const float4 *>(src + lane * kVx + (h ^ 4));
+    v[1] = a.x; v[2] = a.y; v[3] = a.z; v[4] = a.w;
+    v[5] = b.x; v[6] = b.y; v[7] = b.z; v[8] = b.w;
     float l = __shfl_up_sync(kFull, v[8], 1);
     float r = __shfl_down_sync(kFull, v[1], 1);
-    if (lane == 0 && in && !first_t) l = __ldg(row + x - 1);
-    if (lane == 31 && in && !last_t) r = __ldg(row + x + kVx);
+    if (lane == 0) l = src[32 * kVx];
+    if (lane == 31) r = src[32 * kVx + 1];
     v[0] = first_t ? qnan : l;
     v[9] = last_t ? qnan : r;
 }
+
+__device__ __forceinline__ int warp_slot_base(int warp) { return warp * 3 * kSlot; }
+constexpr size_t kWSmemDyn = size_t(kWWarps) * 3 * kSlot * sizeof(float);
 
 template <bool MIN>
 __global__ void __launch_bounds__(kWThreads, 2)
@@ -205,6 +262,9 @@ k_classify_w(const FieldDev *__restrict__ fields, int nf, const uint32_t *__rest
     // 14 neighbour offsets of the current field
     __shared__ __align__(16) uint32_t s_um[kWWarps][32 * kVx];
     __shared__ uint32_t s_off[kWWarps][14];
+    // per warp: planes z-1, z, z+1 staged (slot = plane mod 3)
+    extern __shared__ __align__(16) float w_smem[];
+    float *stage = w_smem + warp_slot_base(threadIdx.x >> 5);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint16_t *lowc = reinterpret_cast<const uint16_t *>(lut + 1024);
     for (int i = tid; i < 1024; i += kWThreads) s_lut[i] = __ldg(lut + i);
@@ -237,19 +297,30 @@ k_classify_w(const FieldDev *__restrict__ fields, int nf, const uint32_t *__rest
         const uint32_t y = valid ? gi / gpr : 0u, xg = valid ? gi - y * gpr : 0u, x = kVx * xg;
         const bool first_t = xg == 0, last_t = !valid || xg + 1 == gpr;
         bool anynan = false;
+        auto slot_of = [&](int p) { return stage + ((p + 3) % 3) * kSlot; };
+        stage_plane(G, slot_of(zs - 1), valid, int(y), zs - 1, x, first_t, last_t, lane);
+        stage_plane(G, slot_of(zs), valid, int(y), zs, x, first_t, last_t, lane);
+        stage_plane(G, slot_of(zs + 1), valid, int(y), zs + 1, x, first_t, last_t, lane);
 
         for (int z = zs; z < ze; z++) {
             const uint32_t brick = uint32_t(z) * wpp + w;
             const uint32_t vrow = uint32_t((uint64_t(uint32_t(z)) * G.n1 + y) * G.n0) + x;
             // rows: A = y-1, B = y, C = y+1; D = plane z-1, C = plane z, U = plane z+1
             float DA[10], DB[10], CA[10], CB[10], CC[10], UB[10], UC[10];
-            load_row(G, valid, int(y) - 1, z - 1, x, first_t, last_t, lane, DA);
-            load_row(G, valid, int(y), z - 1, x, first_t, last_t, lane, DB);
-            load_row(G, valid, int(y) - 1, z, x, first_t, last_t, lane, CA);
-            load_row(G, valid, int(y), z, x, first_t, last_t, lane, CB);
-            load_row(G, valid, int(y) + 1, z, x, first_t, last_t, lane, CC);
-            load_row(G, valid, int(y), z + 1, x, first_t, last_t, lane, UB);
-            load_row(G, valid, int(y) + 1, z + 1, x, first_t, last_t, lane, UC);
+            cp_async_wait0();  // plane z+1 (the last one staged) has landed
+            __syncwarp();
+            {
+                const float *Ds = slot_of(z - 1), *Cs = slot_of(z), *Us = slot_of(z + 1);
+                read_row(Ds, lane, first_t, last_t, DA);
+                read_row(Ds + kTrack, lane, first_t, last_t, DB);
+                read_row(Cs, lane, first_t, last_t, CA);
+                read_row(Cs + kTrack, lane, first_t, last_t, CB);
+                read_row(Cs + 2 * kTrack, lane, first_t, last_t, CC);
+                read_row(Us + kTrack, lane, first_t, last_t, UB);
+                read_row(Us + 2 * kTrack, lane, first_t, last_t, UC);
+            }
+            __syncwarp();  // every lane has read plane z-1's slot: plane z+2 may replace it
+            if (z + 1 < ze) stage_plane(G, slot_of(z + 2), valid, int(y), z + 2, x, first_t, last_t, lane);
             uint32_t um[kVx];
             uint32_t crit = 0, nm = 0, code = 0;
 #pragma unroll
@@ -392,6 +463,8 @@ k_classify_w(const FieldDev *__restrict__ fields, int nf, const uint32_t *__rest
             __syncwarp();  // s_um is rewritten on the next plane
         }
         if (__any_sync(kFull, anynan) && lane == 0) atomicOr(F.err, kErrNaN);
+        cp_async_wait0();  // nothing in flight into the staging slots
+        __syncwarp();
     }
 }
 
@@ -453,6 +526,24 @@ cudaError_t launch_saddle_multi(bool minimum, const FieldDev *fields, int nf, ui
     return cudaGetLastError();
 }
 
+cudaError_t prepare_classify_w()
+{
+    // the staging slots take more than the default 48 KB: raise the limit,
+    // once per device
+    static std::atomic<uint64_t> done_mask{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = 1ull << (dev & 63);
+    if (done_mask.load() & bit) return cudaSuccess;
+    for (auto kern : {k_classify_w<false>, k_classify_w<true>})
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kWSmemDyn))) !=
+            cudaSuccess)
+            return e;
+    done_mask.fetch_or(bit);
+    return cudaSuccess;
+}
+
 cudaError_t launch_classify_w(bool minimum, const FieldDev *fields, int nf, uint64_t total_items, const uint32_t *lut,
                               unsigned long long *ticket, int sm_count, int ctas_per_sm, cudaStream_t st)
 {
@@ -462,7 +553,9 @@ cudaError_t launch_classify_w(bool minimum, const FieldDev *fields, int nf, uint
     uint64_t grid = uint64_t(sm_count > 0 ? sm_count : 1) * uint64_t(ctas_per_sm > 0 ? ctas_per_sm : 2);
     const uint64_t need = (total_items + kWWarps - 1) / kWWarps;
     if (grid > need) grid = need;
-    kern<<<dim3(unsigned(grid)), kWThreads, 0, st>>>(fields, nf, lut, total_items, ticket);
+    cudaError_t e = prepare_classify_w();
+    if (e != cudaSuccess) return e;
+    kern<<<dim3(unsigned(grid)), kWThreads, kWSmemDyn, st>>>(fields, nf, lut, total_items, ticket);
     return cudaGetLastError();
 }
 

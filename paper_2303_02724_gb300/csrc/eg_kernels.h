@@ -35,6 +35,9 @@ cudaError_t launch_widen(uint32_t dtype, const FieldDev *field, uint64_t n, int 
 constexpr uint32_t kWMaxRow = 2048;
 cudaError_t launch_classify_w(bool minimum, const FieldDev *fields, int nf, uint64_t total_items, const uint32_t *lut,
                               unsigned long long *ticket, int sm_count, int ctas_per_sm, cudaStream_t st);
+// Raise the classifier's shared-memory limit on the current device (also done
+// by launch_classify_w; call it before capturing a graph).
+cudaError_t prepare_classify_w();
 // Saddles with three or more components left pending by the warp-marching
 // classifier (a group's fields and bricks; before scan A).
 cudaError_t launch_saddle_multi(bool minimum, const FieldDev *fields, int nf, uint64_t base, uint64_t bricks,

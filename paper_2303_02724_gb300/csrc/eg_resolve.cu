@@ -331,39 +331,56 @@ k_resolve_cwalk(const FieldDev *__restrict__ fields, int nf, uint64_t *xlist, un
             if ((moved >> i) & 1u) lab[vrow + i] = v[i];
         return;
     }
-    // dense maxima: walk the codes
-    uint32_t ci[8];
+    // dense maxima: walk the codes, two walks in flight per lane; a slot whose
+    // walk ends (a maximum, or the step cap) takes the lane's next vertex, so
+    // the lane's time is the sum of its 8 walks, not 8 times the longest
     const uint32_t crow = row * n0p + x;
     const uint32_t w0 = valid ? F.code[crow >> 3] : 0xffffffffu;
-#pragma unroll
-    for (int i = 0; i < 8; i++) {
-        const uint32_t c = (w0 >> (4 * i)) & 15u;
-        v[i] = vrow + i;
-        ci[i] = crow + i;
-        if (uint32_t(i) < nv && c != kCodeMax) {
-            ci[i] += s_coff[c];
-            v[i] += s_voff[c];
-            live |= 1u << i;
+    const uint32_t *code = F.code;
+    uint32_t next = 0;
+    uint32_t sj[2], sci[2], sv[2], sh[2];
+    bool act[2];
+    auto start = [&](int k) {
+        act[k] = false;
+        while (next < nv) {
+            const uint32_t j = next++;
+            const uint32_t c = (w0 >> (4 * j)) & 15u;
+            if (c == kCodeMax) {
+                lab[vrow + j] = vrow + j;  // a maximum labels itself
+                continue;
+            }
+            sj[k] = j;
+            sci[k] = crow + j + s_coff[c];
+            sv[k] = vrow + j + s_voff[c];
+            sh[k] = 1;
+            act[k] = true;
+            return;
         }
-    }
-    for (int step = 1; live && step < kWalkCap; step++) {
+    };
+    start(0);
+    start(1);
+    while (act[0] || act[1]) {
 #pragma unroll
-        for (int i = 0; i < 8; i++)
-            if ((live >> i) & 1u) {
-                const uint32_t c = (F.code[ci[i] >> 3] >> ((ci[i] & 7u) * 4u)) & 15u;
+        for (int k = 0; k < 2; k++)
+            if (act[k]) {
+                const uint32_t c = (code[sci[k] >> 3] >> ((sci[k] & 7u) * 4u)) & 15u;
                 if (c == kCodeMax) {
-                    live &= ~(1u << i);
+                    lab[vrow + sj[k]] = sv[k];
+                    start(k);
+                } else if (sh[k] >= kWalkCap) {
+                    // still going: the current vertex lies on the path;
+                    // k_resolve_exits continues from its entry
+                    lab[vrow + sj[k]] = sv[k] | kLabelExit;
+                    live |= 1u << sj[k];
+                    start(k);
                 } else {
-                    ci[i] += s_coff[c];
-                    v[i] += s_voff[c];
+                    sci[k] += s_coff[c];
+                    sv[k] += s_voff[c];
+                    sh[k]++;
                 }
             }
     }
-    // walks still going: their current vertex lies on the path; k_resolve_exits
-    // continues from its entry
-#pragma unroll
-    for (int i = 0; i < 8; i++)
-        if (uint32_t(i) < nv) lab[vrow + i] = ((live >> i) & 1u) ? (v[i] | kLabelExit) : v[i];
+    // exit list (warp-aggregated)
     const uint32_t ne = __popc(live);
     uint32_t inc = ne;
 #pragma unroll
