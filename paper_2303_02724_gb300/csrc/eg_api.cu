@@ -210,6 +210,8 @@ struct eg_ctx {
     uint64_t ws_tiles = 0;
     void *ws_xlist = nullptr;  // exit list of the code resolver (one u64 per entry)
     uint64_t ws_xcap = 0;
+    void *ws_mlist = nullptr;  // pending multi-saddles of the classifier (one u64 per entry)
+    uint64_t ws_mcap = 0;
     void *lut3 = nullptr;  // saddle class table of the 3D link graph + two-component table
     void *stage = nullptr;  // device staging for eg_compute_host
     size_t stage_bytes = 0;
@@ -295,7 +297,7 @@ Layout make_layout(const Shape &sh, int sm_count, const eg_config &cfg, uint32_t
         }
         L.nzc = (n2 + L.zc - 1) / L.zc;
         L.smem = 0;
-        L.code = sh.N < (1ull << 31);
+        L.code = false;
     } else if (L.kd == 4 && n0 <= 1024 && f32_values) {
         // 4D row classifier: one thread per kR4Vertices consecutive vertices of
         // a row, ty whole rows of one (z, w) plane per brick
@@ -337,7 +339,12 @@ eg_status grow(eg_ctx *h, void **p, uint64_t &cap, uint64_t want, size_t elem)
 
 eg_status ensure_workspace(eg_ctx *h, uint64_t recs, uint64_t bricks, uint64_t tiles, uint64_t xents)
 {
-    if (recs <= h->ws_rec_cap && bricks <= h->ws_bricks && tiles <= h->ws_tiles && xents <= h->ws_xcap)
+    // pending multi-saddles: a sixteenth of the record slots (saddles with
+    // three or more components are far rarer; the classifier completes the
+    // overflow itself)
+    const uint64_t ments = recs / 16 + 1024;
+    if (recs <= h->ws_rec_cap && bricks <= h->ws_bricks && tiles <= h->ws_tiles && xents <= h->ws_xcap &&
+        ments <= h->ws_mcap)
         return EG_OK;
     // earlier computations may still use the old workspace
     cudaEventSynchronize(h->ws_free);
@@ -371,6 +378,14 @@ eg_status ensure_workspace(eg_ctx *h, uint64_t recs, uint64_t bricks, uint64_t t
         }
         (void)t;
         h->ws_tiles = c;
+    }
+    if (ments > h->ws_mcap) {
+        h->pool.release(h->ws_mlist);
+        h->ws_mlist = nullptr;
+        h->ws_mcap = 0;
+        cudaError_t e = h->pool.alloc(&h->ws_mlist, ments * sizeof(uint64_t));
+        if (e != cudaSuccess) return from_cuda(e);
+        h->ws_mcap = ments;
     }
     if (xents > h->ws_xcap) {
         h->pool.release(h->ws_xlist);
@@ -435,7 +450,8 @@ struct Plan {
     std::vector<Group> groups;
     uint64_t total_bricks = 0, total_tiles = 0;
     uint64_t total_rtiles = 0;  // tiled resolution pass (3D kernels)
-    uint64_t total_ctiles = 0;  // code resolver tiles (code fields)
+    uint64_t total_ctiles = 0;  // group walkers of the warp-layout fields (CTAs)
+    uint64_t chase_bricks = 0;  // bricks of the other fields (brick walkers)
     size_t desc_bytes = 0;
     int walks = 4, ctas = 3;
     int sm_count = 0;
@@ -447,6 +463,7 @@ struct Plan {
 // (slots 0-1: scan tickets; 2..: one work-queue ticket per plane-marching
 // group, of which there are at most four: two row classes x two graphs).
 constexpr int kXcountSlot = 31;
+constexpr int kMcountSlot = 30;  // pending multi-saddle count
 
 // Enqueue one phase of the pipeline on st, reading descriptors from Dd:
 //   0: descriptor upload, scan state reset, counters reset, classification
@@ -470,24 +487,27 @@ eg_status enqueue_part(eg_ctx *h, int part, const Plan &P, const FieldDev *Dd, c
             if ((e = launch_widen(t.dtype, Dd + t.pos, t.n, P.sm_count, st)) != cudaSuccess) return from_cuda(e);
             nl++;
         }
-        int zi = 0;  // work-queue tickets of the plane-marching groups: header slots 2, 3, ...
+        int zi = 0;  // work-queue tickets of the warp-marching groups: header slots 2, 3, ...
+        unsigned long long *mcount = reinterpret_cast<unsigned long long *>(h->ws_scan) + kMcountSlot;
         for (size_t gi = 0; gi < P.groups.size(); gi++) {
             const Group &G = P.groups[gi];
             if (G.zm) {
                 e = launch_classify_w(G.minimum, Dd + G.first, G.count, G.items,
                                       static_cast<const uint32_t *>(h->lut3),
                                       reinterpret_cast<unsigned long long *>(h->ws_scan) + 2 + zi++, h->sm_count,
-                                      P.ctas, st);
-                if (e == cudaSuccess)
-                    e = launch_saddle_multi(G.minimum, Dd + G.first, G.count, G.brick0, G.bricks,
-                                            static_cast<const uint32_t *>(h->lut3), st);
-                nl++;
+                                      P.ctas, G.first, static_cast<uint64_t *>(h->ws_mlist), mcount, h->ws_mcap, st);
             } else if (G.r4) {
                 e = launch_classify_r4(G.minimum, Dd + G.first, G.count, G.bricks, st);
             } else {
                 e = launch_classify_flat(G.kd, G.cdt, Dd + G.first, G.count, G.bricks, st);
             }
             if (e != cudaSuccess) return from_cuda(e);
+            nl++;
+        }
+        if (zi) {  // pending multi-saddles of the warp-marching groups
+            if ((e = launch_saddle_multi(Dd, static_cast<const uint64_t *>(h->ws_mlist), mcount, h->ws_mcap,
+                                         static_cast<const uint32_t *>(h->lut3), h->sm_count, st)) != cudaSuccess)
+                return from_cuda(e);
             nl++;
         }
         if ((e = launch_scan(false, Dd, P.nf, P.total_tiles, h->ws_scan, st)) != cudaSuccess) return from_cuda(e);
@@ -497,8 +517,10 @@ eg_status enqueue_part(eg_ctx *h, int part, const Plan &P, const FieldDev *Dd, c
             if ((e = launch_resolve_tiles(Dd, P.nf, P.total_rtiles, st)) != cudaSuccess) return from_cuda(e);
             nl++;
         }
-        if ((e = launch_resolve(Dd, P.nf, P.total_bricks, P.walks, st)) != cudaSuccess) return from_cuda(e);
-        nl++;
+        if (P.chase_bricks) {  // (warp-layout fields are resolved below)
+            if ((e = launch_resolve(Dd, P.nf, P.total_bricks, P.walks, st)) != cudaSuccess) return from_cuda(e);
+            nl++;
+        }
         if (P.total_ctiles) {
             unsigned long long *xcount = reinterpret_cast<unsigned long long *>(h->ws_scan) + kXcountSlot;
             if ((e = launch_resolve_codes(Dd, P.nf, P.total_ctiles, static_cast<uint64_t *>(h->ws_xlist), xcount,
@@ -791,7 +813,8 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
         F.code = static_cast<uint32_t *>(R.code);
         F.n0p = n0p;
         F.ctile0 = P.total_ctiles;
-        if (ly.code) P.total_ctiles += walk_blocks(F.n[0], F.n[1], F.n[2]);
+        if (ly.zm) P.total_ctiles += walk_blocks(F.n[0], F.n[1], F.n[2]);
+        else P.chase_bricks += ly.nbricks;
         G.count++;
         G.bricks += ly.nbricks;
         G.items += ly.zm ? uint64_t(ly.wpp) * ly.nzc : ly.nbricks;

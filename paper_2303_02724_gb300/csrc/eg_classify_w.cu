@@ -33,6 +33,7 @@
 // are read again from L1); a saddle with three or more is completed by
 // k_saddle_multi.  The minimum graph mirrors every comparison and the tie
 // rule.
+#include <algorithm>
 #include <atomic>
 
 #include "eg_internal.cuh"
@@ -164,6 +165,26 @@ __device__ __forceinline__ void slot_step(int k, int &dx, int &dy, int &dz)
     dz = sg * int((p >> 2) & 1u);
 }
 
+// Info word of a saddle with three or more upper-link components, from its 14
+// neighbour values read from the field (NaN outside the domain).
+template <bool MIN>
+__device__ __forceinline__ uint64_t multi_info(const FieldDev &F, uint32_t v, uint64_t pending, const uint16_t *lowc)
+{
+    const uint32_t n0 = F.n[0], n1 = F.n[1], n2 = F.n[2];
+    const uint32_t x = v % n0, t = v / n0, y = t % n1, z = t / n1;
+    float nb[14];
+#pragma unroll
+    for (int k = 0; k < 14; k++) {
+        int dx, dy, dz;
+        slot_step(k, dx, dy, dz);
+        const int xx = int(x) + dx, yy = int(y) + dy, zz = int(z) + dz;
+        const bool in = xx >= 0 && xx < int(n0) && yy >= 0 && yy < int(n1) && zz >= 0 && zz < int(n2);
+        nb[k] = in ? F.f[(uint64_t(uint32_t(zz)) * n1 + uint32_t(yy)) * n0 + uint32_t(xx)] : __int_as_float(0x7fc00000);
+    }
+    const uint32_t upper = uint32_t(pending & 0x3fffu);
+    return saddle_info<MIN>(nb, upper, int((pending >> 16) & 15u), 2u, __ldg(lowc + upper), lowc);
+}
+
 // The warp's view of one field.
 struct WGeom {
     const float *f;
@@ -254,7 +275,7 @@ constexpr size_t kWSmemDyn = size_t(kWWarps) * 3 * kSlot * sizeof(float);
 template <bool MIN>
 __global__ void __launch_bounds__(kWThreads, 2)
 k_classify_w(const FieldDev *__restrict__ fields, int nf, const uint32_t *__restrict__ lut, uint64_t total_items,
-             unsigned long long *ticket)
+             unsigned long long *ticket, int fbase, uint64_t *mlist, unsigned long long *mcount, uint64_t mcap)
 {
     __shared__ uint32_t s_lut[1024];
     // per warp: the classification word of every vertex of the current plane
@@ -274,7 +295,8 @@ k_classify_w(const FieldDev *__restrict__ fields, int nf, const uint32_t *__rest
         if (lane == 0) g = atomicAdd(ticket, 1ull);
         g = __shfl_sync(kFull, g, 0);
         if (g >= total_items) break;
-        const FieldDev &F = fields[find_field<true>(fields, nf, g)];
+        const int fi = find_field<true>(fields, nf, g);
+        const FieldDev &F = fields[fi];
         const uint32_t item = uint32_t(g - F.item0);
         const uint32_t wpp = F.wpp, gpr = F.gpr;
         const uint32_t w = item % wpp, zci = item / wpp;
@@ -373,11 +395,19 @@ k_classify_w(const FieldDev *__restrict__ fields, int nf, const uint32_t *__rest
                 if (F.code) {
                     F.code[code_word(F.n0p, uint64_t(uint32_t(z)) * G.n1 + y, x)] = code;
                 } else {
+                    uint32_t a[kVx];
 #pragma unroll
                     for (int i = 0; i < kVx; i++)
-                        if (x + i < G.n0)
-                            F.lab[vrow + i] = (um[i] & 0x3fffu) ? vrow + i + s_off[warp][(um[i] >> 14) & 15u]
-                                                                : vrow + i;
+                        a[i] = (um[i] & 0x3fffu) ? vrow + i + s_off[warp][(um[i] >> 14) & 15u] : vrow + i;
+                    if (G.vec && x + kVx <= G.n0) {  // (vrow is a multiple of 4 then)
+                        uint4 *dst = reinterpret_cast<uint4 *>(F.lab + vrow);
+                        dst[0] = make_uint4(a[0], a[1], a[2], a[3]);
+                        dst[1] = make_uint4(a[4], a[5], a[6], a[7]);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < kVx; i++)
+                            if (x + i < G.n0) F.lab[vrow + i] = a[i];
+                    }
                 }
             }
             uint4 *um4 = reinterpret_cast<uint4 *>(&s_um[warp][lane * kVx]);
@@ -410,6 +440,8 @@ k_classify_w(const FieldDev *__restrict__ fields, int nf, const uint32_t *__rest
                 }
                 const uint32_t ocrit = __shfl_sync(kFull, crit, own);
                 const uint32_t ovrow = __shfl_sync(kFull, vrow, own);
+                bool pend = false;
+                uint64_t q = 0;
                 if (j < cw) {
                     // vertex i of the owner: its (j - own_excl)-th critical vertex
                     uint32_t k = j - own_excl, mk = ocrit, i = 0;
@@ -421,7 +453,7 @@ k_classify_w(const FieldDev *__restrict__ fields, int nf, const uint32_t *__rest
                     const uint32_t wd = s_um[warp][own * kVx + i];
                     const uint32_t upper = wd & 0x3fffu, sl = wd >> 14;
                     const uint32_t v = ovrow + i;
-                    const uint64_t q = slot0 + j;
+                    q = slot0 + j;
                     F.rec_sid[q] = v;
                     F.rec_val[q] = __ldg(G.f + v);
                     uint64_t inf = 0;
@@ -453,9 +485,27 @@ k_classify_w(const FieldDev *__restrict__ fields, int nf, const uint32_t *__rest
                             // three or more (rare): completed by k_saddle_multi,
                             // which also adds their paths to the brick's count
                             inf = kInfoPending | (uint64_t(first) << 16) | upper;
+                            pend = true;
                         }
                     }
                     F.rec_info[q] = inf;
+                }
+                // pending records onto the list (warp-aggregated); if it is
+                // full, the record is completed here from the field
+                const unsigned pm = __ballot_sync(kFull, pend);
+                if (pm) {
+                    unsigned long long at = 0;
+                    if (lane == __ffs(pm) - 1) at = atomicAdd(mcount, (unsigned long long)__popc(pm));
+                    at = __shfl_sync(kFull, at, __ffs(pm) - 1) + __popc(pm & ((1u << lane) - 1u));
+                    if (pend) {
+                        if (at < mcap) {
+                            mlist[at] = (uint64_t(fbase + fi) << 40) | q;
+                        } else {
+                            const uint64_t inf = multi_info<MIN>(F, F.rec_sid[q], F.rec_info[q], lowc);
+                            F.rec_info[q] = inf;
+                            np += uint32_t(inf >> 56);
+                        }
+                    }
                 }
             }
             np = __reduce_add_sync(kFull, np);
@@ -469,60 +519,33 @@ k_classify_w(const FieldDev *__restrict__ fields, int nf, const uint32_t *__rest
 }
 
 // Saddles with three or more upper-link components left pending by the
-// classifier: one warp per brick finds them among the brick's records, reads
-// their 14 neighbour values from the field (NaN outside the domain), writes
-// the record's info (components and their highest vertices, Sec. 3.4) and
-// adds their paths to the brick's count before scan A.
-template <bool MIN>
+// classifier (the list holds field << 40 | record slot): their record info
+// (components and their highest vertices, Sec. 3.4), and their paths added
+// to their brick's count, before scan A.
 __global__ void __launch_bounds__(256)
-k_saddle_multi(const FieldDev *__restrict__ fields, int nf, uint64_t base, uint64_t bricks,
-               const uint32_t *__restrict__ lut)
+k_saddle_multi(const FieldDev *__restrict__ fields, const uint64_t *mlist, const unsigned long long *mcount,
+               uint64_t mcap, const uint32_t *__restrict__ lut)
 {
-    const int lane = threadIdx.x & 31;
-    const uint64_t t = uint64_t(blockIdx.x) * 8 + (threadIdx.x >> 5);
-    if (t >= bricks) return;
-    const uint64_t g = base + t;
-    const FieldDev &F = fields[find_field<false>(fields, nf, g)];
-    if (F.kd != 3 || F.wpp == 0) return;
     const uint16_t *lowc = reinterpret_cast<const uint16_t *>(lut + 1024);
-    const uint32_t b = uint32_t(g - F.brick0);
-    const uint4 c = F.bcnt[b];
-    const uint32_t nrec = c.x + c.y;
-    const uint64_t slot = uint64_t(b) * F.bcap;
-    const uint32_t n0 = F.n[0], n1 = F.n[1], n2 = F.n[2];
-    uint32_t np = 0;
-    for (uint32_t r = lane; r < nrec; r += 32) {
-        const uint64_t w = F.rec_info[slot + r];
-        if (!(w & kInfoPending)) continue;
-        const uint32_t v = F.rec_sid[slot + r];
-        const uint32_t x = v % n0, tt = v / n0, y = tt % n1, z = tt / n1;
-        float nb[14];
-#pragma unroll
-        for (int k = 0; k < 14; k++) {
-            int dx, dy, dz;
-            slot_step(k, dx, dy, dz);
-            const int xx = int(x) + dx, yy = int(y) + dy, zz = int(z) + dz;
-            const bool in = xx >= 0 && xx < int(n0) && yy >= 0 && yy < int(n1) && zz >= 0 && zz < int(n2);
-            nb[k] = in ? F.f[(uint64_t(uint32_t(zz)) * n1 + uint32_t(yy)) * n0 + uint32_t(xx)]
-                       : __int_as_float(0x7fc00000);
-        }
-        const uint32_t upper = uint32_t(w & 0x3fffu);
-        const int first = int((w >> 16) & 15u);
-        const uint64_t inf = saddle_info<MIN>(nb, upper, first, 2u, __ldg(lowc + upper), lowc);
-        F.rec_info[slot + r] = inf;
-        np += uint32_t(inf >> 56);
+    unsigned long long n = *mcount;
+    if (n > mcap) n = mcap;
+    for (unsigned long long i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += uint64_t(gridDim.x) * blockDim.x) {
+        const uint64_t e = mlist[i];
+        const FieldDev &F = fields[uint32_t(e >> 40)];
+        const uint64_t q = e & ((1ull << 40) - 1);
+        const uint64_t inf = (F.flags & kFlagMinimum) ? multi_info<true>(F, F.rec_sid[q], F.rec_info[q], lowc)
+                                                      : multi_info<false>(F, F.rec_sid[q], F.rec_info[q], lowc);
+        F.rec_info[q] = inf;
+        atomicAdd(&F.bcnt[q / F.bcap].z, uint32_t(inf >> 56));
     }
-    np = __reduce_add_sync(kFull, np);
-    if (lane == 0 && np) atomicAdd(&F.bcnt[b].z, np);
 }
 
-cudaError_t launch_saddle_multi(bool minimum, const FieldDev *fields, int nf, uint64_t base, uint64_t bricks,
-                                const uint32_t *lut, cudaStream_t st)
+cudaError_t launch_saddle_multi(const FieldDev *fields, const uint64_t *mlist, const unsigned long long *mcount,
+                                uint64_t mcap, const uint32_t *lut, int sm_count, cudaStream_t st)
 {
-    if (bricks == 0) return cudaSuccess;
-    const dim3 grid = dim3(unsigned((bricks + 7) / 8));
-    if (minimum) k_saddle_multi<true><<<grid, 256, 0, st>>>(fields, nf, base, bricks, lut);
-    else k_saddle_multi<false><<<grid, 256, 0, st>>>(fields, nf, base, bricks, lut);
+    const dim3 grid = dim3(unsigned(std::max(sm_count, 1) * 2));
+    k_saddle_multi<<<grid, 256, 0, st>>>(fields, mlist, mcount, mcap, lut);
     return cudaGetLastError();
 }
 
@@ -545,7 +568,8 @@ cudaError_t prepare_classify_w()
 }
 
 cudaError_t launch_classify_w(bool minimum, const FieldDev *fields, int nf, uint64_t total_items, const uint32_t *lut,
-                              unsigned long long *ticket, int sm_count, int ctas_per_sm, cudaStream_t st)
+                              unsigned long long *ticket, int sm_count, int ctas_per_sm, int fbase, uint64_t *mlist,
+                              unsigned long long *mcount, uint64_t mcap, cudaStream_t st)
 {
     if (total_items == 0) return cudaSuccess;
     auto kern = minimum ? k_classify_w<true> : k_classify_w<false>;
@@ -555,7 +579,8 @@ cudaError_t launch_classify_w(bool minimum, const FieldDev *fields, int nf, uint
     if (grid > need) grid = need;
     cudaError_t e = prepare_classify_w();
     if (e != cudaSuccess) return e;
-    kern<<<dim3(unsigned(grid)), kWThreads, kWSmemDyn, st>>>(fields, nf, lut, total_items, ticket);
+    kern<<<dim3(unsigned(grid)), kWThreads, kWSmemDyn, st>>>(fields, nf, lut, total_items, ticket, fbase, mlist,
+                                                           mcount, mcap);
     return cudaGetLastError();
 }
 

@@ -34,15 +34,16 @@ cudaError_t launch_widen(uint32_t dtype, const FieldDev *field, uint64_t n, int 
 // every warp takes work items from *ticket (zeroed before the launch).
 constexpr uint32_t kWMaxRow = 2048;
 cudaError_t launch_classify_w(bool minimum, const FieldDev *fields, int nf, uint64_t total_items, const uint32_t *lut,
-                              unsigned long long *ticket, int sm_count, int ctas_per_sm, cudaStream_t st);
+                              unsigned long long *ticket, int sm_count, int ctas_per_sm, int fbase, uint64_t *mlist,
+                              unsigned long long *mcount, uint64_t mcap, cudaStream_t st);
+// Saddles with three or more components left pending by the warp-marching
+// classifier: the list mlist[min(*mcount, mcap)] of (absolute field index in
+// `fields` << 40 | record slot); before scan A.
+cudaError_t launch_saddle_multi(const FieldDev *fields, const uint64_t *mlist, const unsigned long long *mcount,
+                                uint64_t mcap, const uint32_t *lut, int sm_count, cudaStream_t st);
 // Raise the classifier's shared-memory limit on the current device (also done
 // by launch_classify_w; call it before capturing a graph).
 cudaError_t prepare_classify_w();
-// Saddles with three or more components left pending by the warp-marching
-// classifier (a group's fields and bricks; before scan A).
-cudaError_t launch_saddle_multi(bool minimum, const FieldDev *fields, int nf, uint64_t base, uint64_t bricks,
-                                const uint32_t *lut, cudaStream_t st);
-
 // Zero the totals and status word of every field of a launch.
 cudaError_t launch_init_fields(const FieldDev *fields, int nf, cudaStream_t st);
 

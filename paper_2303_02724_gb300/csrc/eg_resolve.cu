@@ -28,7 +28,7 @@ constexpr int kResolveThreads = 256;
 template <int kIlp>
 __device__ __forceinline__ void resolve_brick(const FieldDev &F, uint32_t b)
 {
-    if (F.code) return;  // resolved by the code tiles (below)
+    if (F.wpp) return;  // warp-layout fields: resolved by k_resolve_cwalk
     uint64_t v0;
     uint32_t len;
     brick_range(F, b, v0, len);
@@ -279,7 +279,7 @@ k_resolve_cwalk(const FieldDev *__restrict__ fields, int nf, uint64_t *xlist, un
         fi = lo;
     }
     const FieldDev &F = fields[fi];
-    if (!F.code) return;
+    if (!F.wpp) return;
     const uint32_t n0 = F.n[0], n1 = F.n[1], n0p = F.n0p, gpr = (n0 + 7) / 8;
     const int tid = threadIdx.x, lane = tid & 31;
     if (tid < 14) {
@@ -298,8 +298,9 @@ k_resolve_cwalk(const FieldDev *__restrict__ fields, int nf, uint64_t *xlist, un
     uint32_t *lab = F.lab;
     uint32_t v[8];
     uint32_t live = 0;
-    if (uint64_t(F.totals[0]) * 100 < uint64_t(F.N)) {
-        // after the tiled pass: follow lab[] (a label is a fixed point)
+    if (!F.code || uint64_t(F.totals[0]) * 100 < uint64_t(F.N)) {
+        // gradient pointers, or after the tiled pass (labels or the first
+        // vertex outside a tile): follow lab[] to a fixed point (a maximum)
 #pragma unroll
         for (int i = 0; i < 8; i++) {
             v[i] = vrow + i;
