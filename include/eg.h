@@ -102,11 +102,11 @@ typedef enum eg_dtype {
  * not a knob. */
 typedef struct eg_config {
     uint32_t flags;
-    int32_t classify_rows;    /* unused (kept so the structure keeps its layout)         */
-    int32_t classify_planes;  /* planes one work item of the 2D/3D classifier marches over */
+    int32_t classify_rows;    /* 2D/3D classification tile: grid rows per tile (brick)   */
+    int32_t classify_planes;  /* planes one work item of the classifier marches over     */
     int32_t resolve_walks;    /* gradient walks each resolver thread keeps in flight:
                                  2, 4 or 8                                               */
-    int32_t persistent_ctas;  /* CTAs per SM of the persistent 2D/3D classifier          */
+    int32_t persistent_ctas;  /* CTAs per SM of the persistent classifier work queue     */
     int32_t reserved[3];
 } eg_config;
 

@@ -163,7 +163,6 @@ struct Result {
     void *maxima = nullptr, *max_val = nullptr, *saddles = nullptr, *sad_b0 = nullptr, *sad_val = nullptr,
          *row_ptr = nullptr, *col = nullptr, *ends = nullptr, *ucnt = nullptr;
     void *path_ptr = nullptr, *path_vtx = nullptr, *pbrick = nullptr;  // arc geometry (EG_FLAG_PATHS)
-    void *code = nullptr;   // 4-bit gradient codes (until the result completes)
     uint64_t M = 0, S = 0, P = 0, A = 0, V = 0;
     bool have_A = false;
     uint32_t err = 0;
@@ -208,10 +207,6 @@ struct eg_ctx {
     uint64_t ws_bricks = 0;
     void *ws_scan = nullptr;
     uint64_t ws_tiles = 0;
-    void *ws_xlist = nullptr;  // exit list of the code resolver (one u64 per entry)
-    uint64_t ws_xcap = 0;
-    void *ws_mlist = nullptr;  // pending multi-saddles of the classifier (one u64 per entry)
-    uint64_t ws_mcap = 0;
     void *lut3 = nullptr;  // saddle class table of the 3D link graph + two-component table
     void *stage = nullptr;  // device staging for eg_compute_host
     size_t stage_bytes = 0;
@@ -261,9 +256,7 @@ bool make_shape(int d, const int64_t *ext, Shape &sh)
 // plane-marching classifier when the rows are short enough, else flat.
 struct Layout {
     int kd;
-    bool zm;    // warp-marching classifier (warp brick layout)
-    uint32_t gpr = 0, wpp = 0;
-    bool code;  // gradient codes + tiled code resolution (plane-marching fields below 2^31 vertices)
+    bool zm;
     bool r4;  // 4D row classifier (row layout over (z, w) planes)
     uint32_t ty, nyb, nbricks, bcap, zc, nzc;
     size_t smem;
@@ -277,27 +270,29 @@ Layout make_layout(const Shape &sh, int sm_count, const eg_config &cfg, uint32_t
     // the plane-marching classifier reads float32 (the field, or the float32
     // image of a narrow integer field); other types take the flat classifier
     const bool f32_values = dtype == kF32 || dtype_narrow(dtype);
-    if (L.kd == 3 && n0 <= kWMaxRow && f32_values) {
-        // warp layout: rows cut into groups of 8 vertices (one per lane), a
-        // brick is 32 consecutive groups of one plane (one warp's vertices)
+    if (L.kd == 3 && n0 <= kZmMaxRow && f32_values) {
+        // one thread per 8 consecutive vertices of a row, 256 threads per CTA
+        // (rows of more than 1024 vertices: one row per brick)
+        const uint32_t txn = (n0 + 7) / 8;
+        uint32_t ty = 256 / txn;
+        if (cfg.classify_rows >= 1) ty = std::min<uint32_t>(ty, uint32_t(cfg.classify_rows));
+        // rows per brick: the saddle queue of the classifier stores ring rows in 7 bits
+        ty = std::max<uint32_t>(1, std::min(std::min(ty, 126u), n1));
         L.zm = true;
-        L.ty = 0;
-        L.nyb = 0;
-        L.gpr = (n0 + 7) / 8;
-        L.wpp = uint32_t((uint64_t(n1) * L.gpr + 31) / 32);
-        L.nbricks = L.wpp * n2;
-        L.bcap = 256;
+        L.ty = ty;
+        L.nyb = (n1 + ty - 1) / ty;
+        L.nbricks = L.nyb * n2;
+        L.bcap = ty * n0;
         if (cfg.classify_planes > 0) {
             L.zc = std::min<uint32_t>(n2, uint32_t(cfg.classify_planes));
         } else {
-            // enough work items (one warp each) to fill the GPU a few times over
-            const uint64_t want = uint64_t(std::max(sm_count, 1)) * 64;
-            const uint32_t nzc = uint32_t(std::min<uint64_t>(n2, std::max<uint64_t>(1, (want + L.wpp - 1) / L.wpp)));
+            // enough work items to fill the GPU a few times over
+            const uint64_t want = uint64_t(std::max(sm_count, 1)) * 8;
+            const uint32_t nzc = uint32_t(std::min<uint64_t>(n2, std::max<uint64_t>(1, (want + L.nyb - 1) / L.nyb)));
             L.zc = (n2 + nzc - 1) / nzc;
         }
         L.nzc = (n2 + L.zc - 1) / L.zc;
-        L.smem = 0;
-        L.code = false;
+        L.smem = zm_smem_bytes(n0, ty);
     } else if (L.kd == 4 && n0 <= 1024 && f32_values) {
         // 4D row classifier: one thread per kR4Vertices consecutive vertices of
         // a row, ty whole rows of one (z, w) plane per brick
@@ -337,15 +332,9 @@ eg_status grow(eg_ctx *h, void **p, uint64_t &cap, uint64_t want, size_t elem)
     return EG_OK;
 }
 
-eg_status ensure_workspace(eg_ctx *h, uint64_t recs, uint64_t bricks, uint64_t tiles, uint64_t xents)
+eg_status ensure_workspace(eg_ctx *h, uint64_t recs, uint64_t bricks, uint64_t tiles)
 {
-    // pending multi-saddles: a sixteenth of the record slots (saddles with
-    // three or more components are far rarer; the classifier completes the
-    // overflow itself)
-    const uint64_t ments = recs / 16 + 1024;
-    if (recs <= h->ws_rec_cap && bricks <= h->ws_bricks && tiles <= h->ws_tiles && xents <= h->ws_xcap &&
-        ments <= h->ws_mcap)
-        return EG_OK;
+    if (recs <= h->ws_rec_cap && bricks <= h->ws_bricks && tiles <= h->ws_tiles) return EG_OK;
     // earlier computations may still use the old workspace
     cudaEventSynchronize(h->ws_free);
     h->ws_gen++;
@@ -379,31 +368,13 @@ eg_status ensure_workspace(eg_ctx *h, uint64_t recs, uint64_t bricks, uint64_t t
         (void)t;
         h->ws_tiles = c;
     }
-    if (ments > h->ws_mcap) {
-        h->pool.release(h->ws_mlist);
-        h->ws_mlist = nullptr;
-        h->ws_mcap = 0;
-        cudaError_t e = h->pool.alloc(&h->ws_mlist, ments * sizeof(uint64_t));
-        if (e != cudaSuccess) return from_cuda(e);
-        h->ws_mcap = ments;
-    }
-    if (xents > h->ws_xcap) {
-        h->pool.release(h->ws_xlist);
-        h->ws_xlist = nullptr;
-        h->ws_xcap = 0;
-        const uint64_t c = std::max<uint64_t>(xents, 1024);
-        cudaError_t e = h->pool.alloc(&h->ws_xlist, c * sizeof(uint64_t));
-        if (e != cudaSuccess) return from_cuda(e);
-        h->ws_xcap = c;
-    }
     return EG_OK;
 }
 
 void free_result_buffers(eg_ctx *h, Result *r)
 {
     void **bufs[] = {&r->lab, &r->maxima,   &r->max_val,  &r->saddles, &r->sad_b0, &r->sad_val, &r->row_ptr,
-                     &r->col, &r->ends,     &r->ucnt,     &r->path_ptr, &r->path_vtx, &r->pbrick, &r->wide,
-                     &r->code};
+                     &r->col, &r->ends,     &r->ucnt,     &r->path_ptr, &r->path_vtx, &r->pbrick, &r->wide};
     for (void **b : bufs) {
         h->pool.release(*b);
         *b = nullptr;
@@ -450,20 +421,12 @@ struct Plan {
     std::vector<Group> groups;
     uint64_t total_bricks = 0, total_tiles = 0;
     uint64_t total_rtiles = 0;  // tiled resolution pass (3D kernels)
-    uint64_t total_ctiles = 0;  // group walkers of the warp-layout fields (CTAs)
-    uint64_t chase_bricks = 0;  // bricks of the other fields (brick walkers)
     size_t desc_bytes = 0;
     int walks = 4, ctas = 3;
     int sm_count = 0;
     std::vector<TypedField> widen;   // narrow integer fields: float32 image before classification
     std::string signature;  // identical for calls that can share a captured graph
 };
-
-// Header slot of the scan workspace holding the code resolver's exit count
-// (slots 0-1: scan tickets; 2..: one work-queue ticket per plane-marching
-// group, of which there are at most four: two row classes x two graphs).
-constexpr int kXcountSlot = 31;
-constexpr int kMcountSlot = 30;  // pending multi-saddle count
 
 // Enqueue one phase of the pipeline on st, reading descriptors from Dd:
 //   0: descriptor upload, scan state reset, counters reset, classification
@@ -487,27 +450,18 @@ eg_status enqueue_part(eg_ctx *h, int part, const Plan &P, const FieldDev *Dd, c
             if ((e = launch_widen(t.dtype, Dd + t.pos, t.n, P.sm_count, st)) != cudaSuccess) return from_cuda(e);
             nl++;
         }
-        int zi = 0;  // work-queue tickets of the warp-marching groups: header slots 2, 3, ...
-        unsigned long long *mcount = reinterpret_cast<unsigned long long *>(h->ws_scan) + kMcountSlot;
         for (size_t gi = 0; gi < P.groups.size(); gi++) {
             const Group &G = P.groups[gi];
-            if (G.zm) {
-                e = launch_classify_w(G.minimum, Dd + G.first, G.count, G.items,
-                                      static_cast<const uint32_t *>(h->lut3),
-                                      reinterpret_cast<unsigned long long *>(h->ws_scan) + 2 + zi++, h->sm_count,
-                                      P.ctas, G.first, static_cast<uint64_t *>(h->ws_mlist), mcount, h->ws_mcap, st);
-            } else if (G.r4) {
+            if (G.zm)
+                e = launch_classify_zm(G.minimum, Dd + G.first, G.count, G.items, G.smem,
+                                       static_cast<const uint32_t *>(h->lut3),
+                                       reinterpret_cast<unsigned long long *>(h->ws_scan) + 2 + gi, h->sm_count,
+                                       P.ctas, st);
+            else if (G.r4)
                 e = launch_classify_r4(G.minimum, Dd + G.first, G.count, G.bricks, st);
-            } else {
+            else
                 e = launch_classify_flat(G.kd, G.cdt, Dd + G.first, G.count, G.bricks, st);
-            }
             if (e != cudaSuccess) return from_cuda(e);
-            nl++;
-        }
-        if (zi) {  // pending multi-saddles of the warp-marching groups
-            if ((e = launch_saddle_multi(Dd, static_cast<const uint64_t *>(h->ws_mlist), mcount, h->ws_mcap,
-                                         static_cast<const uint32_t *>(h->lut3), h->sm_count, st)) != cudaSuccess)
-                return from_cuda(e);
             nl++;
         }
         if ((e = launch_scan(false, Dd, P.nf, P.total_tiles, h->ws_scan, st)) != cudaSuccess) return from_cuda(e);
@@ -517,17 +471,8 @@ eg_status enqueue_part(eg_ctx *h, int part, const Plan &P, const FieldDev *Dd, c
             if ((e = launch_resolve_tiles(Dd, P.nf, P.total_rtiles, st)) != cudaSuccess) return from_cuda(e);
             nl++;
         }
-        if (P.chase_bricks) {  // (warp-layout fields are resolved below)
-            if ((e = launch_resolve(Dd, P.nf, P.total_bricks, P.walks, st)) != cudaSuccess) return from_cuda(e);
-            nl++;
-        }
-        if (P.total_ctiles) {
-            unsigned long long *xcount = reinterpret_cast<unsigned long long *>(h->ws_scan) + kXcountSlot;
-            if ((e = launch_resolve_codes(Dd, P.nf, P.total_ctiles, static_cast<uint64_t *>(h->ws_xlist), xcount,
-                                          h->sm_count, st)) != cudaSuccess)
-                return from_cuda(e);
-            nl += 2;
-        }
+        if ((e = launch_resolve(Dd, P.nf, P.total_bricks, P.walks, st)) != cudaSuccess) return from_cuda(e);
+        nl++;
     } else {
         if ((e = cudaMemcpyAsync(const_cast<FieldDev *>(Dd), desc_host, P.desc_bytes, cudaMemcpyHostToDevice, st)) !=
             cudaSuccess)
@@ -592,7 +537,7 @@ eg_status capture_graphs(eg_ctx *h, const Plan &P, const void *desc_host, GraphE
 {
     cudaError_t e = h->pool.alloc(&E.desc_dev, P.desc_bytes);
     if (e != cudaSuccess) return from_cuda(e);
-    if ((e = prepare_classify_w()) != cudaSuccess) return from_cuda(e);
+    if ((e = prepare_classify_zm()) != cudaSuccess) return from_cuda(e);
     for (int p = 0; p < 3; p++) {
         if ((e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return from_cuda(e);
         eg_status s = enqueue_part(h, p, P, static_cast<const FieldDev *>(E.desc_dev), desc_host, cap, &E.launches[p]);
@@ -703,18 +648,16 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
     Plan P;
     P.nf = nf;
     P.walks = cfg.resolve_walks > 0 ? cfg.resolve_walks : 4;
-    P.ctas = cfg.persistent_ctas > 0 ? cfg.persistent_ctas : 2;
+    P.ctas = cfg.persistent_ctas > 0 ? cfg.persistent_ctas : 3;
     P.sm_count = h->sm_count;
     uint64_t total_recs = 0;
-    uint64_t total_xents = 0;  // exit list capacity: the vertices of the code fields
     for (int i = 0; i < nf; i++) {
         P.total_bricks += lay[i].nbricks;
         total_recs += uint64_t(lay[i].nbricks) * lay[i].bcap;
         P.total_tiles += scan_tiles(lay[i].nbricks);
-        if (lay[i].code) total_xents += jobs[i].sh.N;
     }
     P.desc_bytes = sizeof(FieldDev) * size_t(nf);
-    eg_status es = ensure_workspace(h, total_recs, P.total_bricks, P.total_tiles, total_xents);
+    eg_status es = ensure_workspace(h, total_recs, P.total_bricks, P.total_tiles);
     if (es != EG_OK) return es;
 
     auto L = std::make_shared<Launch>();
@@ -759,9 +702,6 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
         r->launch = L;
         e = h->pool.alloc(&r->lab, j.sh.N * sizeof(uint32_t));
         if (e == cudaSuccess && dtype_narrow(j.dtype)) e = h->pool.alloc(&r->wide, j.sh.N * sizeof(float));
-        const uint32_t n0p = (j.sh.n[0] + 7u) & ~7u;
-        if (e == cudaSuccess && ly.code)
-            e = h->pool.alloc(&r->code, uint64_t(n0p) / 8 * j.sh.n[1] * j.sh.n[2] * sizeof(uint32_t));
         r->small = static_cast<SmallBlock *>(L->smalls) + i;
         r->slot = i;
         res[i] = std::move(r);
@@ -794,8 +734,6 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
         F.bcap = ly.bcap;
         F.ty = ly.ty;
         F.nyb = ly.nyb;
-        F.gpr = ly.gpr;
-        F.wpp = ly.wpp;
         F.zc = ly.zc;
         F.nzc = ly.nzc;
         F.vec = (j.sh.n[0] % 4 == 0 && (reinterpret_cast<uintptr_t>(F.f) & 15) == 0) ? 1u : 0u;
@@ -810,20 +748,15 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
             resolve_tile_shape(F.n[0], F.n[1], F.n[2], F.rt, &nt);
             P.total_rtiles += nt;
         }
-        F.code = static_cast<uint32_t *>(R.code);
-        F.n0p = n0p;
-        F.ctile0 = P.total_ctiles;
-        if (ly.zm) P.total_ctiles += walk_blocks(F.n[0], F.n[1], F.n[2]);
-        else P.chase_bricks += ly.nbricks;
         G.count++;
         G.bricks += ly.nbricks;
-        G.items += ly.zm ? uint64_t(ly.wpp) * ly.nzc : ly.nbricks;
+        G.items += ly.zm ? uint64_t(ly.nyb) * ly.nzc : ly.nbricks;
         G.smem = std::max(G.smem, ly.smem);
         brick0 += ly.nbricks;
         rec0 += uint64_t(ly.nbricks) * ly.bcap;
         tile0 += scan_tiles(ly.nbricks);
         char fs[192];
-        std::snprintf(fs, sizeof fs, "%d,%d,%u,%u,%u,%u,%u,%u,%u,%u,%u,%u,%u,%u;", key(i), ly.kd, F.N, ly.ty, ly.wpp,
+        std::snprintf(fs, sizeof fs, "%d,%d,%u,%u,%u,%u,%u,%u,%u,%u,%u,%u,%u,%u;", key(i), ly.kd, F.N, ly.ty, ly.nyb,
                       ly.nbricks, ly.zc, ly.nzc, F.vec, F.n[0], F.n[1], F.n[2], F.n[3], j.dtype);
         P.signature += fs;
     }
@@ -1009,8 +942,7 @@ eg_status collect(eg_ctx *h, Result &r)
         h->pool.release(r.ucnt);
         h->pool.release(r.pbrick);
         h->pool.release(r.wide);
-        h->pool.release(r.code);
-        r.ends = r.ucnt = r.pbrick = r.wide = r.code = nullptr;
+        r.ends = r.ucnt = r.pbrick = r.wide = nullptr;
         if (r.launch && r.launch.use_count() == 1) release_launch(h, r.launch.get());
     }
     if (r.err & kErrNaN) return EG_ERR_NAN;
@@ -1315,7 +1247,7 @@ eg_status eg_autotune(eg_handle h, const eg_field_desc *fields, int n, void *str
     h->timing = true;
     eg_config cur = h->cfg;
     if (cur.resolve_walks <= 0) cur.resolve_walks = 4;
-    if (cur.persistent_ctas <= 0) cur.persistent_ctas = 2;
+    if (cur.persistent_ctas <= 0) cur.persistent_ctas = 3;
     float ms[4];
     eg_status s = timed_trial(h, jobs, st, cur, 2, ms);  // also warms the workspace
     float cur_total = ms[3];
@@ -1323,7 +1255,8 @@ eg_status eg_autotune(eg_handle h, const eg_field_desc *fields, int n, void *str
     struct Knob { int32_t eg_config::*field; std::vector<int32_t> values; };
     const std::vector<Knob> knobs = {
         {&eg_config::classify_planes, {0, 16, 32, 64, 128}},
-        {&eg_config::persistent_ctas, {1, 2}},
+        {&eg_config::classify_rows, {0, 8, 4, 2}},
+        {&eg_config::persistent_ctas, {2, 3}},
         {&eg_config::resolve_walks, {2, 4, 8}},
     };
     for (const Knob &k : knobs) {

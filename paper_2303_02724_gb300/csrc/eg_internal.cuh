@@ -26,11 +26,9 @@
 //
 // Bricks: every kernel after classification works on bricks, contiguous
 // ranges of linear vertex ids, in index order.  Flat layout: 1024 ids per
-// brick.  Warp layout (2D/3D float32 with axis-0 extent <= 2048): each row is
-// cut into groups of 8 vertices, and a brick is 32 consecutive groups of one
-// plane in row-major order (a contiguous id range of at most 256 vertices).
-// Row layout (4D with axis-0 extent <= 1024): `ty` whole rows of one (z, w)
-// plane per brick, so brick b = plane b / nyb, row block b % nyb.
+// brick.  Row layout (2D/3D with axis-0 extent <= 2048, 4D with axis-0 extent
+// <= 1024): `ty` whole rows of one plane per brick (one row when it holds more
+// than 1024 vertices), so brick b = plane b / nyb, row block b % nyb.
 #pragma once
 #include <cstdint>
 #include <type_traits>
@@ -219,21 +217,12 @@ struct FieldDev {
     uint32_t *path_vtx;      // [V] saddle, representative, ..., maximum per path
     uint64_t *pbrick;        // [nbricks + 1] path vertices per brick, then offsets and the total
     uint32_t *err;           // device status word
-    // gradient codes (3D plane-marching classifier, fields of fewer than 2^31
-    // vertices; null otherwise, and the gradient pointers go to lab[]): 4 bits
-    // per vertex, the gradient's neighbour slot or kCodeMax, rows padded to
-    // n0p (a multiple of 8) codes, 8 codes per word, lowest nibble first
-    uint32_t *code;
-    uint32_t n0p;
-    uint64_t ctile0;         // first tile of this field in the code resolver's grid
     uint32_t n[kMaxDim];     // extents (1 beyond the kernel dimension)
     uint32_t s[kMaxDim];     // strides
     uint32_t N;              // vertex count (< 2^32)
     uint32_t nbricks;
     uint32_t bcap;           // record slot capacity per brick (= brick size)
-    uint32_t ty;             // rows per brick (0: flat or warp layout)
-    uint32_t gpr;            // warp layout: groups of 8 vertices per row (ceil(n0 / 8))
-    uint32_t wpp;            // warp layout: warps (bricks) per plane, 0 for other layouts
+    uint32_t ty;             // rows per brick (0: flat layout)
     uint32_t nyb;            // row blocks per plane (row layout)
     uint32_t zc;             // planes per classification work item (row layout)
     uint32_t nzc;            // work items along the slowest axis (row layout)
@@ -248,32 +237,9 @@ struct FieldDev {
     uint32_t dtype;          // element type of fraw
 };
 
-// Gradient codes: the 4-bit code of a maximum; a label whose top bit is set is
-// not a label but the vertex where a gradient path left its resolution tile
-// (code fields only, fields of fewer than 2^31 vertices).
-constexpr uint32_t kCodeMax = 15u;
-constexpr uint32_t kLabelExit = 0x80000000u;
-
-// Word index and bit shift of the code of vertex (x, row), row = z * n1 + y.
-__host__ __device__ __forceinline__ uint64_t code_word(uint32_t n0p, uint64_t row, uint32_t x)
-{
-    return (row * n0p + x) >> 3;
-}
-
 __host__ __device__ __forceinline__ void brick_range(const FieldDev &F, uint32_t b, uint64_t &v0, uint32_t &len)
 {
-    if (F.wpp) {
-        // warp layout: brick = plane p, groups [32 w, 32 w + 32) of its row-major
-        // groups of 8 vertices (whole rows are split only at group boundaries)
-        const uint32_t p = b / F.wpp, w = b - p * F.wpp;
-        const uint64_t G = uint64_t(F.n[1]) * F.gpr;
-        const uint64_t g0 = uint64_t(w) * 32, g1 = (g0 + 32 < G ? g0 + 32 : G) - 1;
-        const uint64_t r0 = g0 / F.gpr, r1 = g1 / F.gpr;
-        const uint64_t x0 = 8 * (g0 - r0 * F.gpr), x1 = 8 * (g1 - r1 * F.gpr) + 8;
-        const uint64_t plane = uint64_t(p) * F.n[1];
-        v0 = (plane + r0) * F.n[0] + x0;
-        len = uint32_t((plane + r1) * F.n[0] + (x1 < F.n[0] ? x1 : F.n[0]) - v0);
-    } else if (F.ty == 0) {
+    if (F.ty == 0) {
         v0 = uint64_t(b) * kFlatBrick;
         const uint64_t rem = uint64_t(F.N) - v0;
         len = rem < kFlatBrick ? uint32_t(rem) : uint32_t(kFlatBrick);
@@ -327,17 +293,6 @@ __device__ __forceinline__ uint32_t slot_vertex(uint32_t v, int k, const uint32_
     uint32_t p = k < NB::H ? uint32_t(NB::H - k) : uint32_t(k - NB::H + 1);
     uint32_t o = pattern_offset(p, s);
     return k < NB::H ? v - o : v + o;
-}
-
-// The gradient target of vertex u before resolution: decoded from the 3D
-// gradient codes, or read from the gradient pointers in lab[].
-__device__ __forceinline__ uint32_t grad_next(const FieldDev &F, uint32_t u)
-{
-    if (!F.code) return F.lab[u];
-    const uint32_t row = u / F.n[0], x = u - row * F.n[0];
-    const uint32_t c = (F.code[code_word(F.n0p, row, x)] >> ((x & 7u) * 4u)) & 15u;
-    if (c == kCodeMax) return u;
-    return slot_vertex<3>(u, int(c), F.s);
 }
 
 __device__ __forceinline__ int lowest_bit(uint32_t m) { return __ffs(m) - 1; }

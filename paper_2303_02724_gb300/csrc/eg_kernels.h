@@ -26,26 +26,23 @@ constexpr int kR4CtaThreads = 256;
 // on the device (so it can be captured in graphs).
 cudaError_t launch_widen(uint32_t dtype, const FieldDev *field, uint64_t n, int sm_count, cudaStream_t st);
 
-// Steps (a)+(c), warp-marching kernel for 2D/3D float32 fields with rows of
-// at most kWMaxRow vertices (warp brick layout: FieldDev::gpr, wpp).
+// Steps (a)+(c), plane-marching kernel for 2D/3D fields with rows of at most
+// kZmMaxRow vertices.
 // lut: the 2-bit class of every 14-bit upper mask (1024 words), then, as
 // 16-bit words, the component holding each mask's lowest set bit.
-// Persistent: min(sm_count * ctas_per_sm, one warp per item) CTAs of 8 warps;
-// every warp takes work items from *ticket (zeroed before the launch).
-constexpr uint32_t kWMaxRow = 2048;
-cudaError_t launch_classify_w(bool minimum, const FieldDev *fields, int nf, uint64_t total_items, const uint32_t *lut,
-                              unsigned long long *ticket, int sm_count, int ctas_per_sm, int fbase, uint64_t *mlist,
-                              unsigned long long *mcount, uint64_t mcap, cudaStream_t st);
-// Saddles with three or more components left pending by the warp-marching
-// classifier: the list mlist[min(*mcount, mcap)] of (absolute field index in
-// `fields` << 40 | record slot); before scan A.
-cudaError_t launch_saddle_multi(const FieldDev *fields, const uint64_t *mlist, const unsigned long long *mcount,
-                                uint64_t mcap, const uint32_t *lut, int sm_count, cudaStream_t st);
-// Raise the classifier's shared-memory limit on the current device (also done
-// by launch_classify_w; call it before capturing a graph).
-cudaError_t prepare_classify_w();
+constexpr uint32_t kZmMaxRow = 2048;
+size_t zm_smem_bytes(uint32_t n0, uint32_t ty);
+// Persistent: grid = min(total_items, sm_count * ctas_per_sm) CTAs take work
+// items from *ticket (zeroed before the launch).
+cudaError_t launch_classify_zm(bool minimum, const FieldDev *fields, int nf, uint64_t total_items, size_t smem,
+                               const uint32_t *lut, unsigned long long *ticket, int sm_count, int ctas_per_sm,
+                               cudaStream_t st);
+
 // Zero the totals and status word of every field of a launch.
 cudaError_t launch_init_fields(const FieldDev *fields, int nf, cudaStream_t st);
+// Set the classifier's shared-memory attribute on the current device (also
+// done lazily by launch_classify_zm; call it before capturing a graph).
+cudaError_t prepare_classify_zm();
 
 // Test hook: a look-back wait whose predecessor never publishes.
 cudaError_t launch_lookback_orphan(uint64_t *st, uint32_t *err, cudaStream_t s);
@@ -69,12 +66,6 @@ cudaError_t launch_resolve_tiles(const FieldDev *fields, int nf, uint64_t tiles,
 // Resolution tile extents (log2) of a field of extents n0 x n1 x n2, and the
 // number of its tiles.
 void resolve_tile_shape(uint32_t n0, uint32_t n1, uint32_t n2, uint32_t rt[3], uint64_t *tiles);
-// Resolution of code fields: walks over groups of 8 vertices (walk_blocks
-// CTAs per code field, numbered from FieldDev::ctile0; after the tiled pass,
-// launch_resolve_tiles), then the exit list (xlist / xcount, zeroed count).
-uint64_t walk_blocks(uint32_t n0, uint32_t n1, uint32_t n2);
-cudaError_t launch_resolve_codes(const FieldDev *fields, int nf, uint64_t blocks, uint64_t *xlist,
-                                 unsigned long long *xcount, int sm_count, cudaStream_t st);
 
 // Steps (d)+(e): nodes and arc ends per brick (one kernel dimension), then CSR.
 cudaError_t launch_nodes_d(int kd, const FieldDev *fields, int nf, uint64_t base, uint64_t bricks, cudaStream_t st);

@@ -1,8 +1,8 @@
 // Arc geometry (the paths Algorithm 2 traces): for every saddle s and every
 // component of its upper link, the vertices s, rep, gradient(rep), ..., up to
 // the maximum reached, where rep is the component's highest vertex
-// (UpperLinkRep, Sec. 3.4).  Gathered between classification and resolution,
-// while the gradient pointers (lab[]) or codes are still in place.
+// (UpperLinkRep, Sec. 3.4).  Gathered while lab[] still holds the gradient
+// pointers, i.e. between classification and resolution.
 //
 // Output (CSR): path_ptr[P + 1] offsets into path_vtx; paths ordered by saddle
 // (index order, the order of the saddle list) and, within a saddle, by
@@ -23,11 +23,11 @@ constexpr int kPathThreads = 256;
 constexpr int kScanPathThreads = 1024;
 
 // Gradient steps from r to its maximum (bounded: a path has fewer than N steps).
-__device__ __forceinline__ uint32_t gradient_steps(const FieldDev &F, uint32_t r, uint32_t N, uint32_t *err)
+__device__ __forceinline__ uint32_t gradient_steps(const uint32_t *lab, uint32_t r, uint32_t N, uint32_t *err)
 {
     uint32_t n = 0;
     for (uint32_t u = r;;) {
-        const uint32_t w = grad_next(F, u);
+        const uint32_t w = lab[u];
         if (w == u) break;
         u = w;
         if (++n > N) {
@@ -86,7 +86,7 @@ k_path_len(const FieldDev *__restrict__ fields, int nf, uint64_t base, uint64_t 
         int k[CompBound<KD>::value];
         const int nc = rec_slots<KD>(info, k);
         for (int q = 0; q < nc; q++) {
-            const uint64_t len = 2 + gradient_steps(F, slot_vertex<KD>(sid, k[q], s), F.N, F.err);
+            const uint64_t len = 2 + gradient_steps(F.lab, slot_vertex<KD>(sid, k[q], s), F.N, F.err);
             const uint64_t p = p_off + lp + uint64_t(q);
             if (p < capP) F.path_ptr[p] = len;
             else atomicOr(F.err, kErrInternal);
@@ -190,7 +190,7 @@ k_path_write(const FieldDev *__restrict__ fields, int nf, uint64_t base, uint64_
             F.path_vtx[at] = sid;
             F.path_vtx[at + 1] = u;
             for (uint64_t j = 2; j < len; j++) {
-                u = grad_next(F, u);
+                u = F.lab[u];
                 F.path_vtx[at + j] = u;
             }
             at += len;

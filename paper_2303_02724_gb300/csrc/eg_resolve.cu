@@ -15,8 +15,6 @@
 // later walks get shorter.  A walk longer than N steps is impossible (the
 // order strictly increases along a path); the bound is a guard that reports
 // kErrNotConverged instead of looping.
-#include <algorithm>
-
 #include "eg_internal.cuh"
 #include "eg_kernels.h"
 
@@ -28,7 +26,6 @@ constexpr int kResolveThreads = 256;
 template <int kIlp>
 __device__ __forceinline__ void resolve_brick(const FieldDev &F, uint32_t b)
 {
-    if (F.wpp) return;  // warp-layout fields: resolved by k_resolve_cwalk
     uint64_t v0;
     uint32_t len;
     brick_range(F, b, v0, len);
@@ -151,7 +148,7 @@ k_resolve_tile(const FieldDev *__restrict__ fields, int nf)
         else hi = mid - 1;
     }
     const FieldDev &F = fields[lo];
-    // dense maxima: short paths, the walks are faster on their own
+    // dense maxima: short paths, the brick walks are faster on their own
     if (F.kd != 3 || uint64_t(F.totals[0]) * 100 >= uint64_t(F.N)) return;
     const uint32_t lx = F.rt[0], ly = F.rt[1], lz = F.rt[2];
     const uint32_t TX = 1u << lx, TY = 1u << ly, T = 1u << (lx + ly + lz);
@@ -171,21 +168,13 @@ k_resolve_tile(const FieldDev *__restrict__ fields, int nf)
     auto gid = [&](uint32_t i) {
         return (z0 + (i >> (lx + ly))) * s2 + (y0 + ((i >> lx) & (TY - 1))) * s1 + x0 + (i & (TX - 1));
     };
-    // gradient target of tile vertex i: its pointer, or decoded from its code
-    auto target = [&](uint32_t i) {
-        const uint32_t v = gid(i);
-        if (!F.code) return lab[v];
-        const uint32_t row = (z0 + (i >> (lx + ly))) * n1 + y0 + ((i >> lx) & (TY - 1)), x = x0 + (i & (TX - 1));
-        const uint32_t c = (F.code[code_word(F.n0p, row, x)] >> ((x & 7u) * 4u)) & 15u;
-        return c == kCodeMax ? v : slot_vertex<3>(v, int(c), F.s);
-    };
     // 1: tile-local gradient targets (every thread runs the same trip counts)
     for (uint32_t i0 = 0; i0 < T; i0 += kTb * kTileThreads) {
         uint32_t a[kTb];
 #pragma unroll
         for (int b = 0; b < kTb; b++) {
             const uint32_t i = i0 + b * kTileThreads + threadIdx.x;
-            a[b] = inside(i) ? target(i) : 0u;
+            a[b] = inside(i) ? lab[gid(i)] : 0u;
         }
 #pragma unroll
         for (int b = 0; b < kTb; b++) {
@@ -229,212 +218,16 @@ k_resolve_tile(const FieldDev *__restrict__ fields, int nf)
         if (!__syncthreads_or(changed)) break;
     }
     // 3: the label of every vertex that ends on a maximum; for the others the
-    // first vertex outside the tile: their terminal's gradient target (with
-    // pointers, terminals keep their entry; with codes every vertex is written)
+    // first vertex outside the tile: their terminal's gradient target, still
+    // in lab[] (terminals keep their entry)
     for (uint32_t i0 = 0; i0 < T; i0 += kTb * kTileThreads) {
 #pragma unroll
         for (int b = 0; b < kTb; b++) {
             const uint32_t i = i0 + b * kTileThreads + threadIdx.x;
             const uint16_t w = s_w[i];
-            if (!inside(i)) continue;
-            if (F.code) lab[gid(i)] = (w & kOut) ? target(w & kIdx) : gid(w & kIdx);
-            else if ((w & kIdx) != i) lab[gid(i)] = (w & kOut) ? lab[gid(w & kIdx)] : gid(w & kIdx);
+            if (inside(i) && (w & kIdx) != i) lab[gid(i)] = (w & kOut) ? lab[gid(w & kIdx)] : gid(w & kIdx);
         }
     }
-}
-
-// ---------------------------------------------------------------------------
-// Resolution of code fields (gradients as 4-bit codes): one thread per group
-// of 8 consecutive vertices of a row (the classifier's groups; one code word).
-// Fields with dense maxima (short paths): the 8 gradient paths are followed
-// through the codes in lock-step (the code array is 1/8 of the pointers', so
-// it mostly stays in L2); a path still going after kWalkCap steps leaves its
-// current vertex with kLabelExit set and goes on the exit list, which
-// k_resolve_exits finishes.  Fields with few maxima (long paths) had the tiled
-// pass first, which left a label or the first vertex outside its tile in
-// every entry of lab[]: the walks follow lab[] to a fixed point.
-// ---------------------------------------------------------------------------
-constexpr int kWalkThreads = 256;
-constexpr int kWalkCap = 64;
-
-uint64_t walk_blocks(uint32_t n0, uint32_t n1, uint32_t n2)
-{
-    const uint64_t groups = uint64_t((n0 + 7) / 8) * n1 * n2;
-    return (groups + kWalkThreads - 1) / kWalkThreads;
-}
-
-__global__ void __launch_bounds__(kWalkThreads)
-k_resolve_cwalk(const FieldDev *__restrict__ fields, int nf, uint64_t *xlist, unsigned long long *xcount)
-{
-    __shared__ uint32_t s_coff[14], s_voff[14];
-    const uint64_t g = blockIdx.x;
-    int fi = 0;
-    {
-        int lo = 0, hi = nf - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (fields[mid].ctile0 <= g) lo = mid;
-            else hi = mid - 1;
-        }
-        fi = lo;
-    }
-    const FieldDev &F = fields[fi];
-    if (!F.wpp) return;
-    const uint32_t n0 = F.n[0], n1 = F.n[1], n0p = F.n0p, gpr = (n0 + 7) / 8;
-    const int tid = threadIdx.x, lane = tid & 31;
-    if (tid < 14) {
-        const uint32_t p = Nbr<3>::pat(tid);
-        const uint32_t co = (p & 1u) + ((p & 2u) ? n0p : 0u) + ((p & 4u) ? n0p * n1 : 0u);
-        const uint32_t vo = (p & 1u) + ((p & 2u) ? n0 : 0u) + ((p & 4u) ? n0 * n1 : 0u);
-        s_coff[tid] = Nbr<3>::neg(tid) ? 0u - co : co;
-        s_voff[tid] = Nbr<3>::neg(tid) ? 0u - vo : vo;
-    }
-    __syncthreads();
-    const uint64_t gi = (g - F.ctile0) * kWalkThreads + uint64_t(tid);
-    const bool valid = gi < uint64_t(gpr) * n1 * F.n[2];
-    const uint32_t row = valid ? uint32_t(gi / gpr) : 0u, x = valid ? 8u * uint32_t(gi - uint64_t(row) * gpr) : 0u;
-    const uint32_t nv = valid ? min(8u, n0 - x) : 0u;
-    const uint32_t vrow = row * n0 + x;
-    uint32_t *lab = F.lab;
-    uint32_t v[8];
-    uint32_t live = 0;
-    if (!F.code || uint64_t(F.totals[0]) * 100 < uint64_t(F.N)) {
-        // gradient pointers, or after the tiled pass (labels or the first
-        // vertex outside a tile): follow lab[] to a fixed point (a maximum)
-#pragma unroll
-        for (int i = 0; i < 8; i++) {
-            v[i] = vrow + i;
-            if (uint32_t(i) < nv) {
-                const uint32_t u = lab[vrow + i];
-                if (u != vrow + i) {
-                    v[i] = u;
-                    live |= 1u << i;
-                }
-            }
-        }
-        const uint32_t moved = live;
-        uint32_t steps = 0;
-        while (live) {
-#pragma unroll
-            for (int i = 0; i < 8; i++)
-                if ((live >> i) & 1u) {
-                    const uint32_t w = lab[v[i]];
-                    if (w == v[i]) live &= ~(1u << i);
-                    else v[i] = w;
-                }
-            if (++steps > F.N) {
-                atomicOr(F.err, kErrNotConverged);
-                break;
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < 8; i++)
-            if ((moved >> i) & 1u) lab[vrow + i] = v[i];
-        return;
-    }
-    // dense maxima: walk the codes, two walks in flight per lane; a slot whose
-    // walk ends (a maximum, or the step cap) takes the lane's next vertex, so
-    // the lane's time is the sum of its 8 walks, not 8 times the longest
-    const uint32_t crow = row * n0p + x;
-    const uint32_t w0 = valid ? F.code[crow >> 3] : 0xffffffffu;
-    const uint32_t *code = F.code;
-    uint32_t next = 0;
-    uint32_t sj[2], sci[2], sv[2], sh[2];
-    bool act[2];
-    auto start = [&](int k) {
-        act[k] = false;
-        while (next < nv) {
-            const uint32_t j = next++;
-            const uint32_t c = (w0 >> (4 * j)) & 15u;
-            if (c == kCodeMax) {
-                lab[vrow + j] = vrow + j;  // a maximum labels itself
-                continue;
-            }
-            sj[k] = j;
-            sci[k] = crow + j + s_coff[c];
-            sv[k] = vrow + j + s_voff[c];
-            sh[k] = 1;
-            act[k] = true;
-            return;
-        }
-    };
-    start(0);
-    start(1);
-    while (act[0] || act[1]) {
-#pragma unroll
-        for (int k = 0; k < 2; k++)
-            if (act[k]) {
-                const uint32_t c = (code[sci[k] >> 3] >> ((sci[k] & 7u) * 4u)) & 15u;
-                if (c == kCodeMax) {
-                    lab[vrow + sj[k]] = sv[k];
-                    start(k);
-                } else if (sh[k] >= kWalkCap) {
-                    // still going: the current vertex lies on the path;
-                    // k_resolve_exits continues from its entry
-                    lab[vrow + sj[k]] = sv[k] | kLabelExit;
-                    live |= 1u << sj[k];
-                    start(k);
-                } else {
-                    sci[k] += s_coff[c];
-                    sv[k] += s_voff[c];
-                    sh[k]++;
-                }
-            }
-    }
-    // exit list (warp-aggregated)
-    const uint32_t ne = __popc(live);
-    uint32_t inc = ne;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += t;
-    }
-    const uint32_t tot = __shfl_sync(0xffffffffu, inc, 31);
-    if (tot == 0) return;
-    unsigned long long b0 = 0;
-    if (lane == 31) b0 = atomicAdd(xcount, (unsigned long long)tot);
-    b0 = __shfl_sync(0xffffffffu, b0, 31) + (inc - ne);
-    for (uint32_t m = live; m; m &= m - 1)
-        xlist[b0++] = (uint64_t(uint32_t(fi)) << 32) | (vrow + uint32_t(__ffs(m) - 1));
-}
-
-// Vertices whose path left the neighbourhood of their tile: follow exits to a
-// label (every vertex carries its label or an exit by now).  Concurrent
-// threads may replace an exit by the label on the same path: either leads to
-// the same maximum.
-__global__ void __launch_bounds__(kWalkThreads)
-k_resolve_exits(const FieldDev *__restrict__ fields, const uint64_t *xlist, const unsigned long long *xcount)
-{
-    const unsigned long long n = *xcount;
-    for (unsigned long long i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-         i += uint64_t(gridDim.x) * blockDim.x) {
-        const uint64_t e = xlist[i];
-        const FieldDev &F = fields[uint32_t(e >> 32)];
-        const uint32_t v = uint32_t(e);
-        uint32_t *lab = F.lab;
-        const uint32_t first = lab[v] & ~kLabelExit;  // the first exit of v's path
-        uint32_t w = lab[first];
-        uint32_t steps = 0;
-        while (w & kLabelExit) {
-            w = lab[w & ~kLabelExit];
-            if (++steps > F.N) {
-                atomicOr(F.err, kErrNotConverged);
-                break;
-            }
-        }
-        w &= ~kLabelExit;
-        lab[v] = w;
-        if (steps) lab[first] = w;  // the first exit lies on the same path: later walks stop there
-    }
-}
-
-cudaError_t launch_resolve_codes(const FieldDev *fields, int nf, uint64_t blocks, uint64_t *xlist,
-                                 unsigned long long *xcount, int sm_count, cudaStream_t st)
-{
-    if (blocks == 0) return cudaSuccess;
-    k_resolve_cwalk<<<dim3(static_cast<unsigned>(blocks)), kWalkThreads, 0, st>>>(fields, nf, xlist, xcount);
-    k_resolve_exits<<<dim3(unsigned(std::max(sm_count, 1) * 8)), kWalkThreads, 0, st>>>(fields, xlist, xcount);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_resolve_tiles(const FieldDev *fields, int nf, uint64_t tiles, cudaStream_t st)
