@@ -207,8 +207,6 @@ struct eg_ctx {
     uint64_t ws_bricks = 0;
     void *ws_scan = nullptr;
     uint64_t ws_tiles = 0;
-    void *ws_mlist = nullptr;  // pending multi-saddles of the classifier (one u64 per entry)
-    uint64_t ws_mcap = 0;
     void *lut3 = nullptr;  // saddle class table of the 3D link graph + two-component table
     void *stage = nullptr;  // device staging for eg_compute_host
     size_t stage_bytes = 0;
@@ -336,12 +334,7 @@ eg_status grow(eg_ctx *h, void **p, uint64_t &cap, uint64_t want, size_t elem)
 
 eg_status ensure_workspace(eg_ctx *h, uint64_t recs, uint64_t bricks, uint64_t tiles)
 {
-    // pending multi-saddles: a sixteenth of the record slots (saddles with
-    // three or more components are far rarer; the classifier completes the
-    // overflow itself)
-    const uint64_t ments = recs / 16 + 1024;
-    if (recs <= h->ws_rec_cap && bricks <= h->ws_bricks && tiles <= h->ws_tiles && ments <= h->ws_mcap)
-        return EG_OK;
+    if (recs <= h->ws_rec_cap && bricks <= h->ws_bricks && tiles <= h->ws_tiles) return EG_OK;
     // earlier computations may still use the old workspace
     cudaEventSynchronize(h->ws_free);
     h->ws_gen++;
@@ -374,14 +367,6 @@ eg_status ensure_workspace(eg_ctx *h, uint64_t recs, uint64_t bricks, uint64_t t
         }
         (void)t;
         h->ws_tiles = c;
-    }
-    if (ments > h->ws_mcap) {
-        h->pool.release(h->ws_mlist);
-        h->ws_mlist = nullptr;
-        h->ws_mcap = 0;
-        cudaError_t e = h->pool.alloc(&h->ws_mlist, ments * sizeof(uint64_t));
-        if (e != cudaSuccess) return from_cuda(e);
-        h->ws_mcap = ments;
     }
     return EG_OK;
 }
@@ -443,12 +428,6 @@ struct Plan {
     std::string signature;  // identical for calls that can share a captured graph
 };
 
-// Header slot of the scan workspace holding the classifier's pending
-// multi-saddle count (slots 0-1: scan tickets; 2..: one work-queue ticket per
-// plane-marching group, of which there are at most four: two row classes x
-// two graphs).
-constexpr int kMcountSlot = 30;
-
 // Enqueue one phase of the pipeline on st, reading descriptors from Dd:
 //   0: descriptor upload, scan state reset, counters reset, classification
 //      (steps a+c), scan A;   1: resolution (step b);
@@ -471,26 +450,18 @@ eg_status enqueue_part(eg_ctx *h, int part, const Plan &P, const FieldDev *Dd, c
             if ((e = launch_widen(t.dtype, Dd + t.pos, t.n, P.sm_count, st)) != cudaSuccess) return from_cuda(e);
             nl++;
         }
-        int zi = 0;  // work-queue tickets of the plane-marching groups: header slots 2, 3, ...
-        unsigned long long *mcount = reinterpret_cast<unsigned long long *>(h->ws_scan) + kMcountSlot;
         for (size_t gi = 0; gi < P.groups.size(); gi++) {
             const Group &G = P.groups[gi];
             if (G.zm)
                 e = launch_classify_zm(G.minimum, Dd + G.first, G.count, G.items, G.smem,
                                        static_cast<const uint32_t *>(h->lut3),
-                                       reinterpret_cast<unsigned long long *>(h->ws_scan) + 2 + zi++, h->sm_count,
-                                       P.ctas, G.first, static_cast<uint64_t *>(h->ws_mlist), mcount, h->ws_mcap, st);
+                                       reinterpret_cast<unsigned long long *>(h->ws_scan) + 2 + gi, h->sm_count,
+                                       P.ctas, st);
             else if (G.r4)
                 e = launch_classify_r4(G.minimum, Dd + G.first, G.count, G.bricks, st);
             else
                 e = launch_classify_flat(G.kd, G.cdt, Dd + G.first, G.count, G.bricks, st);
             if (e != cudaSuccess) return from_cuda(e);
-            nl++;
-        }
-        if (zi) {  // pending multi-saddles of the plane-marching groups
-            if ((e = launch_saddle_multi(Dd, static_cast<const uint64_t *>(h->ws_mlist), mcount, h->ws_mcap,
-                                         static_cast<const uint32_t *>(h->lut3), h->sm_count, st)) != cudaSuccess)
-                return from_cuda(e);
             nl++;
         }
         if ((e = launch_scan(false, Dd, P.nf, P.total_tiles, h->ws_scan, st)) != cudaSuccess) return from_cuda(e);

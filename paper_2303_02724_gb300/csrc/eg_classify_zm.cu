@@ -261,80 +261,12 @@ __device__ __forceinline__ uint64_t saddle_info(const float (&nb)[14], uint32_t 
     return (uint64_t(b0) << 56) | codes;
 }
 
-// Value of neighbour slot k of column xx of ring row `row` of plane buffer C
-// (D and U at float offsets dD, dU from C), slot order as in ring_nbrs.
-__device__ __forceinline__ float ring_val(const float *row, int xx, int rs, int dD, int dU, int k)
-{
-    // per slot, 2-bit fields: row + 1 and column + 1
-    constexpr uint32_t kRows = (0u << 0) | (0u << 2) | (1u << 4) | (1u << 6) | (0u << 8) | (0u << 10) | (1u << 12) |
-                               (1u << 14) | (2u << 16) | (2u << 18) | (1u << 20) | (1u << 22) | (2u << 24) | (2u << 26);
-    constexpr uint32_t kCols = (0u << 0) | (1u << 2) | (0u << 4) | (1u << 6) | (0u << 8) | (1u << 10) | (0u << 12) |
-                               (2u << 14) | (1u << 16) | (2u << 18) | (1u << 20) | (2u << 22) | (1u << 24) | (2u << 26);
-    const int plane = k < 4 ? dD : (k < 10 ? 0 : dU);
-    const int dy = int((kRows >> (2 * k)) & 3u) - 1, dx = int((kCols >> (2 * k)) & 3u) - 1;
-    return row[plane + dy * rs + zm_col(xx + dx)];
-}
-
-// Highest slot of the non-empty mask m by (value, then rank), values read from
-// the ring one set bit at a time (the minimum graph: lowest value, lowest rank).
-template <bool MIN>
-__device__ __forceinline__ int ring_top(const float *row, int xx, int rs, int dD, int dU, uint32_t m)
-{
-    float best = 0.f;
-    int rk = -1;
-    while (m) {
-        const int k = __ffs(m) - 1;
-        m &= m - 1;
-        const float v = ring_val(row, xx, rs, dD, dU, k);
-        if (rk < 0 || (MIN ? v < best : v >= best)) {
-            best = v;
-            rk = k;
-        }
-    }
-    return rk;
-}
-
-// Record info of a saddle with three or more upper-link components, left for
-// k_saddle_multi: bit 63, the gradient slot in bits 16..19, the upper mask in
-// bits 0..13 (a real info word never has bit 63 set).
-constexpr uint64_t kInfoPending = 1ull << 63;
-
-// Neighbour slot k (slot order of Nbr<3>) as a signed step per axis.
-__device__ __forceinline__ void slot_step(int k, int &dx, int &dy, int &dz)
-{
-    const uint32_t p = Nbr<3>::pat(k);
-    const int sg = Nbr<3>::neg(k) ? -1 : 1;
-    dx = sg * int(p & 1u);
-    dy = sg * int((p >> 1) & 1u);
-    dz = sg * int((p >> 2) & 1u);
-}
-
-// Info word of a saddle with three or more upper-link components, from its 14
-// neighbour values read from the field (NaN outside the domain).
-template <bool MIN>
-__device__ __forceinline__ uint64_t multi_info(const FieldDev &F, uint32_t v, uint64_t pending, const uint16_t *lowc)
-{
-    const uint32_t n0 = F.n[0], n1 = F.n[1], n2 = F.n[2];
-    const uint32_t x = v % n0, t = v / n0, y = t % n1, z = t / n1;
-    float nb[14];
-#pragma unroll
-    for (int k = 0; k < 14; k++) {
-        int dx, dy, dz;
-        slot_step(k, dx, dy, dz);
-        const int xx = int(x) + dx, yy = int(y) + dy, zz = int(z) + dz;
-        const bool in = xx >= 0 && xx < int(n0) && yy >= 0 && yy < int(n1) && zz >= 0 && zz < int(n2);
-        nb[k] = in ? F.f[(uint64_t(uint32_t(zz)) * n1 + uint32_t(yy)) * n0 + uint32_t(xx)] : __int_as_float(0x7fc00000);
-    }
-    const uint32_t upper = uint32_t(pending & 0x3fffu);
-    return saddle_info<MIN>(nb, upper, int((pending >> 16) & 15u), 2u, __ldg(lowc + upper), lowc);
-}
-
 constexpr int kVx = 8;  // vertices per thread along axis 0
 
 template <bool MIN>
 __global__ void __launch_bounds__(kZmThreads, 3)
 k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__restrict__ lut, uint64_t total_items,
-              unsigned long long *ticket, int fbase, uint64_t *mlist, unsigned long long *mcount, uint64_t mcap)
+              unsigned long long *ticket)
 {
     extern __shared__ float4 zm_smem4[];
     float *ring = reinterpret_cast<float *>(zm_smem4);
@@ -584,8 +516,6 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
             const uint32_t ovrow = __shfl_sync(0xffffffffu, vrow, own);
             const uint32_t ox = __shfl_sync(0xffffffffu, x, own);
             const uint32_t orr = __shfl_sync(0xffffffffu, rr, own);
-            bool pend = false;
-            uint64_t qp = 0;
             if (j < cw) {
                 // vertex i of the owner: its (j - own_excl)-th critical vertex
                 uint32_t k = j - own_excl, m = ocrit, i = 0;
@@ -603,43 +533,13 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
                 uint64_t inf = 0;
                 if (upper) {
                     const uint32_t cls = sl >> 4;
-                    const int first = int(sl & 15u);
-                    if (cls == 1) {
-                        // two components: the gradient's, represented by the
-                        // gradient slot, and the other one (the component of
-                        // the mask's lowest set bit, or the rest), whose
-                        // highest vertex is found among its own slots only
-                        const uint32_t a2 = __ldg(lowc + upper);
-                        const uint32_t other = ((a2 >> first) & 1u) ? (upper ^ a2) : a2;
-                        const int rk = ring_top<MIN>(orow, int(ox + i), int(rs), dD, dU, other);
-                        inf = (2ull << 56) | uint64_t(first) | (uint64_t(rk) << 5);
-                        np += 2;
-                    } else {
-                        // three or more (rare): completed by k_saddle_multi,
-                        // which also adds their paths to the brick's count
-                        inf = kInfoPending | (uint64_t(first) << 16) | upper;
-                        pend = true;
-                    }
+                    const uint32_t a2 = __ldg(lowc + upper);
+                    float nb[14];
+                    ring_nbrs(orow, int(ox + i), int(rs), dD, dU, nb);
+                    inf = saddle_info<MIN>(nb, upper, int(sl & 15u), cls, a2, lowc);
+                    np += uint32_t(inf >> 56);
                 }
                 F.rec_info[q] = inf;
-                qp = q;
-            }
-            // pending records onto the list (warp-aggregated); if it is full,
-            // the record is completed here from the field
-            const unsigned pm = __ballot_sync(0xffffffffu, pend);
-            if (pm) {
-                unsigned long long at = 0;
-                if (lane == __ffs(pm) - 1) at = atomicAdd(mcount, (unsigned long long)__popc(pm));
-                at = __shfl_sync(0xffffffffu, at, __ffs(pm) - 1) + __popc(pm & ((1u << lane) - 1u));
-                if (pend) {
-                    if (at < mcap) {
-                        mlist[at] = (uint64_t(uint32_t(fbase + fi)) << 40) | qp;
-                    } else {
-                        const uint64_t inf = multi_info<MIN>(F, F.rec_sid[qp], F.rec_info[qp], lowc);
-                        F.rec_info[qp] = inf;
-                        np += uint32_t(inf >> 56);
-                    }
-                }
             }
         }
         np = __reduce_add_sync(0xffffffffu, np);
@@ -654,37 +554,6 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
     // drain this item's outstanding (empty) copy groups before the ring is reused
     asm volatile("cp.async.wait_all;\n" ::: "memory");
     }
-}
-
-// Saddles with three or more upper-link components left pending by the
-// classifier (the list holds field << 40 | record slot): their record info
-// (components and their highest vertices, Sec. 3.4), and their paths added
-// to their brick's count, before scan A.
-__global__ void __launch_bounds__(256)
-k_saddle_multi(const FieldDev *__restrict__ fields, const uint64_t *mlist, const unsigned long long *mcount,
-               uint64_t mcap, const uint32_t *__restrict__ lut)
-{
-    const uint16_t *lowc = reinterpret_cast<const uint16_t *>(lut + 1024);
-    unsigned long long n = *mcount;
-    if (n > mcap) n = mcap;
-    for (unsigned long long i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
-         i += uint64_t(gridDim.x) * blockDim.x) {
-        const uint64_t e = mlist[i];
-        const FieldDev &F = fields[uint32_t(e >> 40)];
-        const uint64_t q = e & ((1ull << 40) - 1);
-        const uint64_t inf = (F.flags & kFlagMinimum) ? multi_info<true>(F, F.rec_sid[q], F.rec_info[q], lowc)
-                                                      : multi_info<false>(F, F.rec_sid[q], F.rec_info[q], lowc);
-        F.rec_info[q] = inf;
-        atomicAdd(&F.bcnt[q / F.bcap].z, uint32_t(inf >> 56));
-    }
-}
-
-cudaError_t launch_saddle_multi(const FieldDev *fields, const uint64_t *mlist, const unsigned long long *mcount,
-                                uint64_t mcap, const uint32_t *lut, int sm_count, cudaStream_t st)
-{
-    const dim3 grid = dim3(unsigned((sm_count > 0 ? sm_count : 1) * 8));
-    k_saddle_multi<<<grid, 256, 0, st>>>(fields, mlist, mcount, mcap, lut);
-    return cudaGetLastError();
 }
 
 cudaError_t prepare_classify_zm()
@@ -712,7 +581,7 @@ size_t zm_smem_bytes(uint32_t n0, uint32_t ty) { return size_t(4) * zm_ring_floa
 
 cudaError_t launch_classify_zm(bool minimum, const FieldDev *fields, int nf, uint64_t total_items, size_t smem,
                                const uint32_t *lut, unsigned long long *ticket, int sm_count, int ctas_per_sm,
-                               int fbase, uint64_t *mlist, unsigned long long *mcount, uint64_t mcap, cudaStream_t st)
+                               cudaStream_t st)
 {
     if (total_items == 0) return cudaSuccess;
     auto kern = minimum ? k_classify_zm<true> : k_classify_zm<false>;
@@ -721,8 +590,7 @@ cudaError_t launch_classify_zm(bool minimum, const FieldDev *fields, int nf, uin
     // (the row layout bounds the ring at 4 x (4 rows x 1032 + 16) floats = 66 KB)
     uint64_t grid = uint64_t(sm_count > 0 ? sm_count : 1) * uint64_t(ctas_per_sm > 0 ? ctas_per_sm : 3);
     if (grid > total_items) grid = total_items;
-    kern<<<dim3(unsigned(grid)), kZmThreads, smem, st>>>(fields, nf, lut, total_items, ticket, fbase, mlist, mcount,
-                                                         mcap);
+    kern<<<dim3(unsigned(grid)), kZmThreads, smem, st>>>(fields, nf, lut, total_items, ticket);
     return cudaGetLastError();
 }
 

@@ -34,17 +34,9 @@ constexpr uint32_t kZmMaxRow = 2048;
 size_t zm_smem_bytes(uint32_t n0, uint32_t ty);
 // Persistent: grid = min(total_items, sm_count * ctas_per_sm) CTAs take work
 // items from *ticket (zeroed before the launch).
-// Saddles with three or more components are left pending: their records go
-// on the list mlist[min(*mcount, mcap)] as (fbase + field index) << 40 |
-// record slot (the classifier completes the overflow itself); fbase is the
-// position of `fields` in the launch's descriptor table.
 cudaError_t launch_classify_zm(bool minimum, const FieldDev *fields, int nf, uint64_t total_items, size_t smem,
                                const uint32_t *lut, unsigned long long *ticket, int sm_count, int ctas_per_sm,
-                               int fbase, uint64_t *mlist, unsigned long long *mcount, uint64_t mcap, cudaStream_t st);
-// Completes the pending saddles (their info and their brick's path count);
-// `fields` is the whole descriptor table; before scan A.
-cudaError_t launch_saddle_multi(const FieldDev *fields, const uint64_t *mlist, const unsigned long long *mcount,
-                                uint64_t mcap, const uint32_t *lut, int sm_count, cudaStream_t st);
+                               cudaStream_t st);
 
 // Zero the totals and status word of every field of a launch.
 cudaError_t launch_init_fields(const FieldDev *fields, int nf, cudaStream_t st);
