@@ -59,21 +59,31 @@ def kernel_fingerprint(source: str) -> str:
     return _fingerprint([os.path.join(CSRC, source)] + _headers())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every .cu under csrc/ and link libeg.so; returns its path."""
-    os.makedirs(BUILD, exist_ok=True)
-    stamp = os.path.join(BUILD, "stamp")
-    fp = _fingerprint()
-    if not force and os.path.exists(LIB) and os.path.exists(stamp):
+LIB_CHECKED = os.path.join(HERE, "libeg_checked.so")
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+
+
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Compile every .cu under csrc/ and link libeg.so; returns its path.
+    checked=True builds the bounds-checked variant libeg_checked.so instead
+    (EG_CHECKED: every computed index is tested before the access, a miss is
+    reported in the status word; for tests, several times slower)."""
+    lib = LIB_CHECKED if checked else LIB
+    bdir = BUILD_CHECKED if checked else BUILD
+    extra = ["-DEG_CHECKED"] if checked else []
+    os.makedirs(bdir, exist_ok=True)
+    stamp = os.path.join(bdir, "stamp")
+    fp = _fingerprint() + ("-checked" if checked else "")
+    if not force and os.path.exists(lib) and os.path.exists(stamp):
         with open(stamp) as f:
             if f.read().strip() == fp:
-                return LIB
+                return lib
     nvcc = _nvcc()
     procs, objs = [], []
     for src in sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj]
+        cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra, "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -93,10 +103,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if r.returncode != 0:
         os.unlink(tmp)
         raise RuntimeError("link failed:\n" + r.stdout.decode(errors="replace"))
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     with open(stamp, "w") as f:
         f.write(fp)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

@@ -948,7 +948,7 @@ eg_status collect(eg_ctx *h, Result &r)
     if (r.err & kErrNaN) return EG_ERR_NAN;
     if (r.err & kErrNotConverged) return EG_ERR_NOT_CONVERGED;
     if (r.err & kErrTimeout) return EG_ERR_TIMEOUT;
-    if (r.err & kErrInternal) return EG_ERR_INTERNAL;
+    if (r.err & (kErrInternal | kErrBounds)) return EG_ERR_INTERNAL;
     return EG_OK;
 }
 

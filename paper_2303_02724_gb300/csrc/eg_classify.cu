@@ -33,6 +33,7 @@ template <uint32_t DT>
 __device__ __forceinline__ typename TypeKey<DT>::B load_bits(const FieldDev &F, uint32_t v)
 {
     using B = typename TypeKey<DT>::B;
+    if (!chk(v, F.N, F.err)) return B(0);
     if constexpr (DT == kF32) return __float_as_uint(__ldg(F.f + v));
     else if constexpr (sizeof(B) == 8) return B(__ldg(static_cast<const unsigned long long *>(F.fraw) + v));
     else return B(__ldg(static_cast<const unsigned int *>(F.fraw) + v));
@@ -194,7 +195,7 @@ __device__ __forceinline__ void classify_brick(const FieldDev &F, uint32_t b)
         const bool crit = v64 < F.N && b0 != 1;
         uint32_t tot;
         const uint32_t pos = block_excl_scan(crit ? 1u : 0u, s_scan, &tot);
-        if (crit) {
+        if (crit && chk(slot + running + pos, rec_cap(F), F.err) && chk(running + pos, F.bcap, F.err)) {
             F.rec_sid[slot + running + pos] = uint32_t(v64);
             F.rec_info[slot + running + pos] = D == 5 ? codess[i] : ((uint64_t(b0) << 56) | codess[i]);
             // (other element types get their value copies from the field
@@ -220,7 +221,7 @@ __device__ __forceinline__ void classify_brick(const FieldDev &F, uint32_t b)
         if (np) atomicAdd(&s_cnt[2], np);
     }
     __syncthreads();
-    if (tid == 0) F.bcnt[b] = make_uint4(s_cnt[0], s_cnt[1], s_cnt[2], 0u);
+    if (tid == 0 && chk(b, F.nbricks, F.err)) F.bcnt[b] = make_uint4(s_cnt[0], s_cnt[1], s_cnt[2], 0u);
 }
 
 template <int D, uint32_t DT>

@@ -164,6 +164,8 @@ k_classify_r4(const FieldDev *__restrict__ fields, int nf)
         else ok = ok && y + dy < n1 && z + dz < n2 && w + dw < n3;
         const uint32_t off = dy * s1 + dz * s2 + dw * s3;
         const uint32_t rb = neg ? vrow - off : vrow + off;  // (only used when ok)
+        if (ok && !(chk(uint64_t(rb) + x, F.N, F.err) && chk(uint64_t(rb) + min(x + kR4Vx, n0) - 1, F.N, F.err)))
+            ok = false;
         if (ok && vec && x + 3 < n0) {
             const float4 q4 = __ldg(reinterpret_cast<const float4 *>(F.f + rb + x));
             v[0] = q4.x;
@@ -179,12 +181,14 @@ k_classify_r4(const FieldDev *__restrict__ fields, int nf)
     // column x-1 (left) and x+4 (right) of a row whose segment is v
     auto left = [&](uint32_t rb, const float *v) {
         float l = __shfl_up_sync(0xffffffffu, v[kR4Vx - 1], 1);
-        if (lane == 0) l = (rb != 0xffffffffu && !first_t) ? __ldg(F.f + rb + x - 1) : qnan;
+        if (lane == 0) l = (rb != 0xffffffffu && !first_t && chk(uint64_t(rb) + x - 1, F.N, F.err)) ? __ldg(F.f + rb + x - 1) : qnan;
         return first_t ? qnan : l;
     };
     auto right = [&](uint32_t rb, const float *v) {
         float rr = __shfl_down_sync(0xffffffffu, v[0], 1);
-        if (lane == 31) rr = (rb != 0xffffffffu && !last_t) ? __ldg(F.f + rb + x + kR4Vx) : qnan;
+        if (lane == 31)
+            rr = (rb != 0xffffffffu && !last_t && chk(uint64_t(rb) + x + kR4Vx, F.N, F.err)) ? __ldg(F.f + rb + x + kR4Vx)
+                                                                                              : qnan;
         return last_t ? qnan : rr;
     };
 
@@ -323,7 +327,7 @@ k_classify_r4(const FieldDev *__restrict__ fields, int nf)
         info[i] = inf;
         if (cv) crit |= 1u << i;
     }
-    if (rowok) {
+    if (rowok && chk(uint64_t(vrow) + x + min(uint32_t(kR4Vx), n0 - x) - 1, F.N, F.err)) {
         uint32_t *dst = F.lab + vrow + x;
         if (vec && x + 3 < n0) {
             *reinterpret_cast<uint4 *>(dst) = make_uint4(asc[0], asc[1], asc[2], asc[3]);
@@ -342,6 +346,7 @@ k_classify_r4(const FieldDev *__restrict__ fields, int nf)
     for (int i = 0; i < kR4Vx; i++)
         if ((crit >> i) & 1u) {
             const uint64_t qd = slot0 + pos0 + k++;
+            if (!chk(qd, rec_cap(F), F.err) || !chk(qd - slot0, F.bcap, F.err)) continue;
             F.rec_sid[qd] = vrow + x + uint32_t(i);
             F.rec_info[qd] = info[i];
             F.rec_val[qd] = C[i + 1];
@@ -356,7 +361,7 @@ k_classify_r4(const FieldDev *__restrict__ fields, int nf)
         if (np) atomicAdd(&s_cnt[2], np);
     }
     __syncthreads();
-    if (tid == 0) F.bcnt[b] = make_uint4(s_cnt[0], s_cnt[1], s_cnt[2], 0u);
+    if (tid == 0 && chk(b, F.nbricks, F.err)) F.bcnt[b] = make_uint4(s_cnt[0], s_cnt[1], s_cnt[2], 0u);
 }
 
 cudaError_t launch_classify_r4(bool minimum, const FieldDev *fields, int nf, uint64_t bricks, cudaStream_t st)

@@ -95,7 +95,7 @@ __device__ __forceinline__ ZmCopy zm_copy_plan(uint32_t n0, bool vec)
 // Stream rows [ylo, yhi) of plane z into ring slot `buf` (or NaN-fill the slot
 // when z is past the last plane).  Always commits one cp.async group.
 __device__ __forceinline__ void zm_load_plane(const FieldDev &F, const ZmGeom &G, const ZmCopy &P, float *buf, int z,
-                                              uint32_t y0, uint32_t ylo, uint32_t yhi, bool vec)
+                                              uint32_t y0, uint32_t ylo, uint32_t yhi, bool vec, const float *ring)
 {
     const uint32_t rows = yhi - ylo;
     float *dst0 = buf + 8 + (ylo - y0 + 1) * G.rstride;
@@ -108,6 +108,15 @@ __device__ __forceinline__ void zm_load_plane(const FieldDev &F, const ZmGeom &G
     const uint32_t w = vec ? 4u : 1u;  // floats per unit
     for (uint32_t r = P.r0, c = P.c0; r < rows;) {
         float *d = dst0 + r * G.rstride + zm_col(int(w * c));
+        if (!chk_ptr<float>(d + w - 1, ring, 4 * uint64_t(G.rb), F.err) || !chk_ptr<float>(d, ring, 4 * uint64_t(G.rb), F.err)) {
+            r += P.dr;
+            c += P.dc;
+            if (c >= P.upr) {
+                c -= P.upr;
+                r++;
+            }
+            continue;
+        }
         if (fill) {
             const float qnan = __int_as_float(0x7fc00000);
             if (vec)
@@ -116,10 +125,12 @@ __device__ __forceinline__ void zm_load_plane(const FieldDev &F, const ZmGeom &G
                 *d = qnan;
         } else {
             const float *g = src0 + uint64_t(r) * G.n0 + w * c;
-            if (vec)
+            if (!chk_ptr(g + w - 1, F.f, F.N, F.err) || !chk_ptr(g, F.f, F.N, F.err)) {
+            } else if (vec) {
                 cp_async16(d, g);
-            else
+            } else {
                 cp_async4(d, g);
+            }
         }
         r += P.dr;
         c += P.dc;
@@ -321,9 +332,9 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
     }
     __syncthreads();
 
-    zm_load_plane(F, G, P, ring + ((zs - 1) & 3) * G.rb, zs - 1, y0, ylo, yhi, vec);
-    zm_load_plane(F, G, P, ring + (zs & 3) * G.rb, zs, y0, ylo, yhi, vec);
-    zm_load_plane(F, G, P, ring + ((zs + 1) & 3) * G.rb, zs + 1, y0, ylo, yhi, vec);
+    zm_load_plane(F, G, P, ring + ((zs - 1) & 3) * G.rb, zs - 1, y0, ylo, yhi, vec, ring);
+    zm_load_plane(F, G, P, ring + (zs & 3) * G.rb, zs, y0, ylo, yhi, vec, ring);
+    zm_load_plane(F, G, P, ring + ((zs + 1) & 3) * G.rb, zs + 1, y0, ylo, yhi, vec, ring);
 
     // thread t owns vertices x .. x+7 of brick row r; threads are in (row, x)
     // order, which is the brick's index order
@@ -339,10 +350,10 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
     for (int z = zs; z < ze; z++) {
         __syncthreads();  // A: previous step done (ring slot, counters final)
         if (tid == 0 && prev_brick != 0xffffffffu) {
-            F.bcnt[prev_brick] = make_uint4(s_cnt[0], s_cnt[1] - s_cnt[0], s_cnt[2], 0u);
+            if (chk(prev_brick, F.nbricks, F.err)) F.bcnt[prev_brick] = make_uint4(s_cnt[0], s_cnt[1] - s_cnt[0], s_cnt[2], 0u);
             s_cnt[0] = s_cnt[1] = s_cnt[2] = s_cnt[3] = 0;
         }
-        zm_load_plane(F, G, P, ring + ((z + 2) & 3) * G.rb, z + 2, y0, ylo, yhi, vec);
+        zm_load_plane(F, G, P, ring + ((z + 2) & 3) * G.rb, z + 2, y0, ylo, yhi, vec, ring);
         cp_async_wait1();
         __syncthreads();  // B: plane z+1 visible, counters reset
 
@@ -369,8 +380,12 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
             const float qnan = __int_as_float(0x7fc00000);
             const bool first_t = txt == 0, last_t = txt + 1 == txn;
             // 8 values of columns x..x+7 of ring row `row`
+            const uint64_t ringn = 4 * uint64_t(G.rb);
             auto seg = [&](const float *row, float *v) {
-                if (vec) {
+                if (!chk_ptr(row + x - 8, ring, ringn, F.err) || !chk_ptr(row + x + 15, ring, ringn, F.err)) {
+#pragma unroll
+                    for (int b = 0; b < kVx; b++) v[b] = qnan;
+                } else if (vec) {
                     const uint32_t h = (x >> 3) & 4u;  // stored order of the two halves
                     const float4 q0 = *reinterpret_cast<const float4 *>(row + x + h);
                     const float4 q1 = *reinterpret_cast<const float4 *>(row + x + (h ^ 4u));
@@ -384,13 +399,14 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
             // column x-1: the left lane's last value, or a load at a warp edge
             auto left = [&](const float *row, float last) {
                 float l = __shfl_up_sync(0xffffffffu, last, 1);
-                if (lane == 0) l = row[zm_col(int(x) - 1)];
+                if (lane == 0) l = chk_ptr(row + zm_col(int(x) - 1), ring, ringn, F.err) ? row[zm_col(int(x) - 1)] : qnan;
                 return first_t ? qnan : l;
             };
             // column x+8: the right lane's first value, or a load at a warp edge
             auto right = [&](const float *row, float first) {
                 float v = __shfl_down_sync(0xffffffffu, first, 1);
-                if (lane == 31) v = row[zm_col(int(x) + kVx)];
+                if (lane == 31)
+                    v = chk_ptr(row + zm_col(int(x) + kVx), ring, ringn, F.err) ? row[zm_col(int(x) + kVx)] : qnan;
                 return last_t ? qnan : v;
             };
 #pragma unroll
@@ -466,7 +482,8 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
             um4[0] = make_uint4(um[0], um[1], um[2], um[3]);
             um4[1] = make_uint4(um[4], um[5], um[6], um[7]);
             uint32_t *dst = F.lab + vrow;
-            if (vec) {
+            if (!chk(uint64_t(vrow) + min(uint32_t(kVx), G.n0 - x) - 1, F.N, F.err)) {
+            } else if (vec) {
                 // n0 is a multiple of 4, so x+3 < n0; the second half may be past the row
                 *reinterpret_cast<uint4 *>(dst) = make_uint4(asc[0], asc[1], asc[2], asc[3]);
                 if (x + 7 < G.n0) *reinterpret_cast<uint4 *>(dst + 4) = make_uint4(asc[4], asc[5], asc[6], asc[7]);
@@ -528,6 +545,14 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
                 const uint32_t upper = w & 0x3fffu, sl = w >> 14;
                 const float *orow = Cb + orr * rs;
                 const uint64_t q = slot0 + pw + j;
+                // (the record stays inside its brick's slot; the 14
+                // neighbours lie within one row and one plane of the ring)
+                const bool qok = chk(q, rec_cap(F), F.err) && chk(pw + j, F.bcap, F.err);
+                const bool nok = chk_ptr(orow + dD - int(rs) + zm_col(int(ox + i) - 1), ring, 4 * uint64_t(G.rb), F.err) &&
+                                 chk_ptr(orow + dU + int(rs) + zm_col(int(ox + i) + 1), ring, 4 * uint64_t(G.rb), F.err) &&
+                                 chk_ptr(orow - int(rs), ring, 4 * uint64_t(G.rb), F.err) &&
+                                 chk_ptr(orow + int(rs) + zm_col(int(ox + i) + 1), ring, 4 * uint64_t(G.rb), F.err);
+                if (!qok || !nok) continue;
                 F.rec_sid[q] = ovrow + i;
                 F.rec_val[q] = orow[zm_col(int(ox + i))];
                 uint64_t inf = 0;
@@ -549,7 +574,7 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
     }
     __syncthreads();
     if (tid == 0 && prev_brick != 0xffffffffu)
-        F.bcnt[prev_brick] = make_uint4(s_cnt[0], s_cnt[1] - s_cnt[0], s_cnt[2], 0u);
+        if (chk(prev_brick, F.nbricks, F.err)) F.bcnt[prev_brick] = make_uint4(s_cnt[0], s_cnt[1] - s_cnt[0], s_cnt[2], 0u);
     if (anynan) atomicOr(F.err, kErrNaN);
     // drain this item's outstanding (empty) copy groups before the ring is reused
     asm volatile("cp.async.wait_all;\n" ::: "memory");

@@ -21,7 +21,8 @@ constexpr int kEmitThreads = 256;
 // Sorted unique arc ends of one saddle; returns their count.
 template <int KD>
 __device__ __forceinline__ int saddle_ends(const uint32_t *lab, const uint32_t (&s)[kMaxDim], uint32_t sid,
-                                           uint64_t info, uint32_t (&t)[CompBound<KD>::value])
+                                           uint64_t info, uint32_t (&t)[CompBound<KD>::value], uint32_t N,
+                                           uint32_t *err)
 {
     // the representatives in record order (the ends are sorted below)
     constexpr int kCap = CompBound<KD>::value;
@@ -36,7 +37,8 @@ __device__ __forceinline__ int saddle_ends(const uint32_t *lab, const uint32_t (
         } else {
             k = int((info >> (5 * c)) & 31u);
         }
-        const uint32_t m = lab[slot_vertex<KD>(sid, k, s)];
+        const uint32_t rv = slot_vertex<KD>(sid, k, s);
+        const uint32_t m = chk(rv, N, err) ? lab[rv] : 0u;
         int j = n;
         bool dup = false;
         while (j > 0 && t[j - 1] >= m) {
@@ -99,6 +101,7 @@ k_nodes(const FieldDev *__restrict__ fields, int nf, uint64_t base, uint64_t bri
     uint32_t s[kMaxDim];
 #pragma unroll
     for (int i = 0; i < kMaxDim; i++) s[i] = F.s[i];
+    if (!chk(b, F.nbricks, F.err)) return;
     const uint4 c = F.bcnt[b];
     const uint4 o = F.boff[b];
     const uint32_t nrec = c.x + c.y;
@@ -114,7 +117,8 @@ k_nodes(const FieldDev *__restrict__ fields, int nf, uint64_t base, uint64_t bri
         uint64_t info = ~0ull;
         float val = 0.f;
         uint64_t mine = 0;
-        if (r < nrec) {
+        const bool have = r < nrec && chk(slot + r, rec_cap(F), F.err) && chk(r, F.bcap, F.err);
+        if (have) {
             sid = F.rec_sid[slot + r];
             info = F.rec_info[slot + r];
             val = F.rec_val[slot + r];
@@ -124,7 +128,7 @@ k_nodes(const FieldDev *__restrict__ fields, int nf, uint64_t base, uint64_t bri
         uint64_t tot;
         const uint64_t pos = run + warp_excl_scan_u64(mine, &tot);
         run += tot;
-        if (r >= nrec) continue;
+        if (!have) continue;
         const uint64_t b0 = uint64_t(rec_b0<KD>(info));
         const uint64_t lm = pos & 0xffffu, ls = (pos >> 16) & 0xffffu, lp = pos >> 32;
         if (b0 == 0) {
@@ -138,7 +142,7 @@ k_nodes(const FieldDev *__restrict__ fields, int nf, uint64_t base, uint64_t bri
             }
         } else {
             const uint64_t q = s_off + ls, p = p_off + lp;
-            const int u = saddle_ends<KD>(F.lab, s, sid, info, tmp);
+            const int u = saddle_ends<KD>(F.lab, s, sid, info, tmp, F.N, F.err);
             if (q < capS && p + b0 <= capP) {
                 F.saddles[q] = sid;
                 F.sad_b0[q] = uint8_t(b0);
@@ -167,6 +171,7 @@ k_csr(const FieldDev *__restrict__ fields, int nf, uint64_t bricks)
     const int fi = find_field<false>(fields, nf, g);
     const FieldDev &F = fields[fi];
     const uint32_t b = uint32_t(g - F.brick0);
+    if (!chk(b, F.nbricks, F.err)) return;
     const uint4 c = F.bcnt[b];
     const uint4 o = F.boff[b];
     const uint32_t ns = c.y;

@@ -91,7 +91,45 @@ enum : uint32_t {
     kErrNotConverged = 2u,
     kErrTimeout = 4u,
     kErrInternal = 8u,
+    kErrBounds = 16u,  // bounds-checked build: an index out of its array (access skipped)
 };
+
+// Bounds-checked build (compiled with EG_CHECKED): every index the kernels
+// compute into a field's arrays, the records, the shared-memory rings and the
+// outputs is tested against the array's size before the access; an index out
+// of range sets kErrBounds in the status word and the access is skipped (a
+// load yields 0), so a faulty index is reported, never dereferenced.  The
+// regular build compiles the tests away.
+#ifdef EG_CHECKED
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+
+// true iff i < n; in the checked build a false also sets kErrBounds
+__device__ __forceinline__ bool chk(uint64_t i, uint64_t n, uint32_t *err)
+{
+    if constexpr (!kChecked) {
+        return true;
+    } else {
+        if (i < n) return true;
+        atomicOr(err, kErrBounds);
+        return false;
+    }
+}
+
+// pointer p inside [base, base + n) (elements of p's type)
+template <typename T>
+__device__ __forceinline__ bool chk_ptr(const T *p, const T *base, uint64_t n, uint32_t *err)
+{
+    if constexpr (!kChecked) {
+        return true;
+    } else {
+        const bool ok = p >= base && uint64_t(p - base) < n;
+        if (!ok) atomicOr(err, kErrBounds);
+        return ok;
+    }
+}
 
 // flags carried per field
 enum : uint32_t { kFlagMinimum = 1u, kFlagNoLabels = 2u, kFlagPaths = 8u };
@@ -236,6 +274,9 @@ struct FieldDev {
     uint32_t flags;
     uint32_t dtype;          // element type of fraw
 };
+
+// Record slots of a field (nbricks slots of bcap entries each).
+__host__ __device__ __forceinline__ uint64_t rec_cap(const FieldDev &F) { return uint64_t(F.nbricks) * F.bcap; }
 
 __host__ __device__ __forceinline__ void brick_range(const FieldDev &F, uint32_t b, uint64_t &v0, uint32_t &len)
 {

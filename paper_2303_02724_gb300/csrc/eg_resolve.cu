@@ -38,7 +38,7 @@ __device__ __forceinline__ void resolve_brick(const FieldDev &F, uint32_t b)
             const uint32_t i = base + q * kResolveThreads;
             v[q] = uint32_t(v0) + i;
             u[q] = v[q];
-            if (i < len) {
+            if (i < len && chk(v[q], F.N, F.err)) {
                 u[q] = lab[v[q]];
                 if (u[q] != v[q]) live |= 1u << q;
             }
@@ -48,6 +48,11 @@ __device__ __forceinline__ void resolve_brick(const FieldDev &F, uint32_t b)
 #pragma unroll
             for (int q = 0; q < kIlp; q++)
                 if ((live >> q) & 1u) {
+                    if (!chk(u[q], F.N, F.err)) {
+                        live &= ~(1u << q);
+                        moved &= ~(1u << q);
+                        continue;
+                    }
                     const uint32_t w = lab[u[q]];
                     if (w == u[q]) {
                         live &= ~(1u << q);
@@ -174,7 +179,7 @@ k_resolve_tile(const FieldDev *__restrict__ fields, int nf)
 #pragma unroll
         for (int b = 0; b < kTb; b++) {
             const uint32_t i = i0 + b * kTileThreads + threadIdx.x;
-            a[b] = inside(i) ? lab[gid(i)] : 0u;
+            a[b] = inside(i) && chk(gid(i), F.N, F.err) ? lab[gid(i)] : 0u;
         }
 #pragma unroll
         for (int b = 0; b < kTb; b++) {
@@ -200,7 +205,7 @@ k_resolve_tile(const FieldDev *__restrict__ fields, int nf)
                            : uint16_t(uint16_t(i) | kDone | kOut);
                 }
             }
-            s_w[i] = w;
+            if (chk(i, kTileMax, F.err)) s_w[i] = w;
         }
     }
     __syncthreads();
@@ -210,7 +215,7 @@ k_resolve_tile(const FieldDev *__restrict__ fields, int nf)
         int changed = 0;
         for (uint32_t i = threadIdx.x; i < T; i += kTileThreads) {
             const uint16_t w = s_w[i];
-            if (!(w & kDone)) {
+            if (!(w & kDone) && chk(w & kIdx, kTileMax, F.err)) {
                 s_w[i] = s_w[w & kIdx];
                 changed = 1;
             }
@@ -225,7 +230,8 @@ k_resolve_tile(const FieldDev *__restrict__ fields, int nf)
         for (int b = 0; b < kTb; b++) {
             const uint32_t i = i0 + b * kTileThreads + threadIdx.x;
             const uint16_t w = s_w[i];
-            if (inside(i) && (w & kIdx) != i) lab[gid(i)] = (w & kOut) ? lab[gid(w & kIdx)] : gid(w & kIdx);
+            if (inside(i) && (w & kIdx) != i && chk(gid(i), F.N, F.err) && chk(gid(w & kIdx), F.N, F.err))
+                lab[gid(i)] = (w & kOut) ? lab[gid(w & kIdx)] : gid(w & kIdx);
         }
     }
 }

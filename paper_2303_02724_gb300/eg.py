@@ -15,7 +15,9 @@ from typing import Optional, Sequence
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libeg.so")
+# EG_CHECKED_LIBRARY=1 selects the bounds-checked build (libeg_checked.so,
+# built by _build.build(checked=True)) for test runs
+LIB_PATH = os.path.join(_HERE, "libeg_checked.so" if os.environ.get("EG_CHECKED_LIBRARY") == "1" else "libeg.so")
 MAX_DIM = 5
 
 EG_OK, EG_ERR_ARG, EG_ERR_NAN, EG_ERR_OOM, EG_ERR_CUDA = 0, 1, 2, 3, 4

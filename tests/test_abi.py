@@ -126,3 +126,12 @@ def test_labels_static_checks_arguments_before_any_launch():
         eg.labels_static(torch.zeros((5, 4), dtype=torch.float32).t(), torch.zeros((4, 5), dtype=torch.int32))
     with pytest.raises(ValueError, match="CUDA"):
         eg.labels_static(f, torch.zeros((4, 5), dtype=torch.int32))
+
+
+def test_checked_build_compiles_with_the_same_symbols():
+    """The bounds-checked variant (EG_CHECKED) builds and exports exactly the
+    declared symbols (no GPU needed)."""
+    path = _build.build(checked=True)
+    assert path.endswith("libeg_checked.so")
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    assert set(re.findall(r"\b(eg_\w+)\b", out)) == set(_declared_symbols())
