@@ -264,9 +264,11 @@ EG_API eg_status eg_get_bundled(eg_handle h, eg_result_id id, uint8_t *keep);
  * n_cancelled, n_rounds (may be NULL): cancelled saddles, device rounds run.
  * The simplified graph is the kept saddles with the survivors of their arc
  * ends.  Runs on the handle's own stream and waits for it.
+ * The rounds run in one cooperative launch whose grid barriers wait at most
+ * about a second each (EG_ERR_TIMEOUT if one gives up).
  * Errors: EG_ERR_ARG (unknown id, NaN tau, a result that is not float32,
- * NULL outputs with saddles or maxima present), EG_ERR_OOM, EG_ERR_INTERNAL,
- * plus any deferred device status as eg_get_graph. */
+ * NULL outputs with saddles or maxima present), EG_ERR_OOM, EG_ERR_TIMEOUT,
+ * EG_ERR_INTERNAL, plus any deferred device status as eg_get_graph. */
 EG_API eg_status eg_get_cancelled(eg_handle h, eg_result_id id, float tau, uint8_t *alive, uint32_t *survivor,
                                   int64_t *n_cancelled, int32_t *n_rounds);
 

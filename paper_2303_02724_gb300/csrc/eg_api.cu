@@ -1422,7 +1422,7 @@ eg_status eg_get_cancelled(eg_handle h, eg_result_id id, float tau, uint8_t *ali
     };
     const uint64_t M = r.M, S = r.S, A = r.A;
     const size_t sizes[kBufs] = {4 * A, 4 * A, 4 * M, 8 * M, 8 * M, 8 * S, 8 * S, 4 * S, S,
-                                 4 * S, 4 * S, 64, S, 4 * M};
+                                 4 * S, 4 * S, 128, S, 4 * M};
     cudaError_t e;
     for (int i = 0; i < kBufs; i++)
         if ((e = h->pool.alloc(&buf[i], std::max<size_t>(sizes[i], 16))) != cudaSuccess) return done(from_cuda(e));
@@ -1443,41 +1443,20 @@ eg_status eg_get_cancelled(eg_handle h, eg_result_id id, float tau, uint8_t *ali
     C.list[0] = static_cast<uint32_t *>(buf[9]);
     C.list[1] = static_cast<uint32_t *>(buf[10]);
     C.ctrl = static_cast<unsigned long long *>(buf[11]);
-    C.err = reinterpret_cast<uint32_t *>(C.ctrl + 4);
+    C.err = reinterpret_cast<uint32_t *>(C.ctrl + 12);
     C.M = uint32_t(M);
     C.S = uint32_t(S);
     C.tau = tau;
     C.minimum = (r.flags & kFlagMinimum) ? 1 : 0;
-    const unsigned long long ctrl0[5] = {~0ull, 0ull, S, 0ull, 0ull};
+    // round slot 0 = {no key, 0, 0}, the rest (rounds, barrier, status) zero
+    unsigned long long ctrl0[13] = {};
+    ctrl0[0] = ~0ull;
     if ((e = cudaMemcpyAsync(C.ctrl, ctrl0, sizeof ctrl0, cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return done(from_cuda(e));
     if ((e = launch_cancel_setup(C, static_cast<const uint32_t *>(r.col), A, st)) != cudaSuccess)
         return done(from_cuda(e));
-    h->launches += 2;
-    // multi-CTA rounds while many saddles wait (each round cancels at least
-    // one saddle until none is left to cancel), then the one-CTA tail
-    constexpr uint64_t kTail = 32768;
-    int p = 0, rounds = 0;
-    uint64_t waiting = S;
-    bool finished = S == 0;
-    while (!finished && waiting > kTail) {
-        if ((e = launch_cancel_round(C, p, waiting, st)) != cudaSuccess) return done(from_cuda(e));
-        h->launches += 4;
-        rounds++;
-        p ^= 1;
-        unsigned long long back[4];
-        if ((e = cudaMemcpyAsync(back, C.ctrl, sizeof back, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
-            return done(from_cuda(e));
-        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return done(from_cuda(e));
-        waiting = back[2 + p];
-        finished = back[1] == 0 || waiting == 0;
-        if (rounds > int64_t(S) + 1) return done(EG_ERR_INTERNAL);
-    }
-    if (!finished) {
-        if ((e = launch_cancel_tail(C, p, st)) != cudaSuccess) return done(from_cuda(e));
-        h->launches += 1;
-        rounds++;
-    }
+    if ((e = launch_cancel_rounds(C, h->sm_count, st)) != cudaSuccess) return done(from_cuda(e));
+    h->launches += 3;
     uint8_t *dalive = static_cast<uint8_t *>(buf[12]);
     uint32_t *dsurv = static_cast<uint32_t *>(buf[13]);
     if ((e = launch_cancel_out(C, dalive, dsurv, st)) != cudaSuccess) return done(from_cuda(e));
@@ -1489,13 +1468,18 @@ eg_status eg_get_cancelled(eg_handle h, eg_result_id id, float tau, uint8_t *ali
         return done(from_cuda(e));
     if ((e = cudaMemcpyAsync(&herr, C.err, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return done(from_cuda(e));
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return done(from_cuda(e));
+    if (herr & kErrTimeout) return done(EG_ERR_TIMEOUT);
     if (herr) return done(EG_ERR_INTERNAL);
     if (n_cancelled) {
         int64_t c = 0;
         for (uint64_t i = 0; i < S; i++) c += alive[i] ? 0 : 1;
         *n_cancelled = c;
     }
-    if (n_rounds) *n_rounds = int32_t(rounds);
+    if (n_rounds) {
+        unsigned long long rounds = 0;
+        if ((e = cudaMemcpy(&rounds, C.ctrl + 9, 8, cudaMemcpyDeviceToHost)) != cudaSuccess) return done(from_cuda(e));
+        *n_rounds = int32_t(rounds);
+    }
     return done(EG_OK);
 }
 

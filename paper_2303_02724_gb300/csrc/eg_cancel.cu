@@ -41,12 +41,14 @@
 // following the merges, cost and lb keys, the per-maximum minimum of lb keys,
 // the global cheapest), second minima per maximum, decide (cancel, and point
 // each dying maximum at its survivor), reset the per-maximum minima and keep
-// the still-waiting saddles for the next round.  While many saddles wait, a
-// round is four launches over all CTAs; the tail (few saddles, often many
-// rounds of one or two cancellations between a few large maxima) runs in one
-// CTA with block barriers.  Keys are (float32 bits of a non-negative cost)
+// the still-waiting saddles for the next round.  All rounds run in one
+// cooperative launch with grid barriers between the phases (late rounds often
+// cancel one or two saddles between a few large maxima, so their number can
+// be large; a launch per round would cost far more).  Keys are (float32 bits of a non-negative cost)
 // << 32 | saddle index, so one 64-bit atomicMin orders by cost, then by
 // vertex id (saddles are in id order).
+#include <algorithm>
+
 #include "eg_internal.cuh"
 #include "eg_kernels.h"
 
@@ -228,94 +230,105 @@ __global__ void k_cancel_init(CancelDev C)
     }
 }
 
-// Multi-CTA round over the waiting list `in` (count ctrl[2 + p]); the next
-// list goes to `out` (count ctrl[2 + !p], zeroed by the host).
-__global__ void __launch_bounds__(kCancelThreads) k_cancel_eval(CancelDev C, int p)
+// Grid-wide barrier of the cooperative kernel below (every CTA is resident:
+// cooperative launch).  The last CTA to arrive resets the count and advances
+// the generation; the others wait for the generation to change, for at most
+// about a second (kSpinLimit rounds of a growing sleep), after which they set
+// kErrTimeout and report failure instead of hanging.
+__device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned *gen, uint32_t *err)
 {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long gk = kNoKey;
-    if (i < uint32_t(C.ctrl[2 + p])) gk = c_eval(C, C.list[p][i]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long y = __shfl_xor_sync(0xffffffffu, gk, o);
-        gk = y < gk ? y : gk;
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned g = *reinterpret_cast<volatile unsigned *>(gen);
+        __threadfence();
+        if (atomicAdd(count, 1u) == gridDim.x - 1) {
+            *reinterpret_cast<volatile unsigned *>(count) = 0u;
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            unsigned ns = 32;
+            uint32_t spins = 0;
+            while (*reinterpret_cast<volatile unsigned *>(gen) == g) {
+                if (++spins > kSpinLimit) {
+                    atomicOr(err, kErrTimeout);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(ns);
+                ns = ns < 256 ? ns * 2 : 256;
+            }
+        }
+        __threadfence();
+        s_ok = ok;
     }
-    if ((threadIdx.x & 31) == 0 && gk != kNoKey) atomicMin(C.ctrl, gk);
+    __syncthreads();
+    return s_ok != 0;
 }
 
-__global__ void __launch_bounds__(kCancelThreads) k_cancel_second(CancelDev C, int p)
+// All rounds in one cooperative launch: the CTAs share the waiting list with
+// grid-stride loops, separated by grid barriers (four per round).  The
+// control words of round r live in slot r % 3 ({cheapest key, cancellations,
+// next list length}); slot (r + 1) % 3 is cleared during round r, which no
+// CTA can still be reading (it was last used two rounds before).  The loop
+// ends with the first round that cancels nothing, or when a barrier gives
+// up.  ctrl[9] receives the number of rounds.
+__global__ void __launch_bounds__(kCancelThreads) k_cancel_rounds(CancelDev C)
 {
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < uint32_t(C.ctrl[2 + p])) c_second(C, C.list[p][i]);
-}
-
-__global__ void __launch_bounds__(kCancelThreads) k_cancel_decide(CancelDev C, int p)
-{
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-    int c = 0;
-    if (i < uint32_t(C.ctrl[2 + p])) c = c_decide(C, C.list[p][i], C.ctrl[0]);
-    c = __reduce_add_sync(0xffffffffu, c);
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(C.ctrl + 1, (unsigned long long)c);
-}
-
-__global__ void __launch_bounds__(kCancelThreads) k_cancel_reset(CancelDev C, int p)
-{
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned *bar = reinterpret_cast<unsigned *>(C.ctrl + 10);  // [0] count, [1] generation
+    const uint64_t tid = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
     const int lane = threadIdx.x & 31;
-    bool keep = false;
-    uint32_t s = 0;
-    if (i < uint32_t(C.ctrl[2 + p])) {
-        s = C.list[p][i];
-        keep = c_reset(C, s);
-    }
-    const unsigned m = __ballot_sync(0xffffffffu, keep);
-    if (!m) return;
-    unsigned long long b = 0;
-    if (lane == __ffs(m) - 1) b = atomicAdd(C.ctrl + 2 + (p ^ 1), (unsigned long long)__popc(m));
-    b = __shfl_sync(0xffffffffu, b, __ffs(m) - 1);
-    if (keep) C.list[p ^ 1][b + __popc(m & ((1u << lane) - 1u))] = s;
-}
-
-// The tail: once few saddles wait, one CTA runs the remaining rounds (block
-// barriers instead of launches) until a round cancels nothing.  The round
-// count is bounded by the waiting saddles (each round cancels at least one).
-__global__ void __launch_bounds__(1024) k_cancel_tail(CancelDev C, int p)
-{
-    __shared__ unsigned long long s_gmin;
-    __shared__ unsigned s_count, s_next;
-    const int tid = threadIdx.x;
-    unsigned n = unsigned(C.ctrl[2 + p]);
-    const unsigned bound = n + 1;  // rounds that cancel something: at most the waiting saddles
-    for (unsigned round = 0; round <= bound && n > 0; round++) {
+    int p = 0;
+    unsigned long long n = C.S;
+    uint32_t round = 0;
+    while (n > 0 && round <= C.S) {
+        unsigned long long *slot = C.ctrl + 3 * (round % 3);
         if (tid == 0) {
-            s_gmin = kNoKey;
-            s_count = 0;
-            s_next = 0;
+            unsigned long long *nx = C.ctrl + 3 * ((round + 1) % 3);
+            nx[0] = kNoKey;
+            nx[1] = 0;
+            nx[2] = 0;
         }
-        __syncthreads();
-        for (unsigned i = tid; i < n; i += blockDim.x) {
+        // 1: evaluate
+        for (uint64_t i = tid; i < n; i += stride) {
             const unsigned long long k = c_eval(C, C.list[p][i]);
-            if (k != kNoKey) atomicMin(&s_gmin, k);
+            if (k != kNoKey) atomicMin(slot, k);
         }
-        __syncthreads();
-        for (unsigned i = tid; i < n; i += blockDim.x) c_second(C, C.list[p][i]);
-        __syncthreads();
-        const unsigned long long gmin = s_gmin;
-        for (unsigned i = tid; i < n; i += blockDim.x)
-            if (c_decide(C, C.list[p][i], gmin)) atomicAdd(&s_count, 1u);
-        __syncthreads();
-        for (unsigned i = tid; i < n; i += blockDim.x) {
-            const uint32_t s = C.list[p][i];
-            if (c_reset(C, s)) C.list[p ^ 1][atomicAdd(&s_next, 1u)] = s;
+        if (!grid_barrier(bar, bar + 1, C.err)) break;
+        // 2: second minima
+        for (uint64_t i = tid; i < n; i += stride) c_second(C, C.list[p][i]);
+        if (!grid_barrier(bar, bar + 1, C.err)) break;
+        // 3: decide
+        const unsigned long long gmin = *reinterpret_cast<volatile unsigned long long *>(slot);
+        for (uint64_t i = tid; i < n; i += stride)
+            if (c_decide(C, C.list[p][i], gmin)) atomicAdd(slot + 1, 1ull);
+        if (!grid_barrier(bar, bar + 1, C.err)) break;
+        // 4: reset the per-maximum minima, keep the waiting saddles
+        const unsigned long long cancelled = *reinterpret_cast<volatile unsigned long long *>(slot + 1);
+        for (uint64_t base = tid - lane; base < n; base += stride) {
+            const uint64_t i = base + lane;
+            bool keep = false;
+            uint32_t s = 0;
+            if (i < n) {
+                s = C.list[p][i];
+                keep = c_reset(C, s);
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, keep);
+            if (!m) continue;
+            unsigned long long b = 0;
+            if (lane == __ffs(m) - 1) b = atomicAdd(slot + 2, (unsigned long long)__popc(m));
+            b = __shfl_sync(0xffffffffu, b, __ffs(m) - 1);
+            if (keep) C.list[p ^ 1][b + __popc(m & ((1u << lane) - 1u))] = s;
         }
-        __syncthreads();
-        const unsigned cancelled = s_count;
-        n = s_next;
+        if (!grid_barrier(bar, bar + 1, C.err)) break;
+        round++;
+        n = *reinterpret_cast<volatile unsigned long long *>(slot + 2);
         p ^= 1;
-        __syncthreads();
         if (cancelled == 0) break;
     }
-    if (tid == 0) C.ctrl[1] = 0;
+    if (tid == 0) C.ctrl[9] = round;
 }
 
 // Results: keep flag per saddle, vertex id of each maximum's survivor.
@@ -336,25 +349,20 @@ cudaError_t launch_cancel_setup(const CancelDev &C, const uint32_t *col, uint64_
     return cudaGetLastError();
 }
 
-cudaError_t launch_cancel_round(const CancelDev &C, int p, uint64_t waiting, cudaStream_t st)
+cudaError_t launch_cancel_rounds(const CancelDev &C, int sm_count, cudaStream_t st)
 {
-    cudaError_t e;
-    // ctrl[0] = no key, ctrl[1] = 0, next list count = 0
-    if ((e = cudaMemsetAsync(C.ctrl, 0xff, sizeof(unsigned long long), st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(C.ctrl + 1, 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(C.ctrl + 2 + (p ^ 1), 0, sizeof(unsigned long long), st)) != cudaSuccess) return e;
-    if (waiting == 0) return cudaSuccess;
-    k_cancel_eval<<<grid_of(waiting), kCancelThreads, 0, st>>>(C, p);
-    k_cancel_second<<<grid_of(waiting), kCancelThreads, 0, st>>>(C, p);
-    k_cancel_decide<<<grid_of(waiting), kCancelThreads, 0, st>>>(C, p);
-    k_cancel_reset<<<grid_of(waiting), kCancelThreads, 0, st>>>(C, p);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_cancel_tail(const CancelDev &C, int p, cudaStream_t st)
-{
-    k_cancel_tail<<<1, 1024, 0, st>>>(C, p);
-    return cudaGetLastError();
+    if (C.S == 0) return cudaSuccess;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cancel_rounds, kCancelThreads, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    uint64_t grid = uint64_t(std::max(sm_count, 1)) * uint64_t(std::min(per_sm, 4));
+    const uint64_t need = (uint64_t(C.S) + kCancelThreads - 1) / kCancelThreads;
+    if (grid > need) grid = need;
+    CancelDev arg = C;
+    void *args[] = {&arg};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<void *>(k_cancel_rounds), dim3(unsigned(grid)),
+                                       dim3(kCancelThreads), args, 0, st);
 }
 
 cudaError_t launch_cancel_out(const CancelDev &C, uint8_t *alive, uint32_t *survivor, cudaStream_t st)

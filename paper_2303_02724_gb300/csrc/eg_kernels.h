@@ -111,19 +111,17 @@ struct CancelDev {
     uint32_t *high;              // [S] highest current maximum of the saddle
     uint8_t *state;              // [S] 0 waiting, 1 cancelled, 2 never cancelled
     uint32_t *list[2];           // [S] each: waiting saddles of this / the next round
-    unsigned long long *ctrl;    // [0] cheapest cancellable key, [1] cancellations this
-                                 // round, [2], [3] counts of list[0], list[1]
+    unsigned long long *ctrl;    // [3 r .. 3 r + 2] round slot r (cheapest key, cancellations,
+                                 // next list length), [9] rounds, [10] grid barrier
     uint32_t *err;               // status word
     uint32_t M, S;
     float tau;
     int minimum;
 };
-// Set-up (every saddle waits, in list[0]); one multi-CTA round over list[p]
-// (`waiting` = its count, read back by the host); the one-CTA tail from
-// list[p] to the end; the results.
+// Set-up (every saddle waits, in list[0], ctrl zeroed but slot 0's key, which
+// is all ones); all rounds in one cooperative launch; the results.
 cudaError_t launch_cancel_setup(const CancelDev &C, const uint32_t *col, uint64_t A, cudaStream_t st);
-cudaError_t launch_cancel_round(const CancelDev &C, int p, uint64_t waiting, cudaStream_t st);
-cudaError_t launch_cancel_tail(const CancelDev &C, int p, cudaStream_t st);
+cudaError_t launch_cancel_rounds(const CancelDev &C, int sm_count, cudaStream_t st);
 cudaError_t launch_cancel_out(const CancelDev &C, uint8_t *alive, uint32_t *survivor, cudaStream_t st);
 
 }  // namespace eg
