@@ -275,7 +275,13 @@ Layout make_layout(const Shape &sh, int sm_count, const eg_config &cfg, uint32_t
         // (rows of more than 1024 vertices: one row per brick)
         const uint32_t txn = (n0 + 7) / 8;
         uint32_t ty = 256 / txn;
-        if (cfg.classify_rows >= 1) ty = std::min<uint32_t>(ty, uint32_t(cfg.classify_rows));
+        if (cfg.classify_rows >= 1) {
+            ty = std::min<uint32_t>(ty, uint32_t(cfg.classify_rows));
+        } else if (uint64_t((n1 + ty - 1) / ty) * n2 < uint64_t(std::max(sm_count, 1))) {
+            // a small field: thinner row blocks, so that its bricks (and the
+            // CTAs of every step) cover the GPU
+            ty = std::max<uint32_t>(1, std::min<uint32_t>(ty, uint32_t(uint64_t(n1) * n2 / uint64_t(std::max(sm_count, 1)))));
+        }
         // rows per brick: the saddle queue of the classifier stores ring rows in 7 bits
         ty = std::max<uint32_t>(1, std::min(std::min(ty, 126u), n1));
         L.zm = true;

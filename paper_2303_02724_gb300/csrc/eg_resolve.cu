@@ -125,6 +125,7 @@ constexpr int kTileThreads = 256;
 constexpr uint32_t kTileMax = 8192;
 constexpr uint16_t kDone = 0x8000u, kOut = 0x4000u, kIdx = 0x3fffu;
 constexpr int kTb = 8;  // elements per thread per pass (loads in flight)
+constexpr uint32_t kTileSmallField = 1u << 20;  // fields up to this size always take the tiled pass
 
 void resolve_tile_shape(uint32_t n0, uint32_t n1, uint32_t n2, uint32_t rt[3], uint64_t *tiles)
 {
@@ -153,8 +154,10 @@ k_resolve_tile(const FieldDev *__restrict__ fields, int nf)
         else hi = mid - 1;
     }
     const FieldDev &F = fields[lo];
-    // dense maxima: short paths, the brick walks are faster on their own
-    if (F.kd != 3 || uint64_t(F.totals[0]) * 100 >= uint64_t(F.N)) return;
+    // dense maxima: short paths, the brick walks are faster on their own --
+    // unless the field is small, where a few long paths (e.g. up the slopes of
+    // smooth regions) set the walks' latency and the tiles cut them short
+    if (F.kd != 3 || (uint64_t(F.totals[0]) * 100 >= uint64_t(F.N) && F.N > kTileSmallField)) return;
     const uint32_t lx = F.rt[0], ly = F.rt[1], lz = F.rt[2];
     const uint32_t TX = 1u << lx, TY = 1u << ly, T = 1u << (lx + ly + lz);
     const uint32_t n0 = F.n[0], n1 = F.n[1], n2 = F.n[2];
