@@ -159,6 +159,11 @@ EG_API eg_status eg_destroy(eg_handle h);
  * read; d in 1..5; extents[0..d-1] >= 1, product < 2^32; stream: cudaStream_t.
  * Enqueues classification, path resolution and graph assembly on `stream`; the
  * call itself waits only for the node counts (to size the result buffers).
+ * A field of at most 65,536 vertices (eg_compute and eg_compute_typed,
+ * without EG_FLAG_PATHS) does not wait at all: its result buffers are sized
+ * by bounds (maxima and saddles at most N, arc ends at most N times the most
+ * components an upper link can have), and a device-side error (EG_ERR_NAN,
+ * EG_ERR_TIMEOUT) is then returned by the first call that reads the result.
  * On success *out names the result.
  * Errors: EG_ERR_ARG, EG_ERR_NAN (field holds NaN), EG_ERR_OOM, EG_ERR_CUDA. */
 EG_API eg_status eg_compute(eg_handle h, const float *field, int d, const int64_t *extents,

@@ -143,6 +143,10 @@ struct HostPool {
     }
 };
 
+// Fields of at most this many vertices, computed alone, get result buffers
+// sized by bounds instead of waiting for their node counts.
+constexpr uint64_t kBoundedVertices = 1u << 16;
+
 // Per-field small device block: totals[4] (M, S, P, A) + status word.
 struct alignas(16) SmallBlock {
     unsigned long long totals[4];
@@ -165,6 +169,7 @@ struct Result {
     void *path_ptr = nullptr, *path_vtx = nullptr, *pbrick = nullptr;  // arc geometry (EG_FLAG_PATHS)
     uint64_t M = 0, S = 0, P = 0, A = 0, V = 0;
     bool have_A = false;
+    bool bounded = false;   // buffers sized by bounds; counts read when the result is collected
     uint32_t err = 0;
     cudaEvent_t done = nullptr;  // the launch's completion event (owned by the launch)
     std::shared_ptr<struct Launch> launch;  // keeps the descriptor table alive
@@ -179,6 +184,7 @@ struct Launch {
     void *smalls = nullptr;           // SmallBlock[nsmall] on the device
     int nsmall = 0;
     std::vector<SmallBlock> hsmall;   // host copy once the launch finished
+    void *hsmall_pin = nullptr;       // page-locked copy, written by the launch's last step
     cudaEvent_t done = nullptr;       // recorded after the launch's last step
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // step timing (optional)
     ~Launch()
@@ -393,7 +399,8 @@ void release_launch(eg_ctx *h, Launch *L)
     h->pool.release(L->desc_dev);
     h->hpool.release(L->desc_host);
     h->pool.release(L->smalls);
-    L->desc_dev = L->desc_host = L->smalls = nullptr;
+    h->hpool.release(L->hsmall_pin);
+    L->desc_dev = L->desc_host = L->smalls = L->hsmall_pin = nullptr;
 }
 
 struct Job {
@@ -629,7 +636,7 @@ eg_status enqueue_paths(eg_ctx *h, const Plan &P, Launch *L, FieldDev *Dh,
 }
 
 eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std::vector<uint64_t> &ids,
-                   const eg_config &cfg, bool use_graph = false)
+                   const eg_config &cfg, bool use_graph = false, bool single_call = false)
 {
     const int nf = int(jobs.size());
     std::vector<Layout> lay(nf);
@@ -639,6 +646,10 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
     bool any_paths = false;
     for (int i = 0; i < nf; i++) any_paths = any_paths || (jobs[i].flags & kFlagPaths);
     if (any_paths) use_graph = false;
+    // a small field alone: result buffers sized by bounds, so the call never
+    // waits for the node counts (they arrive with the launch's last copy)
+    // (single-field calls only: batches and served streams keep exact buffers)
+    const bool bounded = single_call && nf == 1 && !any_paths && !use_graph && jobs[0].sh.N <= kBoundedVertices;
     // group fields by classifier kind so every launch covers a contiguous slice
     auto cdt = [&](int i) { return dtype_narrow(jobs[i].dtype) ? uint32_t(kF32) : jobs[i].dtype; };
     auto key = [&](int i) {
@@ -682,6 +693,7 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
     if (!use_graph && (e = h->pool.alloc(&L->desc_dev, L->bytes)) != cudaSuccess) return fail(from_cuda(e));
     if ((e = h->hpool.alloc(&L->desc_host, L->bytes)) != cudaSuccess) return fail(from_cuda(e));
     if ((e = h->pool.alloc(&L->smalls, sizeof(SmallBlock) * size_t(nf))) != cudaSuccess) return fail(from_cuda(e));
+    if ((e = h->hpool.alloc(&L->hsmall_pin, sizeof(SmallBlock) * size_t(nf))) != cudaSuccess) return fail(from_cuda(e));
     L->nsmall = nf;
     FieldDev *Dh = reinterpret_cast<FieldDev *>(L->desc_host);
     std::memset(Dh, 0, L->bytes);
@@ -751,7 +763,7 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
         F.rtile0 = P.total_rtiles;
         if (ly.kd == 3) {
             uint64_t nt = 0;
-            resolve_tile_shape(F.n[0], F.n[1], F.n[2], F.rt, &nt);
+            resolve_tile_shape(F.n[0], F.n[1], F.n[2], nf == 1, F.rt, &nt);
             P.total_rtiles += nt;
         }
         G.count++;
@@ -841,21 +853,34 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
         }
         if (h->timing) cudaEventRecord(L->ev[2], st);
     }
+    if (bounded) {
+        // M + S <= N (a vertex gives at most one record), P <= S times the
+        // most components of an upper link
+        Result &r = *res[0];
+        const int d = jobs[0].sh.d;
+        const uint64_t N = jobs[0].sh.N;
+        r.M = N;
+        r.S = N;
+        r.P = N * uint64_t(d == 1 ? 2 : (d == 2 ? 3 : (d == 5 ? 20 : 10)));
+        r.bounded = true;
+    }
     void *hcounts = nullptr;
-    if ((e = h->hpool.alloc(&hcounts, sizeof(SmallBlock) * size_t(nf))) != cudaSuccess) {
+    if (!bounded && (e = h->hpool.alloc(&hcounts, sizeof(SmallBlock) * size_t(nf))) != cudaSuccess) {
         cudaEventDestroy(k1);
         return fail(from_cuda(e));
     }
-    cudaStreamWaitEvent(h->side, k1, 0);
-    cudaMemcpyAsync(hcounts, L->smalls, sizeof(SmallBlock) * size_t(nf), cudaMemcpyDeviceToHost, h->side);
-    e = cudaStreamSynchronize(h->side);
+    if (!bounded) {
+        cudaStreamWaitEvent(h->side, k1, 0);
+        cudaMemcpyAsync(hcounts, L->smalls, sizeof(SmallBlock) * size_t(nf), cudaMemcpyDeviceToHost, h->side);
+        e = cudaStreamSynchronize(h->side);
+    }
     cudaEventDestroy(k1);
     if (e != cudaSuccess) {
         h->hpool.release(hcounts);
         return fail(from_cuda(e));
     }
     eg_status first_err = EG_OK;
-    for (int i = 0; i < nf; i++) {
+    for (int i = 0; i < nf && !bounded; i++) {
         const SmallBlock &sb = static_cast<SmallBlock *>(hcounts)[i];
         Result &r = *res[i];
         r.M = sb.totals[0];
@@ -912,6 +937,10 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
     if ((es = run_part(2)) != EG_OK) return fail(es);
     if (h->timing) cudaEventRecord(L->ev[4], st);
     cudaEventRecord(h->ws_free, st);
+    // every result's counts and status word, read by collect() once `done` fired
+    if ((e = cudaMemcpyAsync(L->hsmall_pin, L->smalls, sizeof(SmallBlock) * size_t(nf), cudaMemcpyDeviceToHost,
+                             st)) != cudaSuccess)
+        return fail(from_cuda(e));
     ids.resize(nf);
     if ((e = cudaEventCreateWithFlags(&L->done, cudaEventDisableTiming)) != cudaSuccess) return fail(from_cuda(e));
     cudaEventRecord(L->done, st);
@@ -934,13 +963,14 @@ eg_status collect(eg_ctx *h, Result &r)
         Launch &L = *r.launch;
         if (L.hsmall.empty()) {
             L.hsmall.resize(size_t(L.nsmall));
-            e = cudaMemcpy(L.hsmall.data(), L.smalls, sizeof(SmallBlock) * size_t(L.nsmall), cudaMemcpyDeviceToHost);
-            if (e != cudaSuccess) {
-                L.hsmall.clear();
-                return from_cuda(e);
-            }
+            std::memcpy(L.hsmall.data(), L.hsmall_pin, sizeof(SmallBlock) * size_t(L.nsmall));
         }
         const SmallBlock &sb = L.hsmall[size_t(r.slot)];
+        if (r.bounded) {
+            r.M = sb.totals[0];
+            r.S = sb.totals[1];
+            r.P = sb.totals[2];
+        }
         r.A = sb.totals[3];
         r.err |= sb.err;
         r.have_A = true;
@@ -1080,7 +1110,7 @@ eg_status eg_compute(eg_handle h, const float *field, int d, const int64_t *exte
     cudaSetDevice(h->device);
     std::vector<Job> jobs{{field, sh, h->cfg.flags & (kFlagMinimum | kFlagNoLabels | kFlagPaths)}};
     std::vector<uint64_t> ids;
-    eg_status s = run_jobs(h, jobs, static_cast<cudaStream_t>(stream), ids, h->cfg);
+    eg_status s = run_jobs(h, jobs, static_cast<cudaStream_t>(stream), ids, h->cfg, false, true);
     if (s == EG_OK) *out = ids[0];
     return s;
 }
@@ -1101,7 +1131,7 @@ eg_status eg_compute_typed(eg_handle h, const void *field, int dtype, int d, con
     cudaSetDevice(h->device);
     std::vector<Job> jobs{{field, sh, h->cfg.flags & (kFlagMinimum | kFlagNoLabels | kFlagPaths), uint32_t(dtype)}};
     std::vector<uint64_t> ids;
-    eg_status s = run_jobs(h, jobs, static_cast<cudaStream_t>(stream), ids, h->cfg);
+    eg_status s = run_jobs(h, jobs, static_cast<cudaStream_t>(stream), ids, h->cfg, false, true);
     if (s == EG_OK) *out = ids[0];
     return s;
 }
@@ -1152,6 +1182,8 @@ eg_status eg_compute_host(eg_handle h, const float *field, int d, const int64_t 
     if (e != cudaSuccess) return from_cuda(e);
     std::vector<Job> jobs{{static_cast<const float *>(h->stage), sh, h->cfg.flags & (kFlagMinimum | kFlagNoLabels | kFlagPaths)}};
     std::vector<uint64_t> ids;
+    // (not bounded: the staging buffer is reused by the next call, so the
+    // call returns only after classification has read it)
     eg_status s = run_jobs(h, jobs, st, ids, h->cfg);
     if (s == EG_OK) *out = ids[0];
     return s;
@@ -1419,7 +1451,7 @@ eg_status eg_get_cancelled(eg_handle h, eg_result_id id, float tau, uint8_t *ali
     if (s != EG_OK) return s;
     if (r.dtype != kF32 || (r.S && !alive) || (r.M && !survivor)) return EG_ERR_ARG;
     cudaStream_t st = h->side;
-    constexpr int kBufs = 14;
+    constexpr int kBufs = 17;
     void *buf[kBufs] = {};
     auto done = [&](eg_status x) {
         cudaStreamSynchronize(st);
@@ -1428,7 +1460,7 @@ eg_status eg_get_cancelled(eg_handle h, eg_result_id id, float tau, uint8_t *ali
     };
     const uint64_t M = r.M, S = r.S, A = r.A;
     const size_t sizes[kBufs] = {4 * A, 4 * A, 4 * M, 8 * M, 8 * M, 8 * S, 8 * S, 4 * S, S,
-                                 4 * S, 4 * S, 128, S, 4 * M};
+                                 4 * S, 4 * S, 128, S, 4 * M, 4 * A, 8 * M, 8 * M};
     cudaError_t e;
     for (int i = 0; i < kBufs; i++)
         if ((e = h->pool.alloc(&buf[i], std::max<size_t>(sizes[i], 16))) != cudaSuccess) return done(from_cuda(e));
@@ -1438,10 +1470,13 @@ eg_status eg_get_cancelled(eg_handle h, eg_result_id id, float tau, uint8_t *ali
     C.sad_val = static_cast<const float *>(r.sad_val);
     C.row_ptr = static_cast<const uint64_t *>(r.row_ptr);
     C.end = static_cast<uint32_t *>(buf[0]);
-    C.aroot = static_cast<uint32_t *>(buf[1]);
+    C.aroot[0] = static_cast<uint32_t *>(buf[1]);
+    C.aroot[1] = static_cast<uint32_t *>(buf[14]);
     C.parent = static_cast<uint32_t *>(buf[2]);
-    C.minlb = static_cast<unsigned long long *>(buf[3]);
-    C.min2 = static_cast<unsigned long long *>(buf[4]);
+    C.minlb[0] = static_cast<unsigned long long *>(buf[3]);
+    C.minlb[1] = static_cast<unsigned long long *>(buf[15]);
+    C.min2[0] = static_cast<unsigned long long *>(buf[4]);
+    C.min2[1] = static_cast<unsigned long long *>(buf[16]);
     C.costkey = static_cast<unsigned long long *>(buf[5]);
     C.lbkey = static_cast<unsigned long long *>(buf[6]);
     C.high = static_cast<uint32_t *>(buf[7]);

@@ -37,16 +37,21 @@
 // cancelled as soon as it is the cheapest), which is what the serial queue
 // does whenever costs never fall.
 //
-// One round, over the list of waiting saddles: evaluate (current maxima by
+// One round, over the list of saddles still waiting: (1) clear the
+// per-maximum minima of the round before, evaluate (current maxima by
 // following the merges, cost and lb keys, the per-maximum minimum of lb keys,
-// the global cheapest), second minima per maximum, decide (cancel, and point
-// each dying maximum at its survivor), reset the per-maximum minima and keep
-// the still-waiting saddles for the next round.  All rounds run in one
-// cooperative launch with grid barriers between the phases (late rounds often
-// cancel one or two saddles between a few large maxima, so their number can
-// be large; a launch per round would cost far more).  Keys are (float32 bits of a non-negative cost)
-// << 32 | saddle index, so one 64-bit atomicMin orders by cost, then by
-// vertex id (saddles are in id order).
+// the global cheapest) and keep the saddles that still wait in the next
+// list; (2) second minima per maximum; (3) decide (cancel, and point each
+// dying maximum at its survivor).  The per-maximum minima and the arcs'
+// snapshots of their current maxima are kept twice, by the parity of the
+// round: round r writes set r % 2 and clears set (r + 1) % 2, which round r - 1
+// wrote, through that round's snapshots, so no reset pass is needed and a
+// round takes three grid barriers.  All rounds run in one cooperative launch
+// (late rounds often cancel one or two saddles between a few large maxima,
+// so their number can be large; a launch per round would cost far more), one
+// CTA of 1024 threads per SM, so that few CTAs meet at each barrier.  Keys are
+// (float32 bits of a non-negative cost) << 32 | saddle index, so one 64-bit
+// atomicMin orders by cost, then by vertex id (saddles are in id order).
 #include <algorithm>
 
 #include "eg_internal.cuh"
@@ -54,7 +59,8 @@
 
 namespace eg {
 
-constexpr int kCancelThreads = 256;
+constexpr int kCancelThreads = 1024;
+constexpr int kSetupThreads = 256;
 constexpr int kMaxAdj = 20;  // most distinct maxima one saddle reaches (beta0+ bound, 5D)
 constexpr unsigned long long kNoKey = ~0ull;
 
@@ -97,12 +103,12 @@ __device__ __forceinline__ uint32_t c_find(const CancelDev &C, uint32_t m)
     return r;
 }
 
-// Distinct current maxima of saddle s from the per-arc snapshot.
-__device__ __forceinline__ int c_adjacent(const CancelDev &C, uint32_t s, uint32_t (&u)[kMaxAdj])
+// Distinct current maxima of saddle s from the snapshot of set b.
+__device__ __forceinline__ int c_adjacent(const CancelDev &C, int b, uint32_t s, uint32_t (&u)[kMaxAdj])
 {
     int n = 0;
     for (uint64_t a = C.row_ptr[s]; a < C.row_ptr[s + 1]; a++) {
-        const uint32_t r = C.aroot[a];
+        const uint32_t r = C.aroot[b][a];
         bool dup = false;
         for (int k = 0; k < n; k++) dup |= u[k] == r;
         if (!dup && n < kMaxAdj) u[n++] = r;
@@ -110,13 +116,14 @@ __device__ __forceinline__ int c_adjacent(const CancelDev &C, uint32_t s, uint32
     return n;
 }
 
-// Phase 1 for one waiting saddle: its current maxima, keys, the per-maximum
-// minimum lb key; returns its cost key if it may be cancelled (else kNoKey).
-__device__ __forceinline__ unsigned long long c_eval(const CancelDev &C, uint32_t s)
+// Phase 1 for one waiting saddle: its current maxima (snapshot b), keys, the
+// per-maximum minimum lb key; returns its cost key if it may be cancelled
+// (else kNoKey).
+__device__ __forceinline__ unsigned long long c_eval(const CancelDev &C, int b, uint32_t s)
 {
-    for (uint64_t a = C.row_ptr[s]; a < C.row_ptr[s + 1]; a++) C.aroot[a] = c_find(C, C.end[a]);
+    for (uint64_t a = C.row_ptr[s]; a < C.row_ptr[s + 1]; a++) C.aroot[b][a] = c_find(C, C.end[a]);
     uint32_t u[kMaxAdj];
-    const int n = c_adjacent(C, s, u);
+    const int n = c_adjacent(C, b, s, u);
     if (n < 2) {
         C.state[s] = 2;  // joins one maximum: never cancelled
         return kNoKey;
@@ -141,30 +148,39 @@ __device__ __forceinline__ unsigned long long c_eval(const CancelDev &C, uint32_
     C.costkey[s] = ck;
     C.lbkey[s] = lk;
     C.high[s] = h1;
-    for (int k = 0; k < n; k++) atomicMin(C.minlb + u[k], lk);
+    for (int k = 0; k < n; k++) atomicMin(C.minlb[b] + u[k], lk);
     return cost <= C.tau ? ck : kNoKey;
 }
 
-// Phase 2: per maximum, the smallest lb key other than the minimum's holder.
-__device__ __forceinline__ void c_second(const CancelDev &C, uint32_t s)
+// Clear the per-maximum minima of set b that saddle s wrote (through the
+// snapshot of set b).
+__device__ __forceinline__ void c_clear(const CancelDev &C, int b, uint32_t s)
 {
-    if (C.state[s] != 0) return;
+    for (uint64_t a = C.row_ptr[s]; a < C.row_ptr[s + 1]; a++) {
+        const uint32_t r = C.aroot[b][a];
+        C.minlb[b][r] = kNoKey;
+        C.min2[b][r] = kNoKey;
+    }
+}
+
+// Phase 2: per maximum, the smallest lb key other than the minimum's holder.
+__device__ __forceinline__ void c_second(const CancelDev &C, int b, uint32_t s)
+{
     uint32_t u[kMaxAdj];
-    const int n = c_adjacent(C, s, u);
+    const int n = c_adjacent(C, b, s, u);
     const unsigned long long lk = C.lbkey[s];
     for (int k = 0; k < n; k++)
-        if (C.minlb[u[k]] != lk) atomicMin(C.min2 + u[k], lk);
+        if (C.minlb[b][u[k]] != lk) atomicMin(C.min2[b] + u[k], lk);
 }
 
 // Phase 3: cancel the saddle if it is safe or the global cheapest; its dying
 // maxima get their survivor as parent.  Returns 1 when it is cancelled.
-__device__ __forceinline__ int c_decide(const CancelDev &C, uint32_t s, unsigned long long gmin)
+__device__ __forceinline__ int c_decide(const CancelDev &C, int b, uint32_t s, unsigned long long gmin)
 {
-    if (C.state[s] != 0) return 0;
     const unsigned long long ck = C.costkey[s];
     if (__uint_as_float(uint32_t(ck >> 32)) > C.tau) return 0;
     uint32_t u[kMaxAdj];
-    const int n = c_adjacent(C, s, u);
+    const int n = c_adjacent(C, b, s, u);
     const uint32_t h1 = C.high[s];
     bool safe = ck == gmin;
     if (!safe) {
@@ -172,8 +188,8 @@ __device__ __forceinline__ int c_decide(const CancelDev &C, uint32_t s, unsigned
         safe = true;
         for (int k = 0; k < n; k++) {
             if (u[k] == h1) continue;  // the survivor: see above
-            const unsigned long long m1 = C.minlb[u[k]];
-            const unsigned long long other = m1 == lk ? C.min2[u[k]] : m1;
+            const unsigned long long m1 = C.minlb[b][u[k]];
+            const unsigned long long other = m1 == lk ? C.min2[b][u[k]] : m1;
             safe &= other > ck;
         }
     }
@@ -183,18 +199,6 @@ __device__ __forceinline__ int c_decide(const CancelDev &C, uint32_t s, unsigned
     for (int k = 0; k < n; k++)
         if (u[k] != h1) C.parent[u[k]] = h1;
     return 1;
-}
-
-// Phase 4: clear the per-maximum minima this saddle set (from its snapshot:
-// the maxima of this round), and keep it for the next round if it waits.
-__device__ __forceinline__ bool c_reset(const CancelDev &C, uint32_t s)
-{
-    for (uint64_t a = C.row_ptr[s]; a < C.row_ptr[s + 1]; a++) {
-        const uint32_t r = C.aroot[a];
-        C.minlb[r] = kNoKey;
-        C.min2[r] = kNoKey;
-    }
-    return C.state[s] == 0;
 }
 
 // Arc ends as indices into the (sorted) maxima list.
@@ -221,8 +225,10 @@ __global__ void k_cancel_init(CancelDev C)
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < C.M) {
         C.parent[i] = i;
-        C.minlb[i] = kNoKey;
-        C.min2[i] = kNoKey;
+        for (int b = 0; b < 2; b++) {
+            C.minlb[b][i] = kNoKey;
+            C.min2[b][i] = kNoKey;
+        }
     }
     if (i < C.S) {
         C.state[i] = 0;
@@ -267,13 +273,22 @@ __device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned *gen, uin
     return s_ok != 0;
 }
 
-// All rounds in one cooperative launch: the CTAs share the waiting list with
-// grid-stride loops, separated by grid barriers (four per round).  The
+__device__ __forceinline__ unsigned long long c_read(const unsigned long long *p)
+{
+    return *reinterpret_cast<const volatile unsigned long long *>(p);
+}
+
+// All rounds in one cooperative launch: the CTAs share the lists with
+// grid-stride loops, separated by grid barriers (three per round).  The
 // control words of round r live in slot r % 3 ({cheapest key, cancellations,
-// next list length}); slot (r + 1) % 3 is cleared during round r, which no
-// CTA can still be reading (it was last used two rounds before).  The loop
-// ends with the first round that cancels nothing, or when a barrier gives
-// up.  ctrl[9] receives the number of rounds.
+// length of the list the round keeps}); slot (r + 1) % 3 is cleared during
+// round r, which no CTA can still be reading (it was last used two rounds
+// before).  Round r walks the list kept by round r - 1 (every saddle of it
+// clears what it wrote then, and the ones cancelled since drop out), keeps
+// the saddles that still wait after its evaluation, and runs phases 2 and 3
+// over those.  The loop ends with the first round that cancels nothing (or
+// keeps no saddle), or when a barrier gives up.  ctrl[9] receives the number
+// of rounds.
 __global__ void __launch_bounds__(kCancelThreads) k_cancel_rounds(CancelDev C)
 {
     unsigned *bar = reinterpret_cast<unsigned *>(C.ctrl + 10);  // [0] count, [1] generation
@@ -283,50 +298,53 @@ __global__ void __launch_bounds__(kCancelThreads) k_cancel_rounds(CancelDev C)
     int p = 0;
     unsigned long long n = C.S;
     uint32_t round = 0;
-    while (n > 0 && round <= C.S) {
+    while (round <= C.S) {
         unsigned long long *slot = C.ctrl + 3 * (round % 3);
+        const int b = int(round & 1);
         if (tid == 0) {
             unsigned long long *nx = C.ctrl + 3 * ((round + 1) % 3);
             nx[0] = kNoKey;
             nx[1] = 0;
             nx[2] = 0;
         }
-        // 1: evaluate
-        for (uint64_t i = tid; i < n; i += stride) {
-            const unsigned long long k = c_eval(C, C.list[p][i]);
-            if (k != kNoKey) atomicMin(slot, k);
-        }
-        if (!grid_barrier(bar, bar + 1, C.err)) break;
-        // 2: second minima
-        for (uint64_t i = tid; i < n; i += stride) c_second(C, C.list[p][i]);
-        if (!grid_barrier(bar, bar + 1, C.err)) break;
-        // 3: decide
-        const unsigned long long gmin = *reinterpret_cast<volatile unsigned long long *>(slot);
-        for (uint64_t i = tid; i < n; i += stride)
-            if (c_decide(C, C.list[p][i], gmin)) atomicAdd(slot + 1, 1ull);
-        if (!grid_barrier(bar, bar + 1, C.err)) break;
-        // 4: reset the per-maximum minima, keep the waiting saddles
-        const unsigned long long cancelled = *reinterpret_cast<volatile unsigned long long *>(slot + 1);
+        // 1: clear the previous round's minima, evaluate, keep the waiting
         for (uint64_t base = tid - lane; base < n; base += stride) {
             const uint64_t i = base + lane;
             bool keep = false;
             uint32_t s = 0;
             if (i < n) {
                 s = C.list[p][i];
-                keep = c_reset(C, s);
+                if (round > 0) c_clear(C, b ^ 1, s);
+                if (C.state[s] == 0) {
+                    const unsigned long long k = c_eval(C, b, s);
+                    if (k != kNoKey) atomicMin(slot, k);
+                    keep = C.state[s] == 0;
+                }
             }
             const unsigned m = __ballot_sync(0xffffffffu, keep);
             if (!m) continue;
-            unsigned long long b = 0;
-            if (lane == __ffs(m) - 1) b = atomicAdd(slot + 2, (unsigned long long)__popc(m));
-            b = __shfl_sync(0xffffffffu, b, __ffs(m) - 1);
-            if (keep) C.list[p ^ 1][b + __popc(m & ((1u << lane) - 1u))] = s;
+            unsigned long long o = 0;
+            if (lane == __ffs(m) - 1) o = atomicAdd(slot + 2, (unsigned long long)__popc(m));
+            o = __shfl_sync(0xffffffffu, o, __ffs(m) - 1);
+            if (keep) C.list[p ^ 1][o + __popc(m & ((1u << lane) - 1u))] = s;
         }
         if (!grid_barrier(bar, bar + 1, C.err)) break;
-        round++;
-        n = *reinterpret_cast<volatile unsigned long long *>(slot + 2);
+        n = c_read(slot + 2);
         p ^= 1;
-        if (cancelled == 0) break;
+        if (n == 0) {
+            round++;
+            break;
+        }
+        // 2: second minima
+        for (uint64_t i = tid; i < n; i += stride) c_second(C, b, C.list[p][i]);
+        if (!grid_barrier(bar, bar + 1, C.err)) break;
+        // 3: decide
+        const unsigned long long gmin = c_read(slot);
+        for (uint64_t i = tid; i < n; i += stride)
+            if (c_decide(C, b, C.list[p][i], gmin)) atomicAdd(slot + 1, 1ull);
+        if (!grid_barrier(bar, bar + 1, C.err)) break;
+        round++;
+        if (c_read(slot + 1) == 0) break;
     }
     if (tid == 0) C.ctrl[9] = round;
 }
@@ -339,13 +357,13 @@ __global__ void k_cancel_out(CancelDev C, uint8_t *alive, uint32_t *survivor)
     if (i < C.M) survivor[i] = C.maxima[c_find(C, i)];
 }
 
-static inline dim3 grid_of(uint64_t n) { return dim3(unsigned((n + kCancelThreads - 1) / kCancelThreads)); }
+static inline dim3 grid_of(uint64_t n) { return dim3(unsigned((n + kSetupThreads - 1) / kSetupThreads)); }
 
 cudaError_t launch_cancel_setup(const CancelDev &C, const uint32_t *col, uint64_t A, cudaStream_t st)
 {
     const uint64_t n = C.M > C.S ? C.M : C.S;
-    if (n) k_cancel_init<<<grid_of(n), kCancelThreads, 0, st>>>(C);
-    if (A) k_cancel_ends<<<grid_of(A), kCancelThreads, 0, st>>>(C, col, A);
+    if (n) k_cancel_init<<<grid_of(n), kSetupThreads, 0, st>>>(C);
+    if (A) k_cancel_ends<<<grid_of(A), kSetupThreads, 0, st>>>(C, col, A);
     return cudaGetLastError();
 }
 
@@ -356,7 +374,7 @@ cudaError_t launch_cancel_rounds(const CancelDev &C, int sm_count, cudaStream_t 
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cancel_rounds, kCancelThreads, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
-    uint64_t grid = uint64_t(std::max(sm_count, 1)) * uint64_t(std::min(per_sm, 4));
+    uint64_t grid = uint64_t(std::max(sm_count, 1));
     const uint64_t need = (uint64_t(C.S) + kCancelThreads - 1) / kCancelThreads;
     if (grid > need) grid = need;
     CancelDev arg = C;
@@ -368,7 +386,7 @@ cudaError_t launch_cancel_rounds(const CancelDev &C, int sm_count, cudaStream_t 
 cudaError_t launch_cancel_out(const CancelDev &C, uint8_t *alive, uint32_t *survivor, cudaStream_t st)
 {
     const uint64_t n = C.M > C.S ? C.M : C.S;
-    if (n) k_cancel_out<<<grid_of(n), kCancelThreads, 0, st>>>(C, alive, survivor);
+    if (n) k_cancel_out<<<grid_of(n), kSetupThreads, 0, st>>>(C, alive, survivor);
     return cudaGetLastError();
 }
 

@@ -64,8 +64,8 @@ cudaError_t launch_resolve(const FieldDev *fields, int nf, uint64_t total_bricks
 // before launch_resolve: tiles numbered by FieldDev::rtile0 over all fields.
 cudaError_t launch_resolve_tiles(const FieldDev *fields, int nf, uint64_t tiles, cudaStream_t st);
 // Resolution tile extents (log2) of a field of extents n0 x n1 x n2, and the
-// number of its tiles.
-void resolve_tile_shape(uint32_t n0, uint32_t n1, uint32_t n2, uint32_t rt[3], uint64_t *tiles);
+// number of its tiles (alone: the field is the launch's only one).
+void resolve_tile_shape(uint32_t n0, uint32_t n1, uint32_t n2, bool alone, uint32_t rt[3], uint64_t *tiles);
 
 // Steps (d)+(e): nodes and arc ends per brick (one kernel dimension), then CSR.
 cudaError_t launch_nodes_d(int kd, const FieldDev *fields, int nf, uint64_t base, uint64_t bricks, cudaStream_t st);
@@ -102,17 +102,17 @@ struct CancelDev {
     const float *sad_val;        // [S]
     const uint64_t *row_ptr;     // [S+1] arcs of every saddle
     uint32_t *end;               // [A] arc end as an index into maxima
-    uint32_t *aroot;             // [A] survivor of every arc end (this round)
+    uint32_t *aroot[2];          // [A] each: survivor of every arc end, snapshot of the rounds of one parity
     uint32_t *parent;            // [M] merge target of a merged maximum, else itself
-    unsigned long long *minlb;   // [M] smallest lb key of the saddles reaching it
-    unsigned long long *min2;    // [M] smallest lb key but the smallest one's holder
+    unsigned long long *minlb[2]; // [M] each: smallest lb key of the saddles reaching it (by round parity)
+    unsigned long long *min2[2];  // [M] each: smallest lb key but the smallest one's holder
     unsigned long long *costkey; // [S]
     unsigned long long *lbkey;   // [S]
     uint32_t *high;              // [S] highest current maximum of the saddle
     uint8_t *state;              // [S] 0 waiting, 1 cancelled, 2 never cancelled
-    uint32_t *list[2];           // [S] each: waiting saddles of this / the next round
+    uint32_t *list[2];           // [S] each: saddles walked by this / the next round
     unsigned long long *ctrl;    // [3 r .. 3 r + 2] round slot r (cheapest key, cancellations,
-                                 // next list length), [9] rounds, [10] grid barrier
+                                 // length of the list kept), [9] rounds, [10] grid barrier
     uint32_t *err;               // status word
     uint32_t M, S;
     float tau;

@@ -127,9 +127,19 @@ constexpr uint16_t kDone = 0x8000u, kOut = 0x4000u, kIdx = 0x3fffu;
 constexpr int kTb = 8;  // elements per thread per pass (loads in flight)
 constexpr uint32_t kTileSmallField = 1u << 20;  // fields up to this size always take the tiled pass
 
-void resolve_tile_shape(uint32_t n0, uint32_t n1, uint32_t n2, uint32_t rt[3], uint64_t *tiles)
+void resolve_tile_shape(uint32_t n0, uint32_t n1, uint32_t n2, bool alone, uint32_t rt[3], uint64_t *tiles)
 {
-    if (n2 > 1) {
+    if (alone && uint64_t(n0) * n1 * n2 <= kTileSmallField) {
+        // a small field launched on its own: 1024-vertex tiles, so that its
+        // tiles spread over the GPU (in a batch the other fields fill it)
+        if (n2 > 1) {
+            rt[0] = 4; rt[1] = 3; rt[2] = 3;  // 16 x 8 x 8
+        } else if (n1 > 1) {
+            rt[0] = 5; rt[1] = 5; rt[2] = 0;  // 32 x 32
+        } else {
+            rt[0] = 10; rt[1] = 0; rt[2] = 0;  // 1024
+        }
+    } else if (n2 > 1) {
         rt[0] = 5; rt[1] = 4; rt[2] = 4;  // 32 x 16 x 16
     } else if (n1 > 1) {
         rt[0] = 5; rt[1] = 8; rt[2] = 0;  // 32 x 256

@@ -181,6 +181,34 @@ def test_host_entry_point(handle):
     assert_same(g, oracle.compute(f.values))
 
 
+@pytest.mark.parametrize("shape", [(256, 256), (255, 257), (251, 263), (41, 40, 40), (41, 40, 39), (65536,),
+                                   (65537,), (16, 16, 16, 16)],
+                         ids=lambda s: "x".join(map(str, s)))
+def test_bounded_and_exact_result_buffers(handle, handle_min, shape):
+    """Fields of at most 65,536 vertices get result buffers sized by bounds
+    (no wait for the node counts), larger ones exact buffers: both sides of
+    the limit, both graphs, against the oracle."""
+    f = F.white_noise(shape, zlib.crc32(repr(shape).encode()) % 1000)
+    assert_same(run_gpu(handle, f.values), oracle.compute(f.values))
+    assert_same(run_gpu(handle_min, f.values), oracle.compute(f.values, minimum=True))
+
+
+def test_bounded_result_reports_nan_when_read(handle):
+    """A small field's NaN surfaces when the result is read; the handle
+    stays usable and the next result is exact."""
+    from paper_2303_02724_gb300 import eg
+    v = F.white_noise((40, 30), 5).values.copy()
+    v[7, 9] = np.nan
+    t = torch.from_numpy(v).cuda()
+    rid = handle.compute(t)
+    with pytest.raises(eg.EGError) as ei:
+        handle.get_graph(rid)
+    assert ei.value.status == eg.EG_ERR_NAN
+    handle.release(rid)
+    f = F.white_noise((40, 30), 6)
+    assert_same(run_gpu(handle, f.values), oracle.compute(f.values))
+
+
 def test_pinned_buffers_reused(handle):
     from paper_2303_02724_gb300 import eg
     buf = eg.GraphBuffers(4096, 8192, 16384, 24 * 24 * 24, pinned=True)
