@@ -95,6 +95,8 @@ typedef enum eg_dtype {
 #define EG_FLAG_NO_GRAPH      0x4u  /* eg_batch_submit: launch the steps directly
                                        instead of replaying captured CUDA graphs    */
 #define EG_FLAG_PATHS         0x8u  /* also keep the arc geometry (eg_get_paths)    */
+#define EG_FLAG_NO_FUSED      0x10u /* eg_compute(_typed): small fields take the
+                                       general launches, not the fused kernel       */
 
 /* Tuning knobs.  Zero in any field means "library default" (or the value a
  * previous eg_autotune chose for this handle).  The neighbourhood halo is one

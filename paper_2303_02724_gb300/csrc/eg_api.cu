@@ -27,6 +27,9 @@ static_assert(kF32 == EG_DTYPE_F32 && kF64 == EG_DTYPE_F64 && kI8 == EG_DTYPE_I8
                   kI16 == EG_DTYPE_I16 && kU16 == EG_DTYPE_U16 && kI32 == EG_DTYPE_I32 && kU32 == EG_DTYPE_U32 &&
                   kI64 == EG_DTYPE_I64 && kU64 == EG_DTYPE_U64 && kNumTypes == EG_DTYPE_COUNT,
               "internal element-type codes follow eg_dtype");
+static_assert(kFlagMinimum == EG_FLAG_MINIMUM_GRAPH && kFlagNoLabels == EG_FLAG_NO_LABELS && kFlagPaths == EG_FLAG_PATHS &&
+                  kFlagNoFused == EG_FLAG_NO_FUSED,
+              "flag bits of the ABI and the kernels differ");
 
 namespace {
 
@@ -151,7 +154,8 @@ constexpr uint64_t kBoundedVertices = 1u << 16;
 struct alignas(16) SmallBlock {
     unsigned long long totals[4];
     uint32_t err;
-    uint32_t pad[7];
+    uint32_t bar[2];   // grid-barrier words of the fused small-field kernel
+    uint32_t pad[5];
 };
 
 struct Result {
@@ -187,12 +191,8 @@ struct Launch {
     void *hsmall_pin = nullptr;       // page-locked copy, written by the launch's last step
     cudaEvent_t done = nullptr;       // recorded after the launch's last step
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // step timing (optional)
-    ~Launch()
-    {
-        for (auto &e : ev)
-            if (e) cudaEventDestroy(e);
-        if (done) cudaEventDestroy(done);
-    }
+    struct eg_ctx *owner = nullptr;   // the handle whose event pool the events return to
+    ~Launch();
 };
 
 }  // namespace
@@ -225,7 +225,35 @@ struct eg_ctx {
     cudaStream_t cap = nullptr;  // private stream for graph capture
     std::unique_ptr<struct eg_graph_cache> graphs;
     uint64_t ws_gen = 0;  // bumped whenever the workspace is reallocated
+    std::vector<cudaEvent_t> ev_pool[2];  // idle events: [0] without timing, [1] with
 };
+
+namespace {
+
+// Events are reused: creating them costs more host time than a small field's
+// whole computation.  An event returns to its handle's pool only when its
+// launch is gone, i.e. after every result of the launch was released (which
+// waits for the launch's last event), or after a failed call synchronised
+// its stream.
+cudaError_t get_event(eg_ctx *h, cudaEvent_t *e, bool timed)
+{
+    auto &pool = h->ev_pool[timed ? 1 : 0];
+    if (!pool.empty()) {
+        *e = pool.back();
+        pool.pop_back();
+        return cudaSuccess;
+    }
+    return timed ? cudaEventCreate(e) : cudaEventCreateWithFlags(e, cudaEventDisableTiming);
+}
+
+}  // namespace
+
+Launch::~Launch()
+{
+    for (auto &e : ev)
+        if (e) owner->ev_pool[1].push_back(e);
+    if (done) owner->ev_pool[0].push_back(done);
+}
 
 namespace {
 
@@ -650,6 +678,17 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
     // waits for the node counts (they arrive with the launch's last copy)
     // (single-field calls only: batches and served streams keep exact buffers)
     const bool bounded = single_call && nf == 1 && !any_paths && !use_graph && jobs[0].sh.N <= kBoundedVertices;
+    // ... and a 1D-3D float32 one takes every step in one cooperative launch
+    // over a flat layout of 256-vertex bricks (eg_small.cu)
+    const bool fused = bounded && !(cfg.flags & kFlagNoFused) && jobs[0].sh.d <= 3 && jobs[0].dtype == kF32 &&
+                       jobs[0].sh.N <= kSmallMaxVertices;
+    if (fused) {
+        Layout &ly = lay[0];
+        ly = Layout{};
+        ly.kd = 3;
+        ly.nbricks = small_bricks(jobs[0].sh.N);
+        ly.bcap = kSmallBrick;
+    }
     // group fields by classifier kind so every launch covers a contiguous slice
     auto cdt = [&](int i) { return dtype_narrow(jobs[i].dtype) ? uint32_t(kF32) : jobs[i].dtype; };
     auto key = [&](int i) {
@@ -678,6 +717,7 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
     if (es != EG_OK) return es;
 
     auto L = std::make_shared<Launch>();
+    L->owner = h;
     L->bytes = P.desc_bytes;
     cudaError_t e;
     std::vector<std::unique_ptr<Result>> res(nf);
@@ -699,10 +739,12 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
     std::memset(Dh, 0, L->bytes);
 
     uint64_t brick0 = 0, rec0 = 0, tile0 = 0;
-    char sig[128];
-    std::snprintf(sig, sizeof sig, "c%d/%d/%d/%d/%u|", cfg.classify_rows, cfg.classify_planes, P.walks, P.ctas,
-                  cfg.flags);
-    P.signature = sig;
+    if (use_graph) {  // (the key of the captured graphs)
+        char sig[128];
+        std::snprintf(sig, sizeof sig, "c%d/%d/%d/%d/%u|", cfg.classify_rows, cfg.classify_planes, P.walks, P.ctas,
+                      cfg.flags);
+        P.signature = sig;
+    }
     for (int oi = 0; oi < nf; oi++) {
         const int i = order[oi];
         const Job &j = jobs[i];
@@ -773,10 +815,12 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
         brick0 += ly.nbricks;
         rec0 += uint64_t(ly.nbricks) * ly.bcap;
         tile0 += scan_tiles(ly.nbricks);
-        char fs[192];
-        std::snprintf(fs, sizeof fs, "%d,%d,%u,%u,%u,%u,%u,%u,%u,%u,%u,%u,%u,%u;", key(i), ly.kd, F.N, ly.ty, ly.nyb,
-                      ly.nbricks, ly.zc, ly.nzc, F.vec, F.n[0], F.n[1], F.n[2], F.n[3], j.dtype);
-        P.signature += fs;
+        if (use_graph) {  // (the key of the captured graphs)
+            char fs[192];
+            std::snprintf(fs, sizeof fs, "%d,%d,%u,%u,%u,%u,%u,%u,%u,%u,%u,%u,%u,%u;", key(i), ly.kd, F.N, ly.ty,
+                          ly.nyb, ly.nbricks, ly.zc, ly.nzc, F.vec, F.n[0], F.n[1], F.n[2], F.n[3], j.dtype);
+            P.signature += fs;
+        }
     }
 
     // graphs for this layout (captured on first use; the workspace generation
@@ -835,20 +879,23 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
     if ((e = cudaStreamWaitEvent(st, h->ws_free, 0)) != cudaSuccess) return fail(from_cuda(e));
     if (h->timing) {
         for (auto &ev : L->ev)
-            if ((e = cudaEventCreate(&ev)) != cudaSuccess) return fail(from_cuda(e));
+            if ((e = get_event(h, &ev, true)) != cudaSuccess) return fail(from_cuda(e));
         cudaEventRecord(L->ev[0], st);
     }
-    // steps (a)+(c) and the node counts
-    if ((es = run_part(0)) != EG_OK) return fail(es);
-    if (h->timing) cudaEventRecord(L->ev[1], st);
-    cudaEvent_t k1;
-    if ((e = cudaEventCreateWithFlags(&k1, cudaEventDisableTiming)) != cudaSuccess) return fail(from_cuda(e));
-    cudaEventRecord(k1, st);
+    // steps (a)+(c) and the node counts (the fused path runs every step
+    // further down, once its result buffers exist)
+    if (!fused && (es = run_part(0)) != EG_OK) return fail(es);
+    if (h->timing && !fused) cudaEventRecord(L->ev[1], st);
+    cudaEvent_t k1 = nullptr;
+    if (!bounded) {
+        if ((e = cudaEventCreateWithFlags(&k1, cudaEventDisableTiming)) != cudaSuccess) return fail(from_cuda(e));
+        cudaEventRecord(k1, st);
+    }
     // step (b) runs while the host reads the counts back (after the geometry
     // when that is wanted)
-    if (!any_paths) {
+    if (!any_paths && !fused) {
         if ((es = run_part(1)) != EG_OK) {
-            cudaEventDestroy(k1);
+            if (k1) cudaEventDestroy(k1);
             return fail(es);
         }
         if (h->timing) cudaEventRecord(L->ev[2], st);
@@ -866,7 +913,7 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
     }
     void *hcounts = nullptr;
     if (!bounded && (e = h->hpool.alloc(&hcounts, sizeof(SmallBlock) * size_t(nf))) != cudaSuccess) {
-        cudaEventDestroy(k1);
+        if (k1) cudaEventDestroy(k1);
         return fail(from_cuda(e));
     }
     if (!bounded) {
@@ -874,7 +921,7 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
         cudaMemcpyAsync(hcounts, L->smalls, sizeof(SmallBlock) * size_t(nf), cudaMemcpyDeviceToHost, h->side);
         e = cudaStreamSynchronize(h->side);
     }
-    cudaEventDestroy(k1);
+    if (k1) cudaEventDestroy(k1);
     if (e != cudaSuccess) {
         h->hpool.release(hcounts);
         return fail(from_cuda(e));
@@ -933,16 +980,27 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
     }
     // phase 0 has finished (we waited for it), so the host table may change;
     // phase 2 uploads it again, ordered after resolution on the stream
-    if (h->timing) cudaEventRecord(L->ev[3], st);
-    if ((es = run_part(2)) != EG_OK) return fail(es);
-    if (h->timing) cudaEventRecord(L->ev[4], st);
+    if (fused) {
+        // counts, status and barrier words zeroed, then every step;
+        // the step timing reports the whole kernel as classification
+        unsigned *bar = static_cast<SmallBlock *>(L->smalls)->bar;
+        if ((e = cudaMemsetAsync(L->smalls, 0, sizeof(SmallBlock), st)) != cudaSuccess) return fail(from_cuda(e));
+        if ((e = launch_small(Dh[0], bar, h->sm_count, st)) != cudaSuccess) return fail(from_cuda(e));
+        h->launches += 1;
+        if (h->timing)
+            for (int q = 1; q < 5; q++) cudaEventRecord(L->ev[q], st);
+    } else {
+        if (h->timing) cudaEventRecord(L->ev[3], st);
+        if ((es = run_part(2)) != EG_OK) return fail(es);
+        if (h->timing) cudaEventRecord(L->ev[4], st);
+    }
     cudaEventRecord(h->ws_free, st);
     // every result's counts and status word, read by collect() once `done` fired
     if ((e = cudaMemcpyAsync(L->hsmall_pin, L->smalls, sizeof(SmallBlock) * size_t(nf), cudaMemcpyDeviceToHost,
                              st)) != cudaSuccess)
         return fail(from_cuda(e));
     ids.resize(nf);
-    if ((e = cudaEventCreateWithFlags(&L->done, cudaEventDisableTiming)) != cudaSuccess) return fail(from_cuda(e));
+    if ((e = get_event(h, &L->done, false)) != cudaSuccess) return fail(from_cuda(e));
     cudaEventRecord(L->done, st);
     for (int i = 0; i < nf; i++) res[i]->done = L->done;
     for (int i = 0; i < nf; i++) {
@@ -1081,9 +1139,9 @@ eg_status eg_destroy(eg_handle h)
         std::lock_guard<std::mutex> g(h->mu);
         cudaSetDevice(h->device);
         cudaDeviceSynchronize();
-        for (auto &kv : h->results)
-            if (kv.second->done) cudaEventDestroy(kv.second->done);
-        h->results.clear();
+        h->results.clear();  // (their launches return their events to the pools)
+        for (auto &pool : h->ev_pool)
+            for (cudaEvent_t e : pool) cudaEventDestroy(e);
         if (h->graphs) {
             for (auto &kv : h->graphs->entries) destroy_graph(h, kv.second);
             h->graphs.reset();

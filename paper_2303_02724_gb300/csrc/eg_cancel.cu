@@ -236,43 +236,6 @@ __global__ void k_cancel_init(CancelDev C)
     }
 }
 
-// Grid-wide barrier of the cooperative kernel below (every CTA is resident:
-// cooperative launch).  The last CTA to arrive resets the count and advances
-// the generation; the others wait for the generation to change, for at most
-// about a second (kSpinLimit rounds of a growing sleep), after which they set
-// kErrTimeout and report failure instead of hanging.
-__device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned *gen, uint32_t *err)
-{
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        const unsigned g = *reinterpret_cast<volatile unsigned *>(gen);
-        __threadfence();
-        if (atomicAdd(count, 1u) == gridDim.x - 1) {
-            *reinterpret_cast<volatile unsigned *>(count) = 0u;
-            __threadfence();
-            atomicAdd(gen, 1u);
-        } else {
-            unsigned ns = 32;
-            uint32_t spins = 0;
-            while (*reinterpret_cast<volatile unsigned *>(gen) == g) {
-                if (++spins > kSpinLimit) {
-                    atomicOr(err, kErrTimeout);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(ns);
-                ns = ns < 256 ? ns * 2 : 256;
-            }
-        }
-        __threadfence();
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
 __device__ __forceinline__ unsigned long long c_read(const unsigned long long *p)
 {
     return *reinterpret_cast<const volatile unsigned long long *>(p);

@@ -132,7 +132,7 @@ __device__ __forceinline__ bool chk_ptr(const T *p, const T *base, uint64_t n, u
 }
 
 // flags carried per field
-enum : uint32_t { kFlagMinimum = 1u, kFlagNoLabels = 2u, kFlagPaths = 8u };
+enum : uint32_t { kFlagMinimum = 1u, kFlagNoLabels = 2u, kFlagPaths = 8u, kFlagNoFused = 16u };
 
 // element types of a field (the values of eg_dtype)
 enum : uint32_t {
@@ -424,6 +424,44 @@ __device__ __forceinline__ uint64_t ld_volatile_u64(const uint64_t *p)
 __device__ __forceinline__ void st_volatile_u64(uint64_t *p, uint64_t v)
 {
     *reinterpret_cast<volatile uint64_t *>(p) = v;
+}
+
+// Grid-wide barrier of a cooperative kernel (every CTA is resident:
+// cooperative launch); count and gen start at zero.  The last CTA to arrive
+// resets the count and advances the generation; the others wait for the
+// generation to change, for at most about a second (kSpinLimit rounds of a
+// growing sleep), after which they set kErrTimeout and report failure
+// instead of hanging.
+__device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned *gen, uint32_t *err)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned g = *reinterpret_cast<volatile unsigned *>(gen);
+        __threadfence();
+        if (atomicAdd(count, 1u) == gridDim.x - 1) {
+            *reinterpret_cast<volatile unsigned *>(count) = 0u;
+            __threadfence();
+            atomicAdd(gen, 1u);
+        } else {
+            unsigned ns = 32;
+            uint32_t spins = 0;
+            while (*reinterpret_cast<volatile unsigned *>(gen) == g) {
+                if (++spins > kSpinLimit) {
+                    atomicOr(err, kErrTimeout);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(ns);
+                ns = ns < 256 ? ns * 2 : 256;
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
 }
 
 // Called by one full warp.  st: status array indexed by global item id;

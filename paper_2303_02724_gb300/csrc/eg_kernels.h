@@ -118,6 +118,14 @@ struct CancelDev {
     float tau;
     int minimum;
 };
+// Fused path for one small 1D-3D float32 field: every step in one
+// cooperative launch over a flat layout of small_bricks(N) bricks of 256
+// vertices (bcap 256, at most 256 bricks); bar: two zeroed words.
+constexpr uint64_t kSmallMaxVertices = 1u << 16;
+constexpr uint32_t kSmallBrick = 256;
+uint32_t small_bricks(uint64_t n);
+cudaError_t launch_small(const FieldDev &F, unsigned *bar, int sm_count, cudaStream_t st);
+
 // Set-up (every saddle waits, in list[0], ctrl zeroed but slot 0's key, which
 // is all ones); all rounds in one cooperative launch; the results.
 cudaError_t launch_cancel_setup(const CancelDev &C, const uint32_t *col, uint64_t A, cudaStream_t st);

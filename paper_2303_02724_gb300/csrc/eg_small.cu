@@ -1,0 +1,152 @@
+// Fused path for one small field (1D-3D float32, at most kSmallMaxVertices
+// vertices): classification (Sec. 3.3), path resolution (Sec. 3.4) and graph
+// assembly (Sec. 2 arcs, CSR) in one cooperative launch.
+//
+// A field this small is too little work to fill the GPU in any one step, so
+// the separate launches of the general path (and the count read-back between
+// them) cost more than the steps themselves.  Here one launch runs them all,
+// separated by grid barriers:
+//   1. classification, one vertex per thread, a brick = one CTA's 256
+//      consecutive vertex ids (the flat layout's per-vertex classifier, so the
+//      records are those of the general path);
+//   2. brick offsets and the totals M, S, P (one CTA scans the <= 256 brick
+//      counts), while every thread resolves its vertex's label by following
+//      the gradient pointers (concurrent walks read either a pointer or a
+//      finished label on the same path, so the races are benign);
+//   3. nodes and arc ends, one warp per brick;
+//   4. arc offsets and the total A (one CTA);
+//   5. CSR, one warp per brick.
+// Every barrier wait is bounded (kErrTimeout after about a second).
+#include <atomic>
+
+#include "eg_emit.cuh"
+#include "eg_flat.cuh"
+#include "eg_internal.cuh"
+#include "eg_kernels.h"
+
+namespace eg {
+
+constexpr int kSmallThreads = int(kSmallBrick);  // one vertex per thread, a brick per CTA
+
+__global__ void __launch_bounds__(kSmallThreads) k_small(const FieldDev F, unsigned *bar)
+{
+    __shared__ uint32_t s_scan[33];
+    __shared__ unsigned s_cnt[3];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t nb = F.nbricks;
+    uint32_t s[kMaxDim];
+#pragma unroll
+    for (int i = 0; i < kMaxDim; i++) s[i] = F.s[i];
+    const bool minimum = (F.flags & kFlagMinimum) != 0;
+
+    // 1: classification and the brick's records in index order
+    for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
+        if (tid < 3) s_cnt[tid] = 0;
+        const uint64_t v64 = uint64_t(b) * kSmallThreads + uint64_t(tid);
+        const bool in = v64 < F.N;
+        const uint32_t v = uint32_t(v64);
+        int b0 = 1;
+        uint64_t codes = 0;
+        bool nan = false;
+        if (in && chk(v, F.N, F.err)) F.lab[v] = classify_vertex<3, kF32>(F, s, v, minimum, b0, codes, nan);
+        if (nan) atomicOr(F.err, kErrNaN);
+        const bool crit = in && b0 != 1;
+        uint32_t tot;
+        const uint32_t pos = block_excl_scan(crit ? 1u : 0u, s_scan, &tot);  // (its barriers publish s_cnt = 0)
+        const uint64_t q = uint64_t(b) * F.bcap + pos;
+        if (crit && chk(q, rec_cap(F), F.err) && chk(pos, F.bcap, F.err)) {
+            F.rec_sid[q] = v;
+            F.rec_info[q] = (uint64_t(b0) << 56) | codes;
+            F.rec_val[q] = F.f[v];
+        }
+        const unsigned nm = __reduce_add_sync(0xffffffffu, crit && b0 == 0 ? 1u : 0u);
+        const unsigned ns = __reduce_add_sync(0xffffffffu, crit && b0 > 0 ? 1u : 0u);
+        const unsigned np = __reduce_add_sync(0xffffffffu, crit && b0 > 0 ? unsigned(b0) : 0u);
+        if (lane == 0) {
+            if (nm) atomicAdd(&s_cnt[0], nm);
+            if (ns) atomicAdd(&s_cnt[1], ns);
+            if (np) atomicAdd(&s_cnt[2], np);
+        }
+        __syncthreads();
+        if (tid == 0 && chk(b, nb, F.err)) F.bcnt[b] = make_uint4(s_cnt[0], s_cnt[1], s_cnt[2], 0u);
+        __syncthreads();  // s_cnt is cleared again by the next brick
+    }
+    if (!grid_barrier(bar, bar + 1, F.err)) return;
+
+    // 2: brick offsets (CTA 0: one thread per brick), labels (every thread)
+    if (blockIdx.x == 0) {
+        uint4 c = make_uint4(0u, 0u, 0u, 0u);
+        if (uint32_t(tid) < nb) c = F.bcnt[tid];
+        uint32_t tm, ts, tp;
+        const uint32_t om = block_excl_scan(c.x, s_scan, &tm);
+        const uint32_t os = block_excl_scan(c.y, s_scan, &ts);
+        const uint32_t op = block_excl_scan(c.z, s_scan, &tp);
+        if (uint32_t(tid) < nb) F.boff[tid] = make_uint4(om, os, op, 0u);
+        if (tid == 0) {
+            F.totals[0] = tm;
+            F.totals[1] = ts;
+            F.totals[2] = tp;
+        }
+    }
+    for (uint64_t v = uint64_t(blockIdx.x) * kSmallThreads + tid; v < F.N; v += uint64_t(gridDim.x) * kSmallThreads) {
+        uint32_t u = F.lab[v];
+        bool moved = false;
+        // a path climbs strictly in the order, so it has fewer than N steps
+        for (uint32_t steps = 0; u != uint32_t(v); steps++) {
+            if (steps > F.N) {
+                atomicOr(F.err, kErrNotConverged);
+                break;
+            }
+            if (!chk(u, F.N, F.err)) break;
+            const uint32_t w = F.lab[u];
+            if (w == u) break;  // a maximum
+            u = w;
+            moved = true;
+        }
+        if (moved) F.lab[v] = u;
+    }
+    if (!grid_barrier(bar, bar + 1, F.err)) return;
+
+    // 3: nodes and arc ends
+    constexpr uint32_t kWarps = kSmallThreads / 32;
+    for (uint32_t b = blockIdx.x * kWarps + uint32_t(warp); b < nb; b += gridDim.x * kWarps) nodes_brick<3>(F, b);
+    if (!grid_barrier(bar, bar + 1, F.err)) return;
+
+    // 4: arc offsets
+    if (blockIdx.x == 0) {
+        const uint32_t a = uint32_t(tid) < nb ? F.acnt[tid] : 0u;
+        uint32_t ta;
+        const uint32_t oa = block_excl_scan(a, s_scan, &ta);
+        if (uint32_t(tid) < nb) F.aoff[tid] = oa;
+        if (tid == 0) F.totals[3] = ta;
+    }
+    if (!grid_barrier(bar, bar + 1, F.err)) return;
+
+    // 5: CSR
+    for (uint32_t b = blockIdx.x * kWarps + uint32_t(warp); b < nb; b += gridDim.x * kWarps) csr_brick(F, b);
+}
+
+uint32_t small_bricks(uint64_t n) { return uint32_t((n + kSmallThreads - 1) / kSmallThreads); }
+
+cudaError_t launch_small(const FieldDev &F, unsigned *bar, int sm_count, cudaStream_t st)
+{
+    if (F.nbricks == 0 || F.nbricks > uint32_t(kSmallThreads) || F.bcap != uint32_t(kSmallThreads))
+        return cudaErrorInvalidValue;
+    // (the same kernel and CTA size on every device of the build's architecture)
+    static std::atomic<int> per_sm_cache{0};
+    int per_sm = per_sm_cache.load();
+    if (per_sm == 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_small, kSmallThreads, 0);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+        per_sm_cache.store(per_sm);
+    }
+    uint64_t grid = uint64_t(sm_count > 0 ? sm_count : 1) * uint64_t(per_sm);
+    if (grid > F.nbricks) grid = F.nbricks;
+    FieldDev arg = F;
+    void *args[] = {&arg, &bar};
+    return cudaLaunchCooperativeKernel(reinterpret_cast<void *>(k_small), dim3(unsigned(grid)), dim3(kSmallThreads),
+                                       args, 0, st);
+}
+
+}  // namespace eg

@@ -26,6 +26,7 @@ EG_FLAG_MINIMUM_GRAPH = 0x1
 EG_FLAG_NO_LABELS = 0x2
 EG_FLAG_NO_GRAPH = 0x4
 EG_FLAG_PATHS = 0x8
+EG_FLAG_NO_FUSED = 0x10
 
 # element types (eg_dtype): numpy dtype <-> code; EG_FLAG_DTYPE(t) = t << 16
 DTYPES = {np.dtype(np.float32): 0, np.dtype(np.float64): 1, np.dtype(np.int8): 2, np.dtype(np.uint8): 3,

@@ -193,6 +193,47 @@ def test_bounded_and_exact_result_buffers(handle, handle_min, shape):
     assert_same(run_gpu(handle_min, f.values), oracle.compute(f.values, minimum=True))
 
 
+@pytest.fixture(scope="module")
+def handles_general():
+    """Handles whose small fields take the general launches (no fused kernel)."""
+    from paper_2303_02724_gb300 import eg
+    hs = {m: eg.Handle(0, minimum=m, config=eg.EGConfig(flags=eg.EG_FLAG_NO_FUSED)) for m in (False, True)}
+    yield hs
+    for h in hs.values():
+        h.close()
+
+
+@pytest.mark.parametrize("shape", [(1,), (2,), (7,), (300,), (1, 1), (5, 3), (17, 9), (1, 5), (256, 256), (255, 257),
+                                   (1, 1, 1), (2, 3, 4), (9, 7, 5), (5, 1, 3), (41, 40, 40), (16, 64, 64)],
+                         ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("kind", ["normal", "ties"])
+def test_fused_and_general_small_paths(handle, handle_min, handles_general, shape, kind):
+    """Small 1D-3D float32 fields run every step in one cooperative launch
+    (the fused kernel) unless the handle asks for the general launches; both
+    match the oracle on both graphs: one brick and many, ragged last bricks,
+    ties, the largest fused field."""
+    seed = zlib.crc32(repr((shape, kind, "fused")).encode()) % 10000
+    f = F.white_noise(shape, seed) if kind == "normal" else F.integer_ties(shape, seed, 3)
+    og, ogm = oracle.compute(f.values), oracle.compute(f.values, minimum=True)
+    assert_same(run_gpu(handle, f.values), og)
+    assert_same(run_gpu(handle_min, f.values), ogm)
+    assert_same(run_gpu(handles_general[False], f.values), og)
+    assert_same(run_gpu(handles_general[True], f.values), ogm)
+
+
+def test_fused_kernel_is_one_launch(handle, handles_general):
+    """The fused path launches one kernel per small field; the general one
+    several."""
+    f = torch.from_numpy(F.white_noise((64, 64), 9).values).cuda()
+    for h, one in ((handle, True), (handles_general[False], False)):
+        n0 = h.launch_count()
+        rid = h.compute(f)
+        h.get_graph(rid)
+        h.release(rid)
+        n = h.launch_count() - n0
+        assert (n == 1) if one else (n > 3), n
+
+
 def test_bounded_result_reports_nan_when_read(handle):
     """A small field's NaN surfaces when the result is read; the handle
     stays usable and the next result is exact."""
