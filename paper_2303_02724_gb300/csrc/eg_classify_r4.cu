@@ -309,8 +309,22 @@ k_classify_r4(const FieldDev *__restrict__ fields, int nf)
             nm++;
             anynan |= C[i + 1] != C[i + 1];  // a NaN value has no upper neighbour
         } else if (ok && comp[i] != U) {
+            // the upper neighbours' values, reloaded through the cache: saddles
+            // are rare, and keeping the row segments live until here would
+            // make every vertex's registers spill
             float nb[30];
-            neighbours(i, nb);
+            const uint32_t up_slots = r4_slots(U), vi = vrow + x + uint32_t(i);
+#pragma unroll
+            for (int k = 0; k < 30; k++) {
+                nb[k] = qnan;
+                if ((up_slots >> k) & 1u) {
+                    const int pt = k < 15 ? 15 - k : k - 14;
+                    const uint32_t o = ((pt & 1) ? 1u : 0u) + ((pt & 2) ? s1 : 0u) + ((pt & 4) ? s2 : 0u) +
+                                       ((pt & 8) ? s3 : 0u);
+                    const uint32_t w = k < 15 ? vi - o : vi + o;
+                    if (chk(w, F.N, F.err)) nb[k] = __ldg(F.f + w);
+                }
+            }
             uint64_t codes = uint64_t(gslot[i]);
             int b0 = 1;
             for (uint32_t lft = U & ~comp[i]; lft;) {
