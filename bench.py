@@ -52,7 +52,7 @@ WORKLOADS = {
                      "plain single-field path (1.07 G vertices: the shape of Table 3's largest 5D row)"),
     "serve": ("Served stream: requests with Poisson arrivals, each a float32 2D/3D/4D field (vertex count "
               "log-uniform 1e4..1e7, sums of U{4..64} Gaussians + 1e-3 uniform noise), seed 4; admission by "
-              "free HBM, continuous batching on two engines, results kept in device memory"),
+              "free HBM, continuous batching on three engines, results kept in device memory"),
     "batch": ("Batched: 256 float32 fields, 2D (side log-uniform 64..2048) or 3D (side log-uniform 32..256) "
               "50/50, sums of U{4..64} Gaussians + 1e-3 uniform noise, seed 3; one submission (persistent "
               "work-queue classifier, captured CUDA graphs, knobs autotuned on the batch) vs per-field plain "
@@ -407,7 +407,10 @@ def serve_leg(args, ws, rank, local, n_requests, fractions):
     free, _total = torch.cuda.mem_get_info(local)
     # results stay in device memory until the client, called as each request
     # completes, releases them
-    engines = [serve.GpuEngine(local, results="device"), serve.GpuEngine(local, results="device")]
+    # three engines (host threads with a handle and stream each) so that one's
+    # host work overlaps the others' GPU work; batches of at most 32 requests
+    # and 64 M vertices keep the tail short under streaming arrivals
+    engines = [serve.GpuEngine(local, results="device") for _ in range(3)]
     budget = int(free * 0.6)
 
     def consume(r):
@@ -415,7 +418,7 @@ def serve_leg(args, ws, rank, local, n_requests, fractions):
             r.result.release()
 
     def run(offsets):
-        srv = serve.Server(engines, budget_bytes=budget, max_batch=64, max_batch_vertices=1 << 27,
+        srv = serve.Server(engines, budget_bytes=budget, max_batch=32, max_batch_vertices=1 << 26,
                            on_done=consume)
         serve.replay(srv, vals[:len(offsets)], offsets)
         srv.drain(3600)

@@ -216,6 +216,13 @@ EG_API eg_status eg_get_graph(eg_handle h, eg_result_id id, eg_graph *out);
  * DEVICE buffers instead of copying (valid until eg_release). */
 EG_API eg_status eg_get_graph_device(eg_handle h, eg_result_id id, eg_graph *out);
 
+/* eg_get_graph_device for n results in one call (one lock, one pass): out[i]
+ * for ids[i]; status[i] (may be NULL) receives each result's status.  Returns
+ * EG_OK, or the first failing result's status (the others are still filled).
+ * Errors: EG_ERR_ARG (n < 0, or NULL arrays with n > 0). */
+EG_API eg_status eg_get_graphs_device(eg_handle h, const eg_result_id *ids, int n, eg_graph *out,
+                                      int32_t *status);
+
 /* Arc geometry (Algorithm 2, Sec. 3.4): for every saddle, in the order of
  * eg_graph.saddles, and every component of its upper link, in ascending order
  * of its highest vertex (UpperLinkRep), the path of vertex ids

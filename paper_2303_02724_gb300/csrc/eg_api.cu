@@ -1263,6 +1263,26 @@ bool job_of(eg_ctx *h, const eg_field_desc &fd, Job &j)
     return true;
 }
 
+// Counts and library-owned device pointers of result `id` (waits for it).
+eg_status device_view(eg_ctx *h, eg_result_id id, eg_graph *out)
+{
+    auto it = h->results.find(id);
+    if (it == h->results.end()) return EG_ERR_ARG;
+    Result &r = *it->second;
+    eg_status s = collect(h, r);
+    fill_counts(r, out);
+    if (s != EG_OK) return s;
+    out->maxima = static_cast<uint32_t *>(r.maxima);
+    out->max_val = r.max_val;
+    out->saddles = static_cast<uint32_t *>(r.saddles);
+    out->sad_beta0 = static_cast<uint8_t *>(r.sad_b0);
+    out->sad_val = r.sad_val;
+    out->row_ptr = static_cast<uint64_t *>(r.row_ptr);
+    out->col = static_cast<uint32_t *>(r.col);
+    out->labels = static_cast<uint32_t *>(r.lab);
+    return EG_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1587,21 +1607,21 @@ eg_status eg_get_graph_device(eg_handle h, eg_result_id id, eg_graph *out)
     if (!h || !out) return EG_ERR_ARG;
     std::lock_guard<std::mutex> g(h->mu);
     cudaSetDevice(h->device);
-    auto it = h->results.find(id);
-    if (it == h->results.end()) return EG_ERR_ARG;
-    Result &r = *it->second;
-    eg_status s = collect(h, r);
-    fill_counts(r, out);
-    if (s != EG_OK) return s;
-    out->maxima = static_cast<uint32_t *>(r.maxima);
-    out->max_val = r.max_val;
-    out->saddles = static_cast<uint32_t *>(r.saddles);
-    out->sad_beta0 = static_cast<uint8_t *>(r.sad_b0);
-    out->sad_val = r.sad_val;
-    out->row_ptr = static_cast<uint64_t *>(r.row_ptr);
-    out->col = static_cast<uint32_t *>(r.col);
-    out->labels = static_cast<uint32_t *>(r.lab);
-    return EG_OK;
+    return device_view(h, id, out);
+}
+
+eg_status eg_get_graphs_device(eg_handle h, const eg_result_id *ids, int n, eg_graph *out, int32_t *status)
+{
+    if (!h || n < 0 || (n > 0 && (!ids || !out))) return EG_ERR_ARG;
+    std::lock_guard<std::mutex> g(h->mu);
+    cudaSetDevice(h->device);
+    eg_status first = EG_OK;
+    for (int i = 0; i < n; i++) {
+        const eg_status s = device_view(h, ids[i], out + i);
+        if (status) status[i] = int32_t(s);
+        if (s != EG_OK && first == EG_OK) first = s;
+    }
+    return first;
 }
 
 eg_status eg_release(eg_handle h, eg_result_id id)

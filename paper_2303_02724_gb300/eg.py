@@ -61,6 +61,12 @@ class EGFieldDesc(ctypes.Structure):
                 ("extents", ctypes.c_int64 * MAX_DIM)]
 
 
+# the same layout as a numpy record, for filling many descriptors at once
+_DESC_DTYPE = np.dtype([("field", np.uint64), ("d", np.int32), ("flags", np.int32),
+                        ("extents", np.int64, (MAX_DIM,))])
+assert _DESC_DTYPE.itemsize == ctypes.sizeof(EGFieldDesc)
+
+
 class EGGraphC(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int32), ("dtype", ctypes.c_int32), ("extents", ctypes.c_int64 * MAX_DIM),
                 ("n_vertices", ctypes.c_int64), ("n_maxima", ctypes.c_int64),
@@ -89,6 +95,8 @@ SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_uint64)]),
     "eg_get_graph": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(EGGraphC)]),
     "eg_get_graph_device": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.POINTER(EGGraphC)]),
+    "eg_get_graphs_device": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), ctypes.c_int,
+                                            ctypes.POINTER(EGGraphC), ctypes.POINTER(ctypes.c_int32)]),
     "eg_get_paths": (ctypes.c_int, [_P, ctypes.c_uint64, _P, _P, ctypes.POINTER(ctypes.c_uint64)]),
     "eg_get_bundled": (ctypes.c_int, [_P, ctypes.c_uint64, _P]),
     "eg_get_cancelled": (ctypes.c_int, [_P, ctypes.c_uint64, ctypes.c_float, _P, _P,
@@ -299,6 +307,22 @@ class Handle:
                "eg_batch_submit")
         return [ids[i] for i in range(n)]
 
+    def batch_submit_ptrs(self, ptrs: Sequence[int], extents: Sequence[tuple], stream=None) -> list:
+        """eg_batch_submit for float32 fields given as device addresses and
+        their extents (axis 0 first), without tensor objects per field."""
+        n = len(ptrs)
+        # the descriptor array filled column by column (EGFieldDesc's layout)
+        arr = np.zeros(max(1, n), dtype=_DESC_DTYPE)
+        arr["field"][:n] = ptrs
+        for i, ext in enumerate(extents):
+            arr["d"][i] = len(ext)
+            arr["extents"][i, :len(ext)] = ext
+        descs = ctypes.cast(arr.ctypes.data, ctypes.POINTER(EGFieldDesc))
+        ids = (ctypes.c_uint64 * max(1, n))()
+        _check(self._lib.eg_batch_submit(self._h, descs, n, ctypes.c_void_p(_stream_ptr(stream)), ids),
+               "eg_batch_submit")
+        return list(ids[:n])
+
     def autotune(self, fields: Sequence, stream=None) -> dict:
         """Pick the fastest knob values on these fields; returns them."""
         descs = self._descs(fields)
@@ -404,6 +428,14 @@ class Handle:
         _check(self._lib.eg_get_graph_device(self._h, ctypes.c_uint64(rid), ctypes.byref(g)),
                "eg_get_graph_device")
         return g
+
+    def get_graphs_device(self, rids: Sequence[int]) -> list:
+        """get_graph_device for many results in one library call."""
+        n = len(rids)
+        ids = (ctypes.c_uint64 * max(1, n))(*rids)
+        gs = (EGGraphC * max(1, n))()
+        _check(self._lib.eg_get_graphs_device(self._h, ids, n, gs, None), "eg_get_graphs_device")
+        return [gs[i] for i in range(n)]
 
     def release(self, rid: int):
         _check(self._lib.eg_release(self._h, ctypes.c_uint64(rid)), "eg_release")

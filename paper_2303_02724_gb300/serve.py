@@ -65,6 +65,7 @@ class Request:
     batch: int = -1                    # batch sequence number it ran in
     engine: int = -1
     event: threading.Event = dc_field(default_factory=threading.Event)
+    nbytes: int = 0                    # device bytes reserved for it while admitted
 
     @property
     def n(self) -> int:
@@ -115,16 +116,21 @@ class GpuEngine:
         torch = self.torch
         sizes = [r.n for r in reqs]
         if all(r.pinned is not None for r in reqs):
-            offs = np.concatenate([[0], np.cumsum([(n + 3) & ~3 for n in sizes])])
-            total = int(offs[-1])
+            padded = [(n + 3) & ~3 for n in sizes]  # 16-byte aligned fields
+            total = sum(padded)
             if self._dev is None or self._dev.numel() < total:
                 self._dev = torch.empty(max(total, 1 << 20), dtype=torch.float32, device=self.device)
-            out = []
-            for r, o in zip(reqs, offs[:-1]):
-                d = self._dev[int(o):int(o) + r.n]
-                d.copy_(r.pinned.view(-1), non_blocking=True)
-                out.append(d.view(r.values.shape))
-            return out
+            # one call for all the batch's copies (views of one buffer)
+            slots = self._dev[:total].split(padded)
+            dst = [sl[:n] for sl, n in zip(slots, sizes)]
+            src = [r.pinned.view(-1) for r in reqs]
+            foreach = getattr(torch, "_foreach_copy_", None)
+            if foreach is not None:
+                foreach(dst, src, non_blocking=True)
+            else:
+                for a, b in zip(dst, src):
+                    a.copy_(b, non_blocking=True)
+            return dst
         offs = np.concatenate([[0], np.cumsum([(n + 3) & ~3 for n in sizes])])  # 16-byte aligned fields
         total = int(offs[-1])
         if self._pinned is None or self._pinned.numel() < total:
@@ -147,15 +153,17 @@ class GpuEngine:
         torch = self.torch
         with torch.cuda.stream(self.stream):
             ts = self._upload(reqs)
-            ids = self.handle.batch_submit(ts, self.stream)
-            keep = []
+            ids = self.handle.batch_submit_ptrs([t.data_ptr() for t in ts],
+                                                [tuple(reversed(r.values.shape)) for r in reqs], self.stream)
+            keep = set()
             try:
-                for r, rid in zip(reqs, ids):
-                    if self.results == "host":
+                if self.results == "host":
+                    for r, rid in zip(reqs, ids):
                         r.result = self.handle.get_graph(rid, labels=False)
-                    else:
-                        r.result = DeviceResult(self, rid, self.handle.get_graph_device(rid))
-                        keep.append(rid)
+                else:
+                    for r, rid, g in zip(reqs, ids, self.handle.get_graphs_device(ids)):
+                        r.result = DeviceResult(self, rid, g)
+                        keep.add(rid)
             finally:
                 for rid in ids:
                     if rid not in keep:
@@ -208,7 +216,8 @@ class Server:
             r.rid = self.next_rid
             self.next_rid += 1
             r.arrival = time.perf_counter()
-            if self.bytes_fn(r.n, r.values.ndim) > self.budget:
+            r.nbytes = self.bytes_fn(r.n, r.values.ndim)
+            if r.nbytes > self.budget:
                 r.status = EG_ERR_BUSY
                 r.done = r.arrival
                 r.event.set()
@@ -239,8 +248,8 @@ class Server:
     def _take(self) -> List[Request]:
         """Under the lock: admit queued requests, in order, while they fit."""
         batch, verts, need = [], 0, 0
-        for r in list(self.queue):
-            b = self.bytes_fn(r.n, r.values.ndim)
+        for r in self.queue:  # (not modified while iterated; popped below)
+            b = r.nbytes
             if len(batch) >= self.max_batch or (batch and verts + r.n > self.max_batch_vertices):
                 break
             if self.in_use + need + b > self.budget:
@@ -289,7 +298,7 @@ class Server:
                     r.status = status
                     self.completed.append(r)
                     r.event.set()
-                self.in_use -= sum(self.bytes_fn(r.n, r.values.ndim) for r in batch)
+                self.in_use -= sum(r.nbytes for r in batch)
                 self.in_flight_batches -= 1
                 self.cv.notify_all()
 

@@ -265,6 +265,33 @@ def test_pinned_buffers_reused(handle):
     handle.release(rid)
 
 
+def test_graphs_device_in_one_call(handle):
+    """eg_get_graphs_device fills the same counts and device pointers as one
+    eg_get_graph_device per result, and reports a bad id in its entry."""
+    import ctypes
+    from paper_2303_02724_gb300 import eg
+    fs = [torch.from_numpy(F.white_noise(e, 7).values).cuda() for e in [(40, 30), (9, 8, 7), (500,), (70, 60)]]
+    ids = handle.batch_submit(fs)
+    try:
+        many = handle.get_graphs_device(ids)
+        for rid, gm in zip(ids, many):
+            g1 = handle.get_graph_device(rid)
+            for name, _ in eg.EGGraphC._fields_:
+                v1, vm = getattr(g1, name), getattr(gm, name)
+                if isinstance(v1, (int, float)) or v1 is None:
+                    assert v1 == vm, name
+        lib = eg.load()
+        bad = (ctypes.c_uint64 * 2)(ids[0], max(ids) + 100)
+        out = (eg.EGGraphC * 2)()
+        st = (ctypes.c_int32 * 2)()
+        assert lib.eg_get_graphs_device(handle._h, bad, 2, out, st) == eg.EG_ERR_ARG
+        assert st[0] == eg.EG_OK and st[1] == eg.EG_ERR_ARG
+        assert out[0].n_maxima == many[0].n_maxima
+    finally:
+        for rid in ids:
+            handle.release(rid)
+
+
 def test_batch_uneven(handle):
     specs = F.batch_specs(3, 24, scale=0.12)
     flds = [F.batch_field(e, s, gn) for (e, s, gn) in specs]
