@@ -26,12 +26,15 @@ def main():
     _build.build(checked=True)
     eg.load()
     n = 0
-    with eg.Handle(0) as hmax, eg.Handle(0, minimum=True) as hmin:
+    general = eg.EGConfig(flags=eg.EG_FLAG_NO_FUSED)
+    with eg.Handle(0) as hmax, eg.Handle(0, minimum=True) as hmin, eg.Handle(0, config=general) as gmax:
+        # (small 1D-3D fields take the fused kernel; gmax sends them through
+        # the general launches too)
         for i, ext in enumerate(shapes()):
             for kind in ("white", "ties"):
                 f = F.white_noise(ext, 100 + i) if kind == "white" else F.integer_ties(ext, 100 + i, 3)
                 t = torch.from_numpy(f.values).cuda()
-                for h, minimum in ((hmax, False), (hmin, True)):
+                for h, minimum in ((hmax, False), (hmin, True), (gmax, False)):
                     g = h.graph_of(t)  # raises on any status, the bounds status included
                     o = oracle.compute(f.values, minimum=minimum)
                     ok = (np.array_equal(g.labels, o.label) and np.array_equal(g.maxima, o.maxima)
