@@ -292,6 +292,7 @@ struct Layout {
     int kd;
     bool zm;
     bool r4;  // 4D row classifier (row layout over (z, w) planes)
+    bool r5;  // 5D row classifier (row layout over (z, w, u) planes)
     uint32_t ty, nyb, nbricks, bcap, zc, nzc;
     size_t smem;
 };
@@ -343,6 +344,18 @@ Layout make_layout(const Shape &sh, int sm_count, const eg_config &cfg, uint32_t
         L.ty = ty;
         L.nyb = (n1 + ty - 1) / ty;
         L.nbricks = L.nyb * n2 * sh.n[3];
+        L.bcap = ty * n0;
+        L.zc = L.nzc = 0;
+        L.smem = 0;
+    } else if (L.kd == 5 && n0 <= kR5MaxRow && f32_values) {
+        // 5D row classifier: ty whole rows of one (z, w, u) plane per brick,
+        // classified in up to kR5Passes passes of one vertex per thread
+        const uint32_t ty = std::max<uint32_t>(1, std::min<uint32_t>(uint32_t(kR5CtaThreads) / n0 * kR5Passes, n1));
+        L.zm = false;
+        L.r5 = true;
+        L.ty = ty;
+        L.nyb = (n1 + ty - 1) / ty;
+        L.nbricks = L.nyb * n2 * sh.n[3] * sh.n[4];
         L.bcap = ty * n0;
         L.zc = L.nzc = 0;
         L.smem = 0;
@@ -447,6 +460,7 @@ struct Group {
     int kd;
     uint32_t cdt;  // type the classifier compares in (float32 for narrow integers)
     bool r4;
+    bool r5;
 };
 
 // A field (table position) whose element type needs extra work.
@@ -500,6 +514,8 @@ eg_status enqueue_part(eg_ctx *h, int part, const Plan &P, const FieldDev *Dd, c
                                        P.ctas, st);
             else if (G.r4)
                 e = launch_classify_r4(G.minimum, Dd + G.first, G.count, G.bricks, st);
+            else if (G.r5)
+                e = launch_classify_r5(G.minimum, Dd + G.first, G.count, G.bricks, st);
             else
                 e = launch_classify_flat(G.kd, G.cdt, Dd + G.first, G.count, G.bricks, st);
             if (e != cudaSuccess) return from_cuda(e);
@@ -694,7 +710,7 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
     auto key = [&](int i) {
         // (the plane-marching kernel's rows longer than 1024 vertices launch
         // on their own: their ring needs more shared memory per CTA)
-        const int kind = lay[i].zm ? (jobs[i].sh.n[0] > 1024 ? 3 : 0) : (lay[i].r4 ? 1 : 2);
+        const int kind = lay[i].zm ? (jobs[i].sh.n[0] > 1024 ? 3 : 0) : (lay[i].r4 ? 1 : (lay[i].r5 ? 4 : 2));
         return int(cdt(i)) * 64 + kind * 16 + lay[i].kd * 2 + ((jobs[i].flags & kFlagMinimum) ? 1 : 0);
     };
     std::vector<int> order(nf);
@@ -751,7 +767,8 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
         const Layout &ly = lay[i];
         if (P.groups.empty() || P.groups.back().key != key(i))
             P.groups.push_back(
-                {key(i), oi, 0, brick0, 0, 0, 0, ly.zm, (j.flags & kFlagMinimum) != 0, ly.kd, cdt(i), ly.r4});
+                {key(i), oi, 0, brick0, 0, 0, 0, ly.zm, (j.flags & kFlagMinimum) != 0, ly.kd, cdt(i), ly.r4,
+                 ly.r5});
         Group &G = P.groups.back();
         auto r = std::make_unique<Result>();
         r->d = j.sh.d;

@@ -18,6 +18,12 @@ cudaError_t launch_classify_flat(int kd, uint32_t dtype, const FieldDev *fields,
 // 1024 vertices (row layout: ty whole rows of one (z, w) plane per brick);
 // one CTA per brick, global ids from fields[0].brick0.
 cudaError_t launch_classify_r4(bool minimum, const FieldDev *fields, int nf, uint64_t bricks, cudaStream_t st);
+// 5D row classifier: float32 fields whose rows hold at most kR5MaxRow
+// vertices; one thread per vertex, bricks of whole rows of one (z, w, u) plane.
+constexpr int kR5CtaThreads = 256;
+constexpr uint32_t kR5MaxRow = 256;
+constexpr uint32_t kR5Passes = 4;  // bricks of up to 4 x 256 vertices
+cudaError_t launch_classify_r5(bool minimum, const FieldDev *fields, int nf, uint64_t bricks, cudaStream_t st);
 constexpr int kR4Vertices = 4;    // vertices per thread along axis 0
 constexpr int kR4CtaThreads = 256;
 
