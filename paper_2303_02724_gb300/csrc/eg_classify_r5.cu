@@ -114,7 +114,13 @@ __global__ void __launch_bounds__(kR5Threads) k_classify_r5(const FieldDev *__re
         // upper bits in the pattern layout: positive pattern p at bit p, negative
         // at bit 32 + p; four accumulators of at most 16 bits each
         float aP0 = 8388608.f, aP1 = 8388608.f, aN0 = 8388608.f, aN1 = 8388608.f;
-        float best = 0.f;
+        // running extreme over all 62 values (NaN ignored) and the slot of its
+        // last (minimum graph: first) occurrence; that slot is upper whenever
+        // the link has an upper neighbour: an extreme strictly beyond c is
+        // upper in either half, and an extreme equal to c is upper exactly in
+        // the half the tie rule prefers (positive slots come later), so the
+        // upper test need not gate the update
+        float best = MIN ? __int_as_float(0x7f800000) : __int_as_float(0xff800000);
         int bestk = -1;
         auto consider = [&](int k, float nb) {  // slot k (Nbr<5> order), value nb
             const bool neg = k < 31;
@@ -129,10 +135,9 @@ __global__ void __launch_bounds__(kR5Threads) k_classify_r5(const FieldDev *__re
             }
             // slots arrive in increasing order: ties go to the later slot (>=),
             // in the minimum graph to the earlier one (<)
-            if (up != 0.f && (bestk < 0 || (MIN ? nb < best : nb >= best))) {
-                best = nb;
-                bestk = k;
-            }
+            const bool t = MIN ? nb < best : nb >= best;
+            best = MIN ? fminf(best, nb) : fmaxf(best, nb);
+            bestk = t ? k : bestk;
         };
         // negative rows q = 15 .. 1: slots 30 - 2q (pattern 2q + 1, column x - 1)
         // and 31 - 2q (pattern 2q, column x)
