@@ -9,8 +9,7 @@
 // lies in row q = p >> 1 (offset along the axes of q) at column x - (p & 1)
 // (negative) or x + (p & 1) (positive),
 // so 31 rows are read: the centre row and 15 on each side, one coalesced value
-// per thread per row, the columns x - 1 and x + 1 from the neighbouring lanes
-// by shuffle.  Rows are consumed as they arrive, in slot order: the upper bits
+// per thread per row and the column x - 1 or x + 1 from the same cache lines.  Rows are consumed as they arrive, in slot order: the upper bits
 // (set-compares accumulated with FMAs into floats whose exponent pins the
 // integer part) and the running extreme with its slot, so only the centre
 // value and a few accumulators stay live.  Out-of-domain rows and columns read
@@ -93,22 +92,17 @@ __global__ void __launch_bounds__(kR5Threads) k_classify_r5(const FieldDev *__re
             (y + 1 < n1 ? 1u : 0u) | (z + 1 < n2 ? 2u : 0u) | (w + 1 < n3 ? 4u : 0u) | (u + 1 < n4 ? 8u : 0u);
         const float c = (rowok && chk(v, F.N, F.err)) ? __ldg(F.f + v) : qnan;
 
-        // row q's value at column x, and the columns x - 1 / x + 1 (all lanes run
-        // every row: they are one another's shuffle partners)
+        // row q's value at column x, and at column x - 1 (negative rows) or
+        // x + 1 (positive rows)
         auto row = [&](int q, bool neg, float &vx, float &vside) {
             const bool ok = rowok && (neg ? (lo & uint32_t(q)) == uint32_t(q) : (hi & uint32_t(q)) == uint32_t(q));
             const uint32_t o = r5_row_off(q, s1, s2, s3, s4);
             const uint32_t rb = neg ? v - o : v + o;
             vx = (ok && chk(rb, F.N, F.err)) ? __ldg(F.f + rb) : qnan;
-            if (neg) {
-                float l = __shfl_up_sync(0xffffffffu, vx, 1);
-                if (lane == 0) l = (ok && left_ok && chk(rb - 1, F.N, F.err)) ? __ldg(F.f + rb - 1) : qnan;
-                vside = left_ok ? l : qnan;
-            } else {
-                float rr = __shfl_down_sync(0xffffffffu, vx, 1);
-                if (lane == 31) rr = (ok && right_ok && chk(rb + 1, F.N, F.err)) ? __ldg(F.f + rb + 1) : qnan;
-                vside = right_ok ? rr : qnan;
-            }
+            // (a second load from the same cache lines costs fewer instructions
+            // than a shuffle with its lane-edge fix-up)
+            if (neg) vside = (ok && left_ok && chk(rb - 1, F.N, F.err)) ? __ldg(F.f + rb - 1) : qnan;
+            else vside = (ok && right_ok && chk(rb + 1, F.N, F.err)) ? __ldg(F.f + rb + 1) : qnan;
         };
 
         // upper bits in the pattern layout: positive pattern p at bit p, negative
@@ -150,12 +144,8 @@ __global__ void __launch_bounds__(kR5Threads) k_classify_r5(const FieldDev *__re
         }
         {
             // centre row: slot 30 (pattern 1, column x - 1) and 31 (column x + 1)
-            float l = __shfl_up_sync(0xffffffffu, c, 1);
-            if (lane == 0) l = (rowok && left_ok && chk(v - 1, F.N, F.err)) ? __ldg(F.f + v - 1) : qnan;
-            float rr = __shfl_down_sync(0xffffffffu, c, 1);
-            if (lane == 31) rr = (rowok && right_ok && chk(v + 1, F.N, F.err)) ? __ldg(F.f + v + 1) : qnan;
-            consider(30, left_ok ? l : qnan);
-            consider(31, right_ok ? rr : qnan);
+            consider(30, (rowok && left_ok && chk(v - 1, F.N, F.err)) ? __ldg(F.f + v - 1) : qnan);
+            consider(31, (rowok && right_ok && chk(v + 1, F.N, F.err)) ? __ldg(F.f + v + 1) : qnan);
         }
         // positive rows q = 1 .. 15: slots 30 + 2q (pattern 2q, column x) and
         // 31 + 2q (pattern 2q + 1, column x + 1)

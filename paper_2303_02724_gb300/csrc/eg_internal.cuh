@@ -399,7 +399,7 @@ struct PatternLink {
                 dn |= (dn >> (1 << i)) & lacks(i);
             }
             const Mask n = (up | dn) & u;
-            if (n == s) return s;
+            if (n == s || n == u) return n;  // (nothing can join a component that is all of u)
             s = n;
         }
     }
