@@ -152,6 +152,31 @@ __device__ __forceinline__ unsigned long long c_eval(const CancelDev &C, int b, 
     return cost <= C.tau ? ck : kNoKey;
 }
 
+// Phase 1 shortcut for a saddle evaluated in the round before: when every
+// maximum it reached then is still a survivor (no merge took one away; merges
+// happen only in phase 3, so the survivors are fixed during phase 1), its
+// maxima, keys and highest maximum are the same as then.  The snapshot of set
+// b ^ 1 is carried over to set b and the stored lb key contributed; *ck
+// receives its cost key if it may be cancelled.  Returns false (nothing
+// written) when a maximum changed.
+__device__ __forceinline__ bool c_unchanged(const CancelDev &C, int b, uint32_t s, unsigned long long *ck)
+{
+    const uint64_t a0 = C.row_ptr[s], a1 = C.row_ptr[s + 1];
+    for (uint64_t a = a0; a < a1; a++) {
+        const uint32_t r = C.aroot[b ^ 1][a];
+        if (C.parent[r] != r) return false;
+    }
+    const unsigned long long lk = C.lbkey[s];
+    for (uint64_t a = a0; a < a1; a++) {
+        const uint32_t r = C.aroot[b ^ 1][a];
+        C.aroot[b][a] = r;
+        atomicMin(C.minlb[b] + r, lk);
+    }
+    const unsigned long long k = C.costkey[s];
+    *ck = __uint_as_float(uint32_t(k >> 32)) <= C.tau ? k : kNoKey;
+    return true;
+}
+
 // Clear the per-maximum minima of set b that saddle s wrote (through the
 // snapshot of set b).
 __device__ __forceinline__ void c_clear(const CancelDev &C, int b, uint32_t s)
@@ -279,7 +304,10 @@ __global__ void __launch_bounds__(kCancelThreads) k_cancel_rounds(CancelDev C)
                 s = C.list[p][i];
                 if (round > 0) c_clear(C, b ^ 1, s);
                 if (C.state[s] == 0) {
-                    const unsigned long long k = c_eval(C, b, s);
+                    // (every saddle of a later round's list was evaluated in the
+                    // round before and still waits)
+                    unsigned long long k;
+                    if (round == 0 || !c_unchanged(C, b, s, &k)) k = c_eval(C, b, s);
                     if (k != kNoKey) atomicMin(slot, k);
                     keep = C.state[s] == 0;
                 }
