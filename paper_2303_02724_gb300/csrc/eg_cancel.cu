@@ -300,18 +300,25 @@ __global__ void __launch_bounds__(kCancelThreads) k_cancel_rounds(CancelDev C)
             const uint64_t i = base + lane;
             bool keep = false;
             uint32_t s = 0;
+            unsigned long long k = kNoKey;
             if (i < n) {
                 s = C.list[p][i];
                 if (round > 0) c_clear(C, b ^ 1, s);
                 if (C.state[s] == 0) {
                     // (every saddle of a later round's list was evaluated in the
                     // round before and still waits)
-                    unsigned long long k;
                     if (round == 0 || !c_unchanged(C, b, s, &k)) k = c_eval(C, b, s);
-                    if (k != kNoKey) atomicMin(slot, k);
                     keep = C.state[s] == 0;
                 }
             }
+            // the warp's cheapest key, then one atomic per warp (every
+            // candidate of the round would otherwise meet at one address)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long y = __shfl_xor_sync(0xffffffffu, k, o);
+                k = y < k ? y : k;
+            }
+            if (lane == 0 && k != kNoKey) atomicMin(slot, k);
             const unsigned m = __ballot_sync(0xffffffffu, keep);
             if (!m) continue;
             unsigned long long o = 0;
