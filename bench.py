@@ -18,6 +18,7 @@ a bounded slab of the same workload.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import platform
@@ -404,6 +405,11 @@ def serve_leg(args, ws, rank, local, n_requests, fractions):
     # requests arrive in page-locked host buffers (where a network receive
     # path would place them); the engines copy them straight to the device
     vals = [torch.from_numpy(v).pin_memory() for v in vals]
+    # the interpreter's cyclic collector would otherwise walk every object of
+    # the process (this bench holds many) in the middle of a served stream:
+    # collect once, then leave what exists now out of later collections
+    gc.collect()
+    gc.freeze()
     free, _total = torch.cuda.mem_get_info(local)
     # results stay in device memory until the client, called as each request
     # completes, releases them
@@ -435,6 +441,7 @@ def serve_leg(args, ws, rank, local, n_requests, fractions):
         res[str(frac)] = run(offs)
     for e in engines:
         e.close()
+    gc.unfreeze()
     # the same requests one at a time through the plain path (upload, compute,
     # wait, release), for comparison with the served throughput
     hp = eg.Handle(local)

@@ -175,7 +175,13 @@ class GpuEngine:
 
 
 class Server:
-    """Continuous batching over one or more engines with device-memory admission."""
+    """Continuous batching over one or more engines with device-memory admission.
+
+    The engines' threads run Python between their library calls, so a
+    collection of the interpreter's cyclic garbage collector stalls them all;
+    in a process holding many objects that pause sets the latency tail.
+    Callers that serve under latency targets should collect once and call
+    gc.freeze() before the stream starts (the benchmark does)."""
 
     def __init__(self, engines: list, budget_bytes: int, max_batch: int = 128,
                  max_batch_vertices: int = 1 << 28,
