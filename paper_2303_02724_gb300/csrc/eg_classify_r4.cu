@@ -9,8 +9,8 @@
 // lies in row q = p >> 1 (offset s along the axes of q) at column x + s*(p&1),
 // so 15 rows are read: the centre row at x-1 .. x+4, the seven negative rows
 // at x-1 .. x+3, the seven positive rows at x .. x+4.  Columns x .. x+3 come
-// from one 16-byte load, the end columns from the neighbouring lanes by
-// shuffle.  Out-of-domain rows and columns read NaN, which fails every
+// from one 16-byte load, the end columns from one more load of the same cache
+// lines.  Out-of-domain rows and columns read NaN, which fails every
 // ordered comparison and is skipped by min/max, so no bounds test enters the
 // per-vertex work.
 //
@@ -156,7 +156,7 @@ k_classify_r4(const FieldDev *__restrict__ fields, int nf)
     const bool first_t = xt == 0, last_t = x + kR4Vx >= n0;
 
     // columns x .. x+3 of the row at offset `off` (sign sg) from this thread's
-    // row, NaN outside the domain; all lanes execute it (shuffle partners)
+    // row, NaN outside the domain
     auto seg = [&](uint32_t q, bool neg, float *v) {
         const uint32_t dy = q & 1u, dz = (q >> 1) & 1u, dw = (q >> 2) & 1u;
         bool ok = rowok;
@@ -179,17 +179,14 @@ k_classify_r4(const FieldDev *__restrict__ fields, int nf)
         return ok ? rb : 0xffffffffu;
     };
     // column x-1 (left) and x+4 (right) of a row whose segment is v
+    // (a load from the same cache lines costs fewer instructions than a
+    // shuffle from the neighbouring lane with its fix-up at the warp's edges)
     auto left = [&](uint32_t rb, const float *v) {
-        float l = __shfl_up_sync(0xffffffffu, v[kR4Vx - 1], 1);
-        if (lane == 0) l = (rb != 0xffffffffu && !first_t && chk(uint64_t(rb) + x - 1, F.N, F.err)) ? __ldg(F.f + rb + x - 1) : qnan;
-        return first_t ? qnan : l;
+        return (rb != 0xffffffffu && !first_t && chk(uint64_t(rb) + x - 1, F.N, F.err)) ? __ldg(F.f + rb + x - 1) : qnan;
     };
     auto right = [&](uint32_t rb, const float *v) {
-        float rr = __shfl_down_sync(0xffffffffu, v[0], 1);
-        if (lane == 31)
-            rr = (rb != 0xffffffffu && !last_t && chk(uint64_t(rb) + x + kR4Vx, F.N, F.err)) ? __ldg(F.f + rb + x + kR4Vx)
-                                                                                              : qnan;
-        return last_t ? qnan : rr;
+        return (rb != 0xffffffffu && !last_t && chk(uint64_t(rb) + x + kR4Vx, F.N, F.err)) ? __ldg(F.f + rb + x + kR4Vx)
+                                                                                             : qnan;
     };
 
     // C: centre row, columns x-1 .. x+4 (index j+1 for column x+j)
@@ -289,7 +286,7 @@ k_classify_r4(const FieldDev *__restrict__ fields, int nf)
             dn |= (dn >> 4) & 0x0f0f0f0fu;
             dn |= (dn >> 8) & 0x00ff00ffu;
             const uint32_t nx = (upc | dn) & Um[i];
-            grew |= nx != s0;
+            grew |= nx != s0 && nx != Um[i];  // (a whole upper link cannot grow)
             comp[i] = nx;
         }
         if (!grew) break;
