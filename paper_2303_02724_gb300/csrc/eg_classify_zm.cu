@@ -371,9 +371,8 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
         // neighbours read NaN pads, which fail every ordered comparison, are
         // ignored by min/max and never equal anything.
         // row segments: C rows r-1..r+1 at x-1..x+8, D rows r-1..r at
-        // x-1..x+7, U rows r..r+1 at x..x+8.  Every lane loads (lanes without
-        // vertices read ring row 1 and discard it) so that the end columns
-        // can come from the neighbouring lanes.
+        // x-1..x+7, U rows r..r+1 at x..x+8 (lanes without vertices read ring
+        // row 1 and discard it).
         float C[3][kVx + 2], D[2][kVx + 1], U[2][kVx + 1];
         {
             const uint32_t rl = rowok ? rr : 1u;
@@ -396,18 +395,15 @@ k_classify_zm(const FieldDev *__restrict__ fields, int nf, const uint32_t *__res
                     for (int b = 0; b < kVx; b++) v[b] = row[zm_col(int(x) + b)];
                 }
             };
-            // column x-1: the left lane's last value, or a load at a warp edge
-            auto left = [&](const float *row, float last) {
-                float l = __shfl_up_sync(0xffffffffu, last, 1);
-                if (lane == 0) l = chk_ptr(row + zm_col(int(x) - 1), ring, ringn, F.err) ? row[zm_col(int(x) - 1)] : qnan;
-                return first_t ? qnan : l;
+            // columns x-1 and x+8, read from the ring (cheaper than a shuffle
+            // from the neighbouring lane with a fix-up read at the warp's edges)
+            auto left = [&](const float *row, float) {
+                if (first_t) return qnan;
+                return chk_ptr(row + zm_col(int(x) - 1), ring, ringn, F.err) ? row[zm_col(int(x) - 1)] : qnan;
             };
-            // column x+8: the right lane's first value, or a load at a warp edge
-            auto right = [&](const float *row, float first) {
-                float v = __shfl_down_sync(0xffffffffu, first, 1);
-                if (lane == 31)
-                    v = chk_ptr(row + zm_col(int(x) + kVx), ring, ringn, F.err) ? row[zm_col(int(x) + kVx)] : qnan;
-                return last_t ? qnan : v;
+            auto right = [&](const float *row, float) {
+                if (last_t) return qnan;
+                return chk_ptr(row + zm_col(int(x) + kVx), ring, ringn, F.err) ? row[zm_col(int(x) + kVx)] : qnan;
             };
 #pragma unroll
             for (int a = 0; a < 3; a++) {
