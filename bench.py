@@ -18,6 +18,7 @@ a bounded slab of the same workload.
 from __future__ import annotations
 
 import argparse
+import contextlib
 import gc
 import json
 import os
@@ -198,6 +199,20 @@ def graph_d2h_bytes(c):
     return 8 * M + 9 * S + 8 * (S + 1) + 4 * A
 
 
+@contextlib.contextmanager
+def quiet_gc():
+    """Keep the interpreter's cyclic collector out of a timed region (as
+    timeit does): this process holds many objects (fields, arrays, results),
+    and a collection walking them in the middle of a run stalls the host loop
+    that feeds the GPU.  Collect once, then exempt the existing objects."""
+    gc.collect()
+    gc.freeze()
+    try:
+        yield
+    finally:
+        gc.unfreeze()
+
+
 def traffic_from_profiles(step, workload):
     """DRAM bytes per launch of `step`'s kernels on `workload` from the
     committed ncu summary, if it was taken on the kernels' current source
@@ -333,11 +348,12 @@ def batch_leg(args, ws, rank, local, steps, warmup):
         l0 = hh.launch_count()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            fn()
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
+        with quiet_gc():
+            e0.record(stream)
+            for _ in range(steps):
+                fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
         ms = replicas.reduce_max(e0.elapsed_time(e1) / steps, device=dev)
         out[name] = {"ms_per_step": ms, "value": sum(sizes) / (ms / 1e3) / 1e6,
                      "gpu_launches": int(hh.launch_count() - l0)}
@@ -405,11 +421,6 @@ def serve_leg(args, ws, rank, local, n_requests, fractions):
     # requests arrive in page-locked host buffers (where a network receive
     # path would place them); the engines copy them straight to the device
     vals = [torch.from_numpy(v).pin_memory() for v in vals]
-    # the interpreter's cyclic collector would otherwise walk every object of
-    # the process (this bench holds many) in the middle of a served stream:
-    # collect once, then leave what exists now out of later collections
-    gc.collect()
-    gc.freeze()
     free, _total = torch.cuda.mem_get_info(local)
     # results stay in device memory until the client, called as each request
     # completes, releases them
@@ -432,16 +443,17 @@ def serve_leg(args, ws, rank, local, n_requests, fractions):
         return srv.stats()
 
     run(np.zeros(len(vals)))  # warm-up: pools and staging buffers reach their steady size
-    cap = run(np.zeros(len(vals)))  # everything queued at once: capacity
+    with quiet_gc():
+        cap = run(np.zeros(len(vals)))  # everything queued at once: capacity
     rate_v = cap["throughput_mvps"] * 1e6
     mean_n = nv / len(vals)
     res = {}
     for frac in fractions:
         offs = serve.poisson_arrivals(frac * rate_v / mean_n, len(vals), 4)
-        res[str(frac)] = run(offs)
+        with quiet_gc():
+            res[str(frac)] = run(offs)
     for e in engines:
         e.close()
-    gc.unfreeze()
     # the same requests one at a time through the plain path (upload, compute,
     # wait, release), for comparison with the served throughput
     hp = eg.Handle(local)
@@ -450,13 +462,14 @@ def serve_leg(args, ws, rank, local, n_requests, fractions):
         hp.get_graph_device(rid)
         hp.release(rid)
     torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    for v in vals:
-        rid = hp.compute(v.to(dev, non_blocking=True))
-        hp.get_graph_device(rid)
-        hp.release(rid)
-    torch.cuda.synchronize(dev)
-    plain_s = time.perf_counter() - t0
+    with quiet_gc():
+        t0 = time.perf_counter()
+        for v in vals:
+            rid = hp.compute(v.to(dev, non_blocking=True))
+            hp.get_graph_device(rid)
+            hp.release(rid)
+        torch.cuda.synchronize(dev)
+        plain_s = time.perf_counter() - t0
     hp.close()
     plain = {"throughput_mvps": nv / plain_s / 1e6, "seconds": plain_s,
              "mode": "each request alone: upload, eg_compute, wait, release"}
@@ -575,28 +588,29 @@ def main():
         dist.barrier()
     torch.cuda.synchronize(dev)
     step_ms = []
-    if flush is None:
-        e0.record(stream)
-        for _ in range(args.steps):
-            rid, g = step()
-            step_ms.append(h.step_times(rid))
-            h.release(rid)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        ms_total = e0.elapsed_time(e1)
-    else:
-        # field smaller than L2: overwrite L2 before every step, outside the
-        # timed spans
-        ms_total = 0.0
-        for _ in range(args.steps):
-            flush.add_(1)
+    with quiet_gc():
+        if flush is None:
             e0.record(stream)
-            rid, g = step()
+            for _ in range(args.steps):
+                rid, g = step()
+                step_ms.append(h.step_times(rid))
+                h.release(rid)
             e1.record(stream)
             torch.cuda.synchronize(dev)
-            ms_total += e0.elapsed_time(e1)
-            step_ms.append(h.step_times(rid))
-            h.release(rid)
+            ms_total = e0.elapsed_time(e1)
+        else:
+            # field smaller than L2: overwrite L2 before every step, outside
+            # the timed spans
+            ms_total = 0.0
+            for _ in range(args.steps):
+                flush.add_(1)
+                e0.record(stream)
+                rid, g = step()
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                ms_total += e0.elapsed_time(e1)
+                step_ms.append(h.step_times(rid))
+                h.release(rid)
     if dist is not None:
         dist.barrier()
     launches = h.launch_count() - launches0
@@ -688,10 +702,11 @@ def main():
         torch.cuda.synchronize(dev)
         if dist is not None:
             dist.barrier()
-        t0 = time.perf_counter()
-        e2e_run(args.steps)
-        torch.cuda.synchronize(dev)
-        e2e_s = time.perf_counter() - t0
+        with quiet_gc():
+            t0 = time.perf_counter()
+            e2e_run(args.steps)
+            torch.cuda.synchronize(dev)
+            e2e_s = time.perf_counter() - t0
         for hx in hs[1:]:
             hx.close()
         if dist is not None:
