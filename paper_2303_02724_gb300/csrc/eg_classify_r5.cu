@@ -26,6 +26,8 @@
 //           (PatternLink<5> closure); a saddle when it is not the whole link,
 //           and then every other component and its highest slot, from values
 //           reloaded through the cache (saddles are rare).
+#include <type_traits>
+
 #include "eg_internal.cuh"
 #include "eg_kernels.h"
 
@@ -94,8 +96,10 @@ __global__ void __launch_bounds__(kR5Threads) k_classify_r5(const FieldDev *__re
 
         // row q's value at column x, and at column x - 1 (negative rows) or
         // x + 1 (positive rows)
-        auto row = [&](int q, bool neg, float &vx, float &vside) {
-            const bool ok = rowok && (neg ? (lo & uint32_t(q)) == uint32_t(q) : (hi & uint32_t(q)) == uint32_t(q));
+        auto row = [&](auto inner, int q, bool neg, float &vx, float &vside) {
+            const bool ok = decltype(inner)::value ? true
+                                                   : rowok && (neg ? (lo & uint32_t(q)) == uint32_t(q)
+                                                                   : (hi & uint32_t(q)) == uint32_t(q));
             const uint32_t o = r5_row_off(q, s1, s2, s3, s4);
             const uint32_t rb = neg ? v - o : v + o;
             vx = (ok && chk(rb, F.N, F.err)) ? __ldg(F.f + rb) : qnan;
@@ -133,29 +137,34 @@ __global__ void __launch_bounds__(kR5Threads) k_classify_r5(const FieldDev *__re
             best = MIN ? fminf(best, nb) : fmaxf(best, nb);
             bestk = t ? k : bestk;
         };
-        // negative rows q = 15 .. 1: slots 30 - 2q (pattern 2q + 1, column x - 1)
-        // and 31 - 2q (pattern 2q, column x)
-    #pragma unroll
-        for (int q = 15; q >= 1; q--) {
-            float vx, vl;
-            row(q, true, vx, vl);
-            consider(30 - 2 * q, vl);
-            consider(31 - 2 * q, vx);
-        }
-        {
+        auto scan = [&](auto inner) {
+            // negative rows q = 15 .. 1: slots 30 - 2q (pattern 2q + 1, column x - 1)
+            // and 31 - 2q (pattern 2q, column x)
+#pragma unroll
+            for (int q = 15; q >= 1; q--) {
+                float vx, vl;
+                row(inner, q, true, vx, vl);
+                consider(30 - 2 * q, vl);
+                consider(31 - 2 * q, vx);
+            }
             // centre row: slot 30 (pattern 1, column x - 1) and 31 (column x + 1)
             consider(30, (rowok && left_ok && chk(v - 1, F.N, F.err)) ? __ldg(F.f + v - 1) : qnan);
             consider(31, (rowok && right_ok && chk(v + 1, F.N, F.err)) ? __ldg(F.f + v + 1) : qnan);
-        }
-        // positive rows q = 1 .. 15: slots 30 + 2q (pattern 2q, column x) and
-        // 31 + 2q (pattern 2q + 1, column x + 1)
-    #pragma unroll
-        for (int q = 1; q <= 15; q++) {
-            float vx, vr;
-            row(q, false, vx, vr);
-            consider(30 + 2 * q, vx);
-            consider(31 + 2 * q, vr);
-        }
+            // positive rows q = 1 .. 15: slots 30 + 2q (pattern 2q, column x) and
+            // 31 + 2q (pattern 2q + 1, column x + 1)
+#pragma unroll
+            for (int q = 1; q <= 15; q++) {
+                float vx, vr;
+                row(inner, q, false, vx, vr);
+                consider(30 + 2 * q, vx);
+                consider(31 + 2 * q, vr);
+            }
+        };
+        // a vertex with room along axes 1..4 on both sides (most of them; the
+        // whole warp agrees, as it lies in one row) takes a copy of the scan
+        // without the rows' domain tests
+        if (rowok && lo == 15u && hi == 15u) scan(std::true_type{});
+        else scan(std::false_type{});
         const uint32_t up_pos = (__float_as_uint(aP0) & 0xffffu) | ((__float_as_uint(aP1) & 0xffffu) << 16);
         const uint32_t up_neg = (__float_as_uint(aN0) & 0xffffu) | ((__float_as_uint(aN1) & 0xffffu) << 16);
         const uint64_t U = uint64_t(up_pos) | (uint64_t(up_neg) << 32);
