@@ -25,6 +25,8 @@
 //           flood over the link edges); a saddle when it is not the whole
 //           mask, and then every other component and its highest vertex.
 // The minimum graph mirrors every comparison and tie rule.
+#include <type_traits>
+
 #include "eg_internal.cuh"
 #include "eg_kernels.h"
 
@@ -157,16 +159,18 @@ k_classify_r4(const FieldDev *__restrict__ fields, int nf)
 
     // columns x .. x+3 of the row at offset `off` (sign sg) from this thread's
     // row, NaN outside the domain
-    auto seg = [&](uint32_t q, bool neg, float *v) {
+    auto seg = [&](auto inner, uint32_t q, bool neg, float *v) {
         const uint32_t dy = q & 1u, dz = (q >> 1) & 1u, dw = (q >> 2) & 1u;
         bool ok = rowok;
-        if (neg) ok = ok && y >= dy && z >= dz && w >= dw;
-        else ok = ok && y + dy < n1 && z + dz < n2 && w + dw < n3;
+        if (!decltype(inner)::value) {
+            if (neg) ok = ok && y >= dy && z >= dz && w >= dw;
+            else ok = ok && y + dy < n1 && z + dz < n2 && w + dw < n3;
+        }
         const uint32_t off = dy * s1 + dz * s2 + dw * s3;
         const uint32_t rb = neg ? vrow - off : vrow + off;  // (only used when ok)
         if (ok && !(chk(uint64_t(rb) + x, F.N, F.err) && chk(uint64_t(rb) + min(x + kR4Vx, n0) - 1, F.N, F.err)))
             ok = false;
-        if (ok && vec && x + 3 < n0) {
+        if (decltype(inner)::value || (ok && vec && x + 3 < n0)) {
             const float4 q4 = __ldg(reinterpret_cast<const float4 *>(F.f + rb + x));
             v[0] = q4.x;
             v[1] = q4.y;
@@ -192,18 +196,27 @@ k_classify_r4(const FieldDev *__restrict__ fields, int nf)
     // C: centre row, columns x-1 .. x+4 (index j+1 for column x+j)
     // Nr[q]: negative row q, columns x-1 .. x+3; Pr[q]: positive row q, x .. x+4
     float C[kR4Vx + 2], Nr[7][kR4Vx + 1], Pr[7][kR4Vx + 1];
-    {
-        const uint32_t rb = seg(0, false, &C[1]);
-        C[0] = left(rb, &C[1]);
-        C[kR4Vx + 1] = right(rb, &C[1]);
-    }
+    auto loads = [&](auto inner) {
+        {
+            const uint32_t rb = seg(inner, 0, false, &C[1]);
+            C[0] = left(rb, &C[1]);
+            C[kR4Vx + 1] = right(rb, &C[1]);
+        }
 #pragma unroll
-    for (int q = 1; q < 8; q++) {
-        const uint32_t rn = seg(uint32_t(q), true, &Nr[q - 1][1]);
-        Nr[q - 1][0] = left(rn, &Nr[q - 1][1]);
-        const uint32_t rp = seg(uint32_t(q), false, &Pr[q - 1][0]);
-        Pr[q - 1][kR4Vx] = right(rp, &Pr[q - 1][0]);
-    }
+        for (int q = 1; q < 8; q++) {
+            const uint32_t rn = seg(inner, uint32_t(q), true, &Nr[q - 1][1]);
+            Nr[q - 1][0] = left(rn, &Nr[q - 1][1]);
+            const uint32_t rp = seg(inner, uint32_t(q), false, &Pr[q - 1][0]);
+            Pr[q - 1][kR4Vx] = right(rp, &Pr[q - 1][0]);
+        }
+    };
+    // a thread with room on both sides along axes 1..3 and 16-byte rows
+    // (most threads; a warp agrees whenever it lies in one row) loads through
+    // a copy without the rows' domain tests
+    if (rowok && vec && y >= 1 && y + 1 < n1 && z >= 1 && z + 1 < n2 && w >= 1 && w + 1 < n3)
+        loads(std::true_type{});
+    else
+        loads(std::false_type{});
     __syncthreads();  // s_cnt
 
     // the 30 neighbour values of vertex i in slot order (slot k: k < 15
