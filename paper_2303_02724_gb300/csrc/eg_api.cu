@@ -191,6 +191,7 @@ struct Launch {
     void *hsmall_pin = nullptr;       // page-locked copy, written by the launch's last step
     cudaEvent_t done = nullptr;       // recorded after the launch's last step
     cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // step timing (optional)
+    bool fused = false;               // one fused kernel: only ev[0] and ev[1] are recorded
     struct eg_ctx *owner = nullptr;   // the handle whose event pool the events return to
     ~Launch();
 };
@@ -214,6 +215,12 @@ struct eg_ctx {
     void *ws_scan = nullptr;
     uint64_t ws_tiles = 0;
     void *lut3 = nullptr;  // saddle class table of the 3D link graph + two-component table
+    // the fused small-field kernel's totals, status and barrier words: two
+    // blocks used in turn; launch k works in block k % 2 and zeroes the
+    // status and barrier count of the other for launch k + 1 (the launches
+    // of a handle are ordered on the GPU by ws_free, so no memset is needed)
+    void *fused_pair = nullptr;
+    uint64_t fused_seq = 0;
     void *stage = nullptr;  // device staging for eg_compute_host
     size_t stage_bytes = 0;
     void *hstage = nullptr;  // pinned staging for pageable host fields
@@ -895,8 +902,8 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
     // the workspace is free once earlier computations' last kernels finished
     if ((e = cudaStreamWaitEvent(st, h->ws_free, 0)) != cudaSuccess) return fail(from_cuda(e));
     if (h->timing) {
-        for (auto &ev : L->ev)
-            if ((e = get_event(h, &ev, true)) != cudaSuccess) return fail(from_cuda(e));
+        for (int q = 0; q < (fused ? 2 : 5); q++)
+            if ((e = get_event(h, &L->ev[q], true)) != cudaSuccess) return fail(from_cuda(e));
         cudaEventRecord(L->ev[0], st);
     }
     // steps (a)+(c) and the node counts (the fused path runs every step
@@ -998,23 +1005,36 @@ eg_status run_jobs(eg_ctx *h, const std::vector<Job> &jobs, cudaStream_t st, std
     // phase 0 has finished (we waited for it), so the host table may change;
     // phase 2 uploads it again, ordered after resolution on the stream
     if (fused) {
-        // counts, status and barrier words zeroed, then every step;
-        // the step timing reports the whole kernel as classification
-        unsigned *bar = static_cast<SmallBlock *>(L->smalls)->bar;
-        if ((e = cudaMemsetAsync(L->smalls, 0, sizeof(SmallBlock), st)) != cudaSuccess) return fail(from_cuda(e));
-        if ((e = launch_small(Dh[0], bar, h->sm_count, st)) != cudaSuccess) return fail(from_cuda(e));
+        // every step in one launch, in the handle's current fused block
+        // (status and barrier count zeroed by the launch before); the kernel
+        // writes the counts and the status into the page-locked block itself
+        // (which reads as a timeout until it does); the step timing reports
+        // the whole kernel as classification, with one event after it
+        SmallBlock *pair = static_cast<SmallBlock *>(h->fused_pair);
+        SmallBlock *cur = pair + (h->fused_seq & 1u), *nxt = pair + ((h->fused_seq + 1u) & 1u);
+        FieldDev &F = Dh[0];
+        F.totals = cur->totals;
+        F.err = &cur->err;
+        SmallBlock *hb = static_cast<SmallBlock *>(L->hsmall_pin);
+        std::memset(hb, 0, sizeof(SmallBlock));
+        hb->err = kErrTimeout;
+        if ((e = launch_small(F, cur->bar, &nxt->err, nxt->bar, hb->totals, &hb->err, h->sm_count, st)) !=
+            cudaSuccess)
+            return fail(from_cuda(e));
+        h->fused_seq++;
         h->launches += 1;
-        if (h->timing)
-            for (int q = 1; q < 5; q++) cudaEventRecord(L->ev[q], st);
+        L->fused = true;
+        if (h->timing) cudaEventRecord(L->ev[1], st);
     } else {
         if (h->timing) cudaEventRecord(L->ev[3], st);
         if ((es = run_part(2)) != EG_OK) return fail(es);
         if (h->timing) cudaEventRecord(L->ev[4], st);
     }
     cudaEventRecord(h->ws_free, st);
-    // every result's counts and status word, read by collect() once `done` fired
-    if ((e = cudaMemcpyAsync(L->hsmall_pin, L->smalls, sizeof(SmallBlock) * size_t(nf), cudaMemcpyDeviceToHost,
-                             st)) != cudaSuccess)
+    // every result's counts and status word, read by collect() once `done`
+    // fired (the fused kernel wrote them already)
+    if (!fused && (e = cudaMemcpyAsync(L->hsmall_pin, L->smalls, sizeof(SmallBlock) * size_t(nf),
+                                       cudaMemcpyDeviceToHost, st)) != cudaSuccess)
         return fail(from_cuda(e));
     ids.resize(nf);
     if ((e = get_event(h, &L->done, false)) != cudaSuccess) return fail(from_cuda(e));
@@ -1145,6 +1165,8 @@ eg_status eg_create(eg_handle *out, int device, const eg_config *cfg)
         if ((e = cudaMemcpy(h->lut3, lut.data(), lut.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
             return from_cuda(e);
     }
+    if ((e = h->pool.alloc(&h->fused_pair, 2 * sizeof(SmallBlock))) != cudaSuccess) return from_cuda(e);
+    if ((e = cudaMemset(h->fused_pair, 0, 2 * sizeof(SmallBlock))) != cudaSuccess) return from_cuda(e);
     *out = h.release();
     return EG_OK;
 }
@@ -1323,18 +1345,32 @@ eg_status eg_batch_submit(eg_handle h, const eg_field_desc *fields, int n, void 
 
 namespace {
 
+// ev: start | classify | resolve | (count read-back, buffer set-up) | emit;
+// a fused launch records start | whole kernel, reported as classification.
+eg_status event_times(const Launch &L, float ms[4])
+{
+    const cudaEvent_t last = L.fused ? L.ev[1] : L.ev[4];
+    cudaError_t e = cudaEventSynchronize(last);
+    if (e != cudaSuccess) return from_cuda(e);
+    float a = 0, b = 0, c = 0, t = 0;
+    cudaEventElapsedTime(&a, L.ev[0], L.ev[1]);
+    if (!L.fused) {
+        cudaEventElapsedTime(&b, L.ev[1], L.ev[2]);
+        cudaEventElapsedTime(&c, L.ev[3], L.ev[4]);
+    }
+    cudaEventElapsedTime(&t, L.ev[0], last);
+    ms[0] = a;
+    ms[1] = b;
+    ms[2] = c;
+    ms[3] = t;
+    return EG_OK;
+}
+
 // Device milliseconds of the steps of one launch (timing must have been on).
 eg_status launch_times(const Launch &L, float ms[4])
 {
     if (!L.ev[0]) return EG_ERR_ARG;
-    cudaError_t e = cudaEventSynchronize(L.ev[4]);
-    if (e != cudaSuccess) return from_cuda(e);
-    // ev: start | classify | resolve | (count read-back, buffer set-up) | emit
-    cudaEventElapsedTime(&ms[0], L.ev[0], L.ev[1]);
-    cudaEventElapsedTime(&ms[1], L.ev[1], L.ev[2]);
-    cudaEventElapsedTime(&ms[2], L.ev[3], L.ev[4]);
-    cudaEventElapsedTime(&ms[3], L.ev[0], L.ev[4]);
-    return EG_OK;
+    return event_times(L, ms);
 }
 
 // One timed run of the whole pipeline on `jobs` with configuration c; the
@@ -1697,20 +1733,7 @@ eg_status eg_step_times(eg_handle h, eg_result_id id, float ms[4])
     cudaSetDevice(h->device);
     auto it = h->results.find(id);
     if (it == h->results.end() || !it->second->launch || !it->second->launch->ev[0]) return EG_ERR_ARG;
-    Launch &L = *it->second->launch;
-    cudaError_t e = cudaEventSynchronize(L.ev[4]);
-    if (e != cudaSuccess) return from_cuda(e);
-    // ev: start | classify | resolve | (count read-back, buffer set-up) | emit
-    float a = 0, b = 0, c = 0, t = 0;
-    cudaEventElapsedTime(&a, L.ev[0], L.ev[1]);
-    cudaEventElapsedTime(&b, L.ev[1], L.ev[2]);
-    cudaEventElapsedTime(&c, L.ev[3], L.ev[4]);
-    cudaEventElapsedTime(&t, L.ev[0], L.ev[4]);
-    ms[0] = a;
-    ms[1] = b;
-    ms[2] = c;
-    ms[3] = t;
-    return EG_OK;
+    return event_times(*it->second->launch, ms);
 }
 
 uint64_t eg_launch_count(eg_handle h) { return h ? h->launches.load() : 0; }

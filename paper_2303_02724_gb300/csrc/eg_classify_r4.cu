@@ -133,13 +133,12 @@ __global__ void __launch_bounds__(kR4Threads, 3)
 k_classify_r4(const FieldDev *__restrict__ fields, int nf)
 {
     __shared__ uint32_t s_scan[33];
-    __shared__ unsigned s_cnt[3];
+    __shared__ uint4 s_warp[kR4Threads / 32];  // per-warp counts of maxima, saddles, arc ends
     const uint64_t g = fields[0].brick0 + blockIdx.x;
     const int fi = find_field<false>(fields, nf, g);
     const FieldDev &F = fields[fi];
     const uint32_t b = uint32_t(g - F.brick0);
     const int tid = threadIdx.x, lane = tid & 31;
-    if (tid < 3) s_cnt[tid] = 0;
 
     const uint32_t n0 = F.n[0], n1 = F.n[1], n2 = F.n[2], n3 = F.n[3];
     const uint32_t p = b / F.nyb, yb = b - p * F.nyb;
@@ -217,7 +216,6 @@ k_classify_r4(const FieldDev *__restrict__ fields, int nf)
         loads(std::true_type{});
     else
         loads(std::false_type{});
-    __syncthreads();  // s_cnt
 
     // the 30 neighbour values of vertex i in slot order (slot k: k < 15
     // negative with pattern 15 - k, k >= 15 positive with pattern k - 14)
@@ -361,6 +359,11 @@ k_classify_r4(const FieldDev *__restrict__ fields, int nf)
                 if (x + i < n0) dst[i] = asc[i];
         }
     }
+    // the brick's counts per warp (published by the scan's barriers)
+    nm = __reduce_add_sync(0xffffffffu, nm);
+    ns = __reduce_add_sync(0xffffffffu, ns);
+    np = __reduce_add_sync(0xffffffffu, np);
+    if (lane == 0) s_warp[tid >> 5] = make_uint4(nm, ns, np, 0u);
     // records of the brick in index order: threads are in (row, x) order
     uint32_t tot;
     const uint32_t pos0 = block_excl_scan(uint32_t(__popc(crit)), s_scan, &tot);
@@ -376,16 +379,17 @@ k_classify_r4(const FieldDev *__restrict__ fields, int nf)
             F.rec_val[qd] = C[i + 1];
         }
     if (anynan) atomicOr(F.err, kErrNaN);
-    nm = __reduce_add_sync(0xffffffffu, nm);
-    ns = __reduce_add_sync(0xffffffffu, ns);
-    np = __reduce_add_sync(0xffffffffu, np);
-    if (lane == 0) {
-        if (nm) atomicAdd(&s_cnt[0], nm);
-        if (ns) atomicAdd(&s_cnt[1], ns);
-        if (np) atomicAdd(&s_cnt[2], np);
+    if (tid == 0 && chk(b, F.nbricks, F.err)) {
+        uint4 c = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int w = 0; w < kR4Threads / 32; w++) {
+            const uint4 q = s_warp[w];
+            c.x += q.x;
+            c.y += q.y;
+            c.z += q.z;
+        }
+        F.bcnt[b] = c;
     }
-    __syncthreads();
-    if (tid == 0 && chk(b, F.nbricks, F.err)) F.bcnt[b] = make_uint4(s_cnt[0], s_cnt[1], s_cnt[2], 0u);
 }
 
 cudaError_t launch_classify_r4(bool minimum, const FieldDev *fields, int nf, uint64_t bricks, cudaStream_t st)

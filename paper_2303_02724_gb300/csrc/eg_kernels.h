@@ -126,11 +126,17 @@ struct CancelDev {
 };
 // Fused path for one small 1D-3D float32 field: every step in one
 // cooperative launch over a flat layout of small_bricks(N) bricks of 256
-// vertices (bcap 256, at most 256 bricks); bar: two zeroed words.
+// vertices (bcap 256, at most 256 bricks); bar: the barrier's count (zero)
+// and generation words; next_err, next_count: the status word and barrier
+// count of the next launch's block, zeroed by this one; htotals[4] and herr:
+// page-locked host memory (device-accessible under unified addressing) that
+// receives F's totals and status word when the launch finishes, and is left
+// as it was if a barrier timed out.  F.err must be zero at the start.
 constexpr uint64_t kSmallMaxVertices = 1u << 16;
 constexpr uint32_t kSmallBrick = 256;
 uint32_t small_bricks(uint64_t n);
-cudaError_t launch_small(const FieldDev &F, unsigned *bar, int sm_count, cudaStream_t st);
+cudaError_t launch_small(const FieldDev &F, unsigned *bar, uint32_t *next_err, unsigned *next_count,
+                         unsigned long long *htotals, uint32_t *herr, int sm_count, cudaStream_t st);
 
 // Set-up (every saddle waits, in list[0], ctrl zeroed but slot 0's key, which
 // is all ones); all rounds in one cooperative launch; the results.

@@ -14,9 +14,13 @@
 //      the gradient pointers (concurrent walks read either a pointer or a
 //      finished label on the same path, so the races are benign);
 //   3. nodes and arc ends, one warp per brick;
-//   4. arc offsets and the total A (one CTA);
-//   5. CSR, one warp per brick.
-// Every barrier wait is bounded (kErrTimeout after about a second).
+//   4. CSR, one warp per brick, each adding up the arc counts of the bricks
+//      before its own (its arc offset) and of all bricks (the total A);
+// then the last CTA to finish copies the totals and the status word to the
+// caller's page-locked host block, so no copy follows the kernel.
+// Every barrier wait is bounded (kErrTimeout after about a second); a CTA
+// that gave up at a barrier never arrives at the end, and the host block
+// keeps the timeout status the caller put there.
 #include <atomic>
 
 #include "eg_emit.cuh"
@@ -28,7 +32,9 @@ namespace eg {
 
 constexpr int kSmallThreads = int(kSmallBrick);  // one vertex per thread, a brick per CTA
 
-__global__ void __launch_bounds__(kSmallThreads) k_small(const FieldDev F, unsigned *bar)
+__global__ void __launch_bounds__(kSmallThreads)
+    k_small(const FieldDev F, unsigned *bar, uint32_t *next_err, unsigned *next_count, unsigned long long *htotals,
+            uint32_t *herr)
 {
     __shared__ uint32_t s_scan[33];
     __shared__ unsigned s_cnt[3];
@@ -38,6 +44,12 @@ __global__ void __launch_bounds__(kSmallThreads) k_small(const FieldDev F, unsig
 #pragma unroll
     for (int i = 0; i < kMaxDim; i++) s[i] = F.s[i];
     const bool minimum = (F.flags & kFlagMinimum) != 0;
+    // the next launch's status word and barrier count (no other launch of
+    // this caller runs before this one ends)
+    if (blockIdx.x == 0 && tid == 0) {
+        *next_err = 0u;
+        *next_count = 0u;
+    }
 
     // 1: classification and the brick's records in index order
     for (uint32_t b = blockIdx.x; b < nb; b += gridDim.x) {
@@ -112,23 +124,45 @@ __global__ void __launch_bounds__(kSmallThreads) k_small(const FieldDev F, unsig
     for (uint32_t b = blockIdx.x * kWarps + uint32_t(warp); b < nb; b += gridDim.x * kWarps) nodes_brick<3>(F, b);
     if (!grid_barrier(bar, bar + 1, F.err)) return;
 
-    // 4: arc offsets
-    if (blockIdx.x == 0) {
-        const uint32_t a = uint32_t(tid) < nb ? F.acnt[tid] : 0u;
-        uint32_t ta;
-        const uint32_t oa = block_excl_scan(a, s_scan, &ta);
-        if (uint32_t(tid) < nb) F.aoff[tid] = oa;
-        if (tid == 0) F.totals[3] = ta;
+    // 4: each warp adds up the arc counts before its brick and in all (at
+    // most 256 bricks), then writes its brick's CSR (every warp writes the
+    // same total A)
+    for (uint32_t b = blockIdx.x * kWarps + uint32_t(warp); b < nb; b += gridDim.x * kWarps) {
+        uint32_t pre = 0, all = 0;
+        for (uint32_t i = uint32_t(lane); i < nb; i += 32) {
+            const uint32_t a = F.acnt[i];
+            all += a;
+            pre += i < b ? a : 0u;
+        }
+        pre = __reduce_add_sync(0xffffffffu, pre);
+        all = __reduce_add_sync(0xffffffffu, all);
+        if (lane == 0) {
+            F.aoff[b] = pre;
+            F.totals[3] = all;
+        }
+        __syncwarp();
+        csr_brick(F, b);
     }
-    if (!grid_barrier(bar, bar + 1, F.err)) return;
 
-    // 5: CSR
-    for (uint32_t b = blockIdx.x * kWarps + uint32_t(warp); b < nb; b += gridDim.x * kWarps) csr_brick(F, b);
+    // arrival at the end (the barrier's count is zero again after the last
+    // barrier); the last CTA sees every other CTA's writes
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            __threadfence();
+#pragma unroll
+            for (int q = 0; q < 4; q++) htotals[q] = *reinterpret_cast<volatile unsigned long long *>(F.totals + q);
+            *herr = *reinterpret_cast<volatile uint32_t *>(F.err);
+            __threadfence_system();
+        }
+    }
 }
 
 uint32_t small_bricks(uint64_t n) { return uint32_t((n + kSmallThreads - 1) / kSmallThreads); }
 
-cudaError_t launch_small(const FieldDev &F, unsigned *bar, int sm_count, cudaStream_t st)
+cudaError_t launch_small(const FieldDev &F, unsigned *bar, uint32_t *next_err, unsigned *next_count,
+                         unsigned long long *htotals, uint32_t *herr, int sm_count, cudaStream_t st)
 {
     if (F.nbricks == 0 || F.nbricks > uint32_t(kSmallThreads) || F.bcap != uint32_t(kSmallThreads))
         return cudaErrorInvalidValue;
@@ -144,7 +178,7 @@ cudaError_t launch_small(const FieldDev &F, unsigned *bar, int sm_count, cudaStr
     uint64_t grid = uint64_t(sm_count > 0 ? sm_count : 1) * uint64_t(per_sm);
     if (grid > F.nbricks) grid = F.nbricks;
     FieldDev arg = F;
-    void *args[] = {&arg, &bar};
+    void *args[] = {&arg, &bar, &next_err, &next_count, &htotals, &herr};
     return cudaLaunchCooperativeKernel(reinterpret_cast<void *>(k_small), dim3(unsigned(grid)), dim3(kSmallThreads),
                                        args, 0, st);
 }
