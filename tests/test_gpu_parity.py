@@ -253,6 +253,30 @@ def test_bounded_result_reports_nan_when_read(handle):
     assert_same(run_gpu(handle, f.values), oracle.compute(f.values))
 
 
+def test_fused_status_blocks_in_turn(handle):
+    """Fused launches take the handle's two status blocks in turn, each
+    zeroing the other's for the next launch: a NaN field's status reaches
+    neither the fields after it nor the next use of its block, with every
+    launch enqueued (on two streams) before any result is read."""
+    from paper_2303_02724_gb300 import eg
+    clean = [F.white_noise((37, 29), 40 + s).values for s in range(4)]
+    bad = clean[0].copy()
+    bad[5, 6] = np.nan
+    seq = [bad, clean[0], clean[1], bad, bad, clean[2], clean[3], bad, clean[1]]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    ts = [torch.from_numpy(v).cuda() for v in seq]
+    torch.cuda.synchronize()
+    rids = [handle.compute(t, streams[i % 2]) for i, t in enumerate(ts)]
+    for v, rid in zip(seq, rids):
+        if np.isnan(v).any():
+            with pytest.raises(eg.EGError) as ei:
+                handle.get_graph(rid)
+            assert ei.value.status == eg.EG_ERR_NAN
+        else:
+            assert_same(handle.get_graph(rid), oracle.compute(v))
+        handle.release(rid)
+
+
 def test_pinned_buffers_reused(handle):
     from paper_2303_02724_gb300 import eg
     buf = eg.GraphBuffers(4096, 8192, 16384, 24 * 24 * 24, pinned=True)
