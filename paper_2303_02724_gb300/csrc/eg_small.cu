@@ -119,15 +119,18 @@ __global__ void __launch_bounds__(kSmallThreads)
     }
     if (!grid_barrier(bar, bar + 1, F.err)) return;
 
-    // 3: nodes and arc ends
+    // 3: nodes and arc ends; a brick per warp, the bricks dealt to the CTAs
+    // first (warp w of CTA c takes bricks c + w G, c + (w + 8) G, ... for a
+    // grid of G CTAs), so the latency-bound warps spread over every SM
     constexpr uint32_t kWarps = kSmallThreads / 32;
-    for (uint32_t b = blockIdx.x * kWarps + uint32_t(warp); b < nb; b += gridDim.x * kWarps) nodes_brick<3>(F, b);
+    const uint32_t b_first = blockIdx.x + gridDim.x * uint32_t(warp), b_step = gridDim.x * kWarps;
+    for (uint32_t b = b_first; b < nb; b += b_step) nodes_brick<3>(F, b);
     if (!grid_barrier(bar, bar + 1, F.err)) return;
 
     // 4: each warp adds up the arc counts before its brick and in all (at
     // most 256 bricks), then writes its brick's CSR (every warp writes the
     // same total A)
-    for (uint32_t b = blockIdx.x * kWarps + uint32_t(warp); b < nb; b += gridDim.x * kWarps) {
+    for (uint32_t b = b_first; b < nb; b += b_step) {
         uint32_t pre = 0, all = 0;
         for (uint32_t i = uint32_t(lane); i < nb; i += 32) {
             const uint32_t a = F.acnt[i];
