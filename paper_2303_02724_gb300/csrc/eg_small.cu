@@ -32,6 +32,39 @@ namespace eg {
 
 constexpr int kSmallThreads = int(kSmallBrick);  // one vertex per thread, a brick per CTA
 
+// Grid barrier over a count that only grows during the launch (zero at its
+// start): barrier k (k = 1, 2, ...) lets the CTAs go once the count reaches k
+// times the grid size, so the last arrival's increment releases the others
+// without a reset or a second word.  Thread 0 waits for at most about a
+// second, then sets kErrTimeout and the CTA leaves.
+__device__ __forceinline__ bool count_barrier(unsigned *count, unsigned k, uint32_t *err)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned target = k * gridDim.x;
+        __threadfence();
+        if (atomicAdd(count, 1u) + 1u < target) {
+            unsigned ns = 32;
+            uint32_t spins = 0;
+            while (*reinterpret_cast<volatile unsigned *>(count) < target) {
+                if (++spins > kSpinLimit) {
+                    atomicOr(err, kErrTimeout);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(ns);
+                ns = ns < 256 ? ns * 2 : 256;
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
 __global__ void __launch_bounds__(kSmallThreads)
     k_small(const FieldDev F, unsigned *bar, uint32_t *next_err, unsigned *next_count, unsigned long long *htotals,
             uint32_t *herr)
@@ -83,7 +116,7 @@ __global__ void __launch_bounds__(kSmallThreads)
         if (tid == 0 && chk(b, nb, F.err)) F.bcnt[b] = make_uint4(s_cnt[0], s_cnt[1], s_cnt[2], 0u);
         __syncthreads();  // s_cnt is cleared again by the next brick
     }
-    if (!grid_barrier(bar, bar + 1, F.err)) return;
+    if (!count_barrier(bar, 1u, F.err)) return;
 
     // 2: brick offsets (CTA 0: one thread per brick), labels (every thread)
     if (blockIdx.x == 0) {
@@ -117,7 +150,7 @@ __global__ void __launch_bounds__(kSmallThreads)
         }
         if (moved) F.lab[v] = u;
     }
-    if (!grid_barrier(bar, bar + 1, F.err)) return;
+    if (!count_barrier(bar, 2u, F.err)) return;
 
     // 3: nodes and arc ends; a brick per warp, the bricks dealt to the CTAs
     // first (warp w of CTA c takes bricks c + w G, c + (w + 8) G, ... for a
@@ -125,7 +158,7 @@ __global__ void __launch_bounds__(kSmallThreads)
     constexpr uint32_t kWarps = kSmallThreads / 32;
     const uint32_t b_first = blockIdx.x + gridDim.x * uint32_t(warp), b_step = gridDim.x * kWarps;
     for (uint32_t b = b_first; b < nb; b += b_step) nodes_brick<3>(F, b);
-    if (!grid_barrier(bar, bar + 1, F.err)) return;
+    if (!count_barrier(bar, 3u, F.err)) return;
 
     // 4: each warp adds up the arc counts before its brick and in all (at
     // most 256 bricks), then writes its brick's CSR (every warp writes the
@@ -147,12 +180,12 @@ __global__ void __launch_bounds__(kSmallThreads)
         csr_brick(F, b);
     }
 
-    // arrival at the end (the barrier's count is zero again after the last
-    // barrier); the last CTA sees every other CTA's writes
+    // arrival at the end (after three barriers the count is 3 G); the last
+    // CTA sees every other CTA's writes
     __syncthreads();
     if (tid == 0) {
         __threadfence();
-        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+        if (atomicAdd(bar, 1u) == 4u * gridDim.x - 1u) {
             __threadfence();
 #pragma unroll
             for (int q = 0; q < 4; q++) htotals[q] = *reinterpret_cast<volatile unsigned long long *>(F.totals + q);
