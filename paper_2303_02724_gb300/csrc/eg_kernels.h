@@ -127,8 +127,9 @@ struct CancelDev {
 // Fused path for one small 1D-3D float32 field: every step in one
 // cooperative launch over a flat layout of small_bricks(N) bricks of 256
 // vertices (bcap 256, at most 256 bricks); bar: the barrier's count, zero at
-// the start (the launch leaves it at 4 times the grid size); next_err, next_count: the status word and barrier
-// count of the next launch's block, zeroed by this one; htotals[4] and herr:
+// the start (the launch leaves it at 4 times the grid size); next_err,
+// next_count: the status word and barrier count of the next launch's block,
+// zeroed by this one; htotals[4] and herr:
 // page-locked host memory (device-accessible under unified addressing) that
 // receives F's totals and status word when the launch finishes, and is left
 // as it was if a barrier timed out.  F.err must be zero at the start.
