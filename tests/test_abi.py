@@ -110,6 +110,41 @@ def test_bench_byte_accounting():
     assert bench.path_bytes(c, es=1) == 1000 + 4 * 1000 + 5 * 10 + 6 * 20 + 8 * 21 + 4 * 40
 
 
+def _bench(args, env_extra=None):
+    import sys
+    env = dict(os.environ)
+    env.update(env_extra or {})
+    return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + args, capture_output=True, text=True,
+                          timeout=300, cwd=ROOT, env=env)
+
+
+def test_bench_reference_arm_line():
+    """The reference arm times the oracle on the host cores and prints one
+    JSON line with the contract's keys (no GPU needed)."""
+    import json
+    r = _bench(["--impl", "reference", "--workload", "gauss2d256", "--steps", "1", "--warmup", "0",
+                "--ref-sample-vertices", "65536"])
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["unit"] == "Mvertices/s" and line["higher_is_better"] is True
+    assert line["warmup"] >= 3 and line["steps"] == 1 and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "Mvertices/s", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert "65536 vertices" in line["config"]["sample"]
+
+
+def test_bench_reference_arm_other_ranks_are_silent():
+    """Under a multi-rank launch only rank 0 runs the reference arm; the
+    other ranks exit 0 without work or output."""
+    r = _bench(["--impl", "reference", "--workload", "gauss2d256", "--steps", "1", "--warmup", "0",
+                "--ref-sample-vertices", "65536"], {"WORLD_SIZE": "2", "RANK": "1", "LOCAL_RANK": "1"})
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+
+
 def test_labels_static_checks_arguments_before_any_launch():
     """eg_labels_static's binding rejects a labels buffer of another size, a
     non-float32 field, a float labels buffer and strided views before it
