@@ -132,6 +132,40 @@ def test_4d_rows_over_1024(handle, handle_min, ext, kind):
     assert_same(run_gpu(handle_min, f.values), oracle.compute(f.values, minimum=True))
 
 
+@pytest.mark.parametrize("ext", [(8, 3, 3, 3), (12, 5, 4, 3), (64, 4, 3, 5), (1024, 3, 3, 3)],
+                         ids=lambda e: "x".join(map(str, e)))
+@pytest.mark.parametrize("kind", ["normal", "ties"])
+def test_4d_interior_rows(handle, handle_min, ext, kind):
+    """4D rows of 16-byte aligned length with room on both sides along axes
+    1..3 take the row classifier's copy without domain tests, the others the
+    checked one: both graphs against the oracle, also through an unaligned
+    field pointer (every row then takes the checked loads)."""
+    f = F.white_noise(ext, 5000 + sum(ext)) if kind == "normal" else F.integer_ties(ext, 5000 + sum(ext), 3)
+    assert f.values.shape[-1] == ext[0]
+    og, ogm = oracle.compute(f.values), oracle.compute(f.values, minimum=True)
+    assert_same(run_gpu(handle, f.values), og)
+    assert_same(run_gpu(handle_min, f.values), ogm)
+    flat = torch.from_numpy(np.concatenate([[0.0], f.values.reshape(-1)]).astype(np.float32)).cuda()
+    t = flat[1:].view(f.values.shape)
+    assert t.data_ptr() % 16 != 0
+    assert_same(handle.graph_of(t), og)
+
+
+@pytest.mark.parametrize("ext", [(3, 3, 3, 3, 3), (16, 3, 3, 3, 4), (255, 3, 3, 3, 3), (256, 3, 3, 3, 3),
+                                 (257, 3, 3, 3, 3)],
+                         ids=lambda e: "x".join(map(str, e)))
+@pytest.mark.parametrize("kind", ["normal", "ties"])
+def test_5d_rows_up_to_256(handle, handle_min, ext, kind):
+    """float32 5D fields: rows of at most 256 vertices take the 5D row
+    classifier (its copy without domain tests for rows with room on both
+    sides along axes 1..4), longer rows the flat classifier: both graphs,
+    against the oracle, on either side of that limit."""
+    f = F.white_noise(ext, 6000 + sum(ext)) if kind == "normal" else F.integer_ties(ext, 6000 + sum(ext), 3)
+    assert f.values.shape[-1] == ext[0]
+    assert_same(run_gpu(handle, f.values), oracle.compute(f.values))
+    assert_same(run_gpu(handle_min, f.values), oracle.compute(f.values, minimum=True))
+
+
 def test_unaligned_field_pointer(handle):
     f = F.config_3d_256(side=36)
     flat = torch.from_numpy(np.concatenate([[0.0], f.values.reshape(-1)]).astype(np.float32)).cuda()
