@@ -224,6 +224,39 @@ def test_axis_permutation_and_reflection(shape):
     assert np.array_equal(inv[g.label], gp.label[inv])
 
 
+@pytest.mark.parametrize("shape", [(9, 7), (6, 5, 4), (4, 3, 3, 3), (3, 3, 3, 2, 3)])
+@pytest.mark.parametrize("kind", ["white", "ties", "zeros_infs"])
+def test_minimum_graph_is_maximum_graph_of_negated_reflection(shape, kind):
+    """The minimum graph reverses the order (value, then index).  Negating
+    the field reverses the values, and reflecting every axis (v -> N-1-v)
+    reverses the index order while mapping the neighbourhood onto itself, so
+    the minimum graph of f is the maximum graph of -f on the reflected grid
+    with every id v read as N-1-v: with ties, signed zeros and infinities
+    too."""
+    rng = np.random.default_rng(sum(shape) * 7 + len(kind))
+    if kind == "white":
+        f = F.white_noise(shape, 31).values
+    elif kind == "ties":
+        f = F.integer_ties(shape, 32, 3).values
+    else:
+        pool = np.array([-np.inf, -1.0, -0.0, 0.0, 1.0, np.inf], np.float32)
+        f = pool[rng.integers(0, len(pool), size=shape)]
+    d = len(shape)
+    N = f.size
+    h = np.ascontiguousarray(-f[(slice(None, None, -1),) * d])
+    gmin = oracle.compute(f, minimum=True)
+    gh = oracle.compute(h)
+    back = lambda a: (N - 1 - np.asarray(a, np.int64)).astype(np.uint32)
+    assert np.array_equal(np.sort(back(gh.maxima)), gmin.maxima)
+    assert np.array_equal(np.sort(back(gh.saddles)), gmin.saddles)
+    assert np.array_equal(back(gh.label)[::-1], gmin.label)
+    assert np.array_equal(back(gh.asc)[::-1], gmin.asc)
+    assert np.array_equal(gh.beta0p[::-1], gmin.beta0p)
+    assert {(int(N - 1 - s), int(N - 1 - m)) for s, m in gh.arcs()} == gmin.arcs()
+    b0h = dict(zip(back(gh.saddles).tolist(), gh.sad_b0.tolist()))
+    assert [b0h[s] for s in gmin.saddles.tolist()] == gmin.sad_b0.tolist()
+
+
 def _interior_minima_2d(f):
     ny, nx = f.shape
     c = f[1:-1, 1:-1]
