@@ -310,7 +310,9 @@ EG_API eg_status eg_mem_info(eg_handle h, uint64_t *free_bytes, uint64_t *total_
  * result is complete, the device time in milliseconds of
  *   ms[0] classification (steps a+c), ms[1] path resolution (step b),
  *   ms[2] graph assembly (steps d+e), ms[3] the whole computation.
- * For a batch every field of the submission reports the batch's times.
+ * For a batch every field of the submission reports the batch's times.  A
+ * small field computed by the fused kernel (every step in one launch)
+ * reports that launch as ms[0] and ms[3], with ms[1] = ms[2] = 0.
  * Errors: EG_ERR_ARG (unknown id, or timing was off for that computation). */
 EG_API eg_status eg_set_timing(eg_handle h, int enable);
 EG_API eg_status eg_step_times(eg_handle h, eg_result_id id, float ms[4]);
