@@ -53,10 +53,47 @@ def _fingerprint(files=None) -> str:
     return h.hexdigest()
 
 
+def _code_text(text: str) -> str:
+    """C/C++/CUDA source without its comments and with runs of white space
+    folded to one blank: what the compiler sees of it."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c == '"' or c == "'":  # a literal, copied through (with escapes)
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            out.append(" ")
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
+def code_fingerprint_of(named_texts) -> str:
+    """SHA-256 over (basename, code text) pairs and the compiler flags."""
+    h = hashlib.sha256()
+    for name, text in named_texts:
+        h.update(name.encode())
+        h.update(_code_text(text).encode())
+    h.update(" ".join(ARCH + NVCC_FLAGS).encode())
+    return h.hexdigest()
+
+
 def kernel_fingerprint(source: str) -> str:
     """Fingerprint of one translation unit (basename under csrc/) and the
-    headers every unit includes: it changes when that kernel's code does."""
-    return _fingerprint([os.path.join(CSRC, source)] + _headers())
+    headers every unit includes, over their code without comments: it changes
+    when that kernel's code does, not when a comment does."""
+    files = [os.path.join(CSRC, source)] + _headers()
+    return code_fingerprint_of((os.path.basename(p), open(p, encoding="utf-8").read()) for p in files)
 
 
 LIB_CHECKED = os.path.join(HERE, "libeg_checked.so")

@@ -94,6 +94,21 @@ def test_element_type_codes():
         assert re.search(rf"EG_DTYPE_{names[dt.name]}\s*=\s*{code}\b", hdr), dt
 
 
+def test_kernel_fingerprint_ignores_comments_only():
+    """The profiles' traffic figures are tied to a kernel's code: comments
+    and layout do not change the fingerprint, code and string literals do."""
+    a = "int a = 1; // one\n/* block\n comment */ float f(float x) { return x * 2.f; }\n"
+    b = "int a = 1;\n\n   float f(float x)  {  return x * 2.f; }   // changed comment\n"
+    c = "int a = 2; float f(float x) { return x * 2.f; }\n"
+    d = 'const char *s = "// kept"; int a = 1;\n'
+    e = 'const char *s = "// kept!"; int a = 1;\n'
+    fp = lambda t: _build.code_fingerprint_of([("k.cu", t)])
+    assert fp(a) == fp(b)
+    assert fp(a) != fp(c)
+    assert fp(d) != fp(e)
+    assert _build._code_text(d) == 'const char *s = "// kept"; int a = 1;'
+
+
 def test_bench_byte_accounting():
     """The roofline's algorithmic bytes: the field in its element type, the
     labels, the records and the graph (counts of a hand-made result)."""
