@@ -244,16 +244,29 @@ def dist_setup(args):
     return ws, rank, local
 
 
+# vertices of oracle work a reference-arm run may take in all (warm-up and
+# timed steps): about three minutes on one host core
+REF_BUDGET_VERTICES = 300_000_000
+
+
+def ref_sample_cap(steps, warmup, requested):
+    """Vertices per step of the reference arm: the requested sample (the
+    cpu_baseline leg's), unless that many steps of it would take more than a
+    few minutes (then proportionally fewer, at least 65,536)."""
+    return min(requested, max(65536, REF_BUDGET_VERTICES // max(1, steps + warmup)))
+
+
 def run_reference(args, ws, rank):
     if rank != 0:
         return
     import numpy as np
     import oracle
+    sample_cap = ref_sample_cap(args.steps, args.warmup, args.ref_sample_vertices)
     if args.workload == "batch":
         from paper_2303_02724_gb300 import fields as F
         samples, n = [], 0
         for (e, sd, g) in F.batch_specs(3, args.batch_count):
-            if n + int(np.prod(e)) > args.ref_sample_vertices:
+            if n + int(np.prod(e)) > sample_cap:
                 continue
             samples.append(F.batch_field(e, sd, g).values)
             n += int(np.prod(e))
@@ -261,14 +274,14 @@ def run_reference(args, ws, rank):
     elif args.workload == "serve":
         samples, n = [], 0
         for v in serve_fields(64):
-            if n + int(v.size) > args.ref_sample_vertices:
+            if n + int(v.size) > sample_cap:
                 continue
             samples.append(v)
             n += int(v.size)
         desc = f"{len(samples)} requests of the served stream ({n} vertices)"
     else:
         fld = make_field(args.workload)
-        sample, desc = oracle_slab(fld, args.ref_sample_vertices)
+        sample, desc = oracle_slab(fld, sample_cap)
         samples, n = [sample], int(sample.size)
     for _ in range(args.warmup):
         for smp in samples:
@@ -508,7 +521,8 @@ def main():
     ap.add_argument("--workload", default="grf512", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-sample-vertices", type=int, default=4 * 1024 * 1024)
     ap.add_argument("--ref-sample-vertices", type=int, default=4 * 1024 * 1024,
-                    help="oracle sample of the reference arm (the same slabs as the cpu_baseline leg)")
+                    help="oracle sample per step of the reference arm (the same slabs as the cpu_baseline leg; "
+                         "fewer when the steps asked for would take the oracle more than a few minutes)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-threads", type=int, default=4,

@@ -151,6 +151,18 @@ def test_bench_reference_arm_line():
     assert "65536 vertices" in line["config"]["sample"]
 
 
+def test_bench_reference_sample_is_bounded():
+    """The reference arm keeps the cpu_baseline leg's sample for a usual run
+    and shrinks it when many steps would take the oracle more than a few
+    minutes in all."""
+    import bench
+    four_m = 4 * 1024 * 1024
+    assert bench.ref_sample_cap(20, 5, four_m) == four_m
+    big = bench.ref_sample_cap(200, 3, four_m)
+    assert big < four_m and big * 203 <= bench.REF_BUDGET_VERTICES
+    assert bench.ref_sample_cap(10 ** 7, 3, four_m) == 65536
+
+
 def test_bench_reference_arm_other_ranks_are_silent():
     """Under a multi-rank launch only rank 0 runs the reference arm; the
     other ranks exit 0 without work or output."""
